@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark: point-iterations per second of Lloyd's k-means with MTI pruning.
+
+One step = one whole k-means run (reset to the Forgy centroids, then Lloyd
+iterations until no assignment changes or the iteration limit) over the
+workload's points, which are resident in HBM before timing starts.  The
+metric is n * iterations / time.  Default workload: 66M points, d = 32,
+k = 20, a 20-component Gaussian mixture with random SPD covariances, Forgy
+seed 42, at most 50 iterations (the MTI FP32 configuration).
+
+Printed (rank 0, one JSON line): the device-timed throughput, the same run
+through the C ABI from pinned host memory (e2e), the roofline of the
+dominant kernel (its CUDA-event time per launch against its algorithmic
+bytes), the speed of plain FP32 Lloyd on the same input (with a check that it
+assigns identically), the FP64 CPU oracle timed on the host cores on a
+bounded sample (cpu_baseline), and the SM clocks sampled while timing.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload NAME] [--no-e2e] [--no-plain] [--no-cpu]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload ("replicas only": the data path has no exchange at one GPU per box).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+THROTTLE_BITS = {  # nvidia-smi clocks_event_reasons bitmask
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+    0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+    0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting",
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mti_66m_d32_k20")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while timing."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 4:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                bits = int(r[3], 16) if r[3].startswith("0x") else int(r[3])
+                for b, name in THROTTLE_BITS.items():
+                    if bits & b and name != "gpu_idle":
+                        reasons.add(name)
+            except ValueError:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernels_cu_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    src = os.path.join(ROOT, "paper_1606_08905_gb300", "csrc", "kernels.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+def make_points(wl, device):
+    from paper_1606_08905_gb300 import synth
+    return synth.make(wl["kind"], wl["n"], wl["d"], wl["k"], wl["data_seed"], device=device)
+
+
+def cpu_oracle_run(Xs, k, max_iters, prune, threads):
+    import oracle
+    C0 = oracle.forgy_centroids(Xs, k, 42)
+    t = time.perf_counter()
+    r = oracle.run(Xs, C0, max_iters, prune=prune, nthreads=threads)
+    dt = time.perf_counter() - t
+    return Xs.shape[0] * r.iters, dt, r.iters
+
+
+def cpu_sample_rows(wl, seconds):
+    # the FP64 oracle does ~4e7 MTI point-iterations/s or ~1.4e7 plain on 8 x86 cores
+    rate = 2.0e7 if wl["prune"] else 0.7e7
+    per_run = rate * seconds / wl["max_iters"]
+    return int(max(20_000, min(wl["n"], per_run)))
+
+
+def reference_arm(args, wl, world, rank):
+    """The FP64 CPU oracle as the reference arm (there is no installable
+    reference implementation: the paper ships no code)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import torch  # noqa: F401
+    from paper_1606_08905_gb300 import synth
+    threads = os.cpu_count() or 1
+    total_budget = 150.0
+    per_step = max(2.0, total_budget / max(1, args.steps + args.warmup))
+    ns = cpu_sample_rows(wl, per_step)
+    Xs = synth.make(wl["kind"], ns, wl["d"], wl["k"], wl["data_seed"], device="cpu").numpy()
+    for _ in range(args.warmup):
+        cpu_oracle_run(Xs, wl["k"], wl["max_iters"], wl["prune"], threads)
+    pts, secs, its = 0, 0.0, []
+    for _ in range(args.steps):
+        p, dt, it = cpu_oracle_run(Xs, wl["k"], wl["max_iters"], wl["prune"], threads)
+        pts += p
+        secs += dt
+        its.append(it)
+    value = pts / secs
+    sample = f"first {ns} points of the workload's distribution (CPU-drawn), full run per step"
+    line = {
+        "impl": "reference", "metric": "point-iterations/sec", "value": value,
+        "unit": "point-iterations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl, args.workload, world),
+        "cpu_baseline": {"value": value, "unit": "point-iterations/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "point-iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "iterations_per_step": its,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, name, world):
+    return {"workload": name, "n": wl["n"], "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
+            "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42",
+            "data_seed": wl["data_seed"], "points_dtype": "f32",
+            "l2": f"inputs larger than L2 ({wl['n'] * wl['d'] * 4 / 1e9:.2f} GB of points)",
+            "parallelism": f"replicas x{world}"}
+
+
+def our_arm(args, wl, world, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1606_08905_gb300 import build as kbuild
+    from paper_1606_08905_gb300 import knor
+    kbuild.build()
+    knor.load()
+    torch.cuda.set_device(local)
+    n, d, k, T = wl["n"], wl["d"], wl["k"], wl["max_iters"]
+    X = make_points(wl, "cuda")
+    torch.cuda.synchronize()
+    ctx = knor.Context(X, k, seed=42, prune=wl["prune"])
+    stream = torch.cuda.ExternalStream(ctx.stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        ctx.reset()
+        ctx.run(T)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        ctx.reset()
+        done, _ = ctx.run(T)
+        iters.append(done)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    pts = float(n) * sum(iters)
+    if world > 1:
+        t = torch.tensor([ms, pts], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, pts_all = float(mx[0]), float(t[1])
+    else:
+        ms_max, pts_all = ms, pts
+    value = pts_all / (ms_max / 1000.0)
+    launches = sum(3 + it * (4 if wl["prune"] else 3) for it in iters)
+
+    # ---- per-kernel CUDA-event timing (profiling mode: kernel by kernel on the
+    # library stream, same reset + run steps), for the roofline
+    ctx.set_profiling(True)
+    ctx.profile(reset=True)
+    prof_iters = []
+    prof_recs = []
+    for _ in range(max(1, min(args.steps, 3))):
+        ctx.reset()
+        done, recs = ctx.run(T)
+        prof_iters.append(done)
+        prof_recs.extend(recs)
+    prof = ctx.profile(reset=True)
+    ctx.set_profiling(False)
+    # algorithmic bytes per launch: dense n(4d + 16);
+    # MTI 8n + active (4d + 8) with active = n - clause1_skipped
+    dense_bytes = sum(n * (4 * d + 16) for r in prof_recs if r["clause1_skipped"] == 0 and (
+        r["iteration"] == 1 or not wl["prune"]))
+    mti_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in prof_recs
+                    if wl["prune"] and r["iteration"] > 1)
+    peaks, peak_src = measured_peaks()
+    kernels = {}
+    for name, byts in (("dense", dense_bytes), ("mti", mti_bytes)):
+        launches_k, ms_k = prof[name]
+        if launches_k == 0 or ms_k <= 0:
+            continue
+        gbs = byts / (ms_k / 1000.0) / 1e9
+        kernels[name] = {"launches": launches_k, "ms_total": ms_k, "ms_per_launch": ms_k / launches_k,
+                         "algorithmic_bytes_per_launch": byts / launches_k, "achieved_gbs": gbs,
+                         "frac_of_" + peak_src + "_hbm": gbs / peaks["hbm_gbs"]}
+    total_prof_ms = sum(v[1] for v in prof.values())
+    dom = max(kernels, key=lambda kk: kernels[kk]["ms_total"])
+    kname = {"dense": "k_dense", "mti": "k_mti"}[dom]
+    roof = {"kernel": f"{kname}<{d}>", "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"],
+            "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
+            "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"],
+            "traffic": ncu_traffic(kname, args.workload),
+            "share_of_kernel_time": kernels[dom]["ms_total"] / total_prof_ms}
+
+    # ---- plain FP32 Lloyd on the same points: speed, and identical assignments
+    plain = None
+    if not args.no_plain and wl["prune"]:
+        ctx.reset()
+        ctx.run(T)
+        a_mti = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.assignments(a_mti)
+        with knor.Context(X, k, seed=42, prune=False) as pc:
+            pc.reset()
+            pc.run(T)
+            pstream = torch.cuda.ExternalStream(pc.stream)
+            ps = max(1, min(args.steps, 2))
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(pstream)
+            pits = 0
+            for _ in range(ps):
+                pc.reset()
+                done, _ = pc.run(T)
+                pits += done
+            q1.record(pstream)
+            torch.cuda.synchronize()
+            a_plain = torch.empty(n, dtype=torch.int32, device="cuda")
+            pc.assignments(a_plain)
+            pv = n * pits / (q0.elapsed_time(q1) / 1000.0)
+            plain = {"value": pv, "unit": "point-iterations/s", "speedup_of_mti": (value / world) / pv,
+                     "identical_assignments": bool(torch.equal(a_mti, a_plain)),
+                     "iterations": pits // ps}
+
+    # ---- e2e through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((n, d), dtype=torch.float32, pin_memory=True)
+        Xh.copy_(X)
+        ah = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        Ch = torch.empty((k, d), dtype=torch.float64, pin_memory=True)
+        del ctx
+        torch.cuda.synchronize()
+        es = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(es):
+            with knor.Context(Xh, k, seed=42, prune=wl["prune"]) as c2:
+                done, _ = c2.run(T)
+                c2.assignments(ah)
+                c2.centroids(Ch)
+                e_iters += done
+        dt = time.perf_counter() - t0
+        e2e = {"value": n * e_iters / dt, "unit": "point-iterations/s",
+               "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * 4 + k * d * 8,
+               "steps": es, "ms_per_step": 1000.0 * dt / es,
+               "includes": "knor_create (H2D copy, input validation, allocation, graph build), knor_run, "
+                           "knor_get_assignments, knor_get_centroids, knor_destroy"}
+
+    # ---- CPU oracle on a bounded sample of the same points (rank 0, N = 1)
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        threads = os.cpu_count() or 1
+        ns = cpu_sample_rows(wl, args.cpu_seconds)
+        Xs = X[:ns].cpu().numpy()
+        p, dt, it = cpu_oracle_run(Xs, k, T, wl["prune"], threads)
+        cpu = {"value": p / dt, "unit": "point-iterations/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {ns} of the {n} points, one full run ({it} iterations, "
+                         f"{'MTI' if wl['prune'] else 'plain'}, FP64), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": "point-iterations/sec", "value": value, "unit": "point-iterations/s",
+                "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(wl, args.workload, world),
+                "iterations_per_step": iters, "roofline": roof, "kernels": kernels,
+                "cpu_baseline": cpu, "e2e": e2e, "vs_plain_fp32": plain,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    from paper_1606_08905_gb300 import synth
+    if args.workload not in synth.WORKLOADS:
+        raise SystemExit(f"unknown workload {args.workload}; one of {sorted(synth.WORKLOADS)}")
+    wl = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, wl, world, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    try:
+        our_arm(args, wl, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * knor.h -- C ABI of libknor.so: Lloyd's k-means with MTI pruning on one
+ * GB300 (sm_103a).
+ *
+ * Paper: Mhembere, Zheng, Priebe, Vogelstein, Burns, "knor: A NUMA-Optimized
+ * In-Memory, Distributed and Semi-External-Memory k-means Library", HPDC'17,
+ * arXiv 1606.08905.  Section references below are to that paper:
+ *   "Nomenclature"                        V in R^{n x d}, k, iteration t,
+ *                                         Euclidean d(v, c), drift f(c^t)
+ *   "Parallel Lloyd's Algorithm"          Phase I / Phase II, Algorithm 1
+ *   "Minimal Triangle Inequality (MTI)
+ *    Pruning"                             Clauses 1-3, the upper bound u^t
+ *   "Asymptotic Memory Consumption"       the k x k centroid table, O(n) bound
+ *
+ * Conventions (every function):
+ *   - Returns a knor_status; never aborts the process.  On error the context
+ *     stays valid and destroyable, and knor_last_error() describes the error.
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the context's GPU; the library tells
+ *     them apart with cudaPointerGetAttributes.  Inputs are copied; the caller
+ *     keeps ownership of every buffer it passes.  Outputs go to caller-owned
+ *     buffers and are complete when the call returns.
+ *   - All arrays are dense and row-major.  Points are FP32; centroids are
+ *     returned as FP64 (the master copy) or FP32 (the copy the scan used).
+ *   - A context is not thread-safe.  It owns all its device memory and one
+ *     CUDA stream, created on the device current at knor_create.
+ *   - Assignments follow Algorithm 1's scan: the nearest centroid, ties to the
+ *     lowest index.  Iteration 1 starts from "no assignment", so every point
+ *     counts as changed in it.
+ */
+#ifndef KNOR_H
+#define KNOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct knor_ctx knor_ctx; /* opaque; owns all device memory */
+
+typedef enum {
+    KNOR_OK = 0,
+    KNOR_ERR_ARG = -1,     /* invalid argument (sizes, NULL, NaN/Inf input, ...) */
+    KNOR_ERR_OOM = -2,     /* a device or host allocation failed */
+    KNOR_ERR_CUDA = -3,    /* a CUDA call failed; the message names it */
+    KNOR_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up */
+    KNOR_ERR_STATE = -5    /* call not valid in the context's current state */
+} knor_status;
+
+typedef enum {
+    KNOR_INIT_FORGY = 0,   /* k distinct rows chosen from the seed (below) */
+    KNOR_INIT_EXPLICIT = 1 /* caller supplies C^0 with knor_set_init_centroids */
+} knor_init;
+
+typedef enum {
+    KNOR_PREC_FP32 = 0, /* FP32 distances, direct form sum_i (x_i - c_i)^2 */
+    KNOR_PREC_BF16 = 1, /* tensor-core BF16 distance block + exact FP32 recheck */
+    KNOR_PREC_FP8 = 2   /* tensor-core FP8 e4m3 with per-dimension scales + recheck */
+} knor_precision;
+
+/* Options.  A zero-initialised struct gives the defaults: MTI pruning on,
+ * FP32 distances, sums maintained by deltas, no debug checks. */
+typedef struct {
+    int32_t no_prune;             /* 0: MTI pruning; 1: plain Lloyd (every distance) */
+    int32_t precision;            /* knor_precision */
+    int32_t full_recompute_every; /* 0: never; m > 0: rebuild the cluster sums
+                                     from all points every m-th iteration */
+    int32_t debug_invariants;     /* 1: after each MTI iteration, check on the
+                                     GPU that every bound u >= d(x, c_a) and count
+                                     violations into knor_iter_stats.violations */
+} knor_opts;
+
+/* Per-iteration counters. */
+typedef struct {
+    int64_t changed;         /* points whose assignment changed */
+    int64_t clause1_skipped; /* points skipped by MTI Clause 1 (nothing read) */
+    int64_t dist_evals;      /* point-centroid distances computed */
+    int64_t rechecked;       /* precision forms: rows re-scored exactly in FP32 */
+    int32_t empty;           /* clusters with no member after the iteration */
+    int32_t iteration;       /* 1-based iteration number */
+    int64_t violations;      /* debug_invariants only: bounds found below the true distance */
+} knor_iter_stats;
+
+/* Creates a context holding a copy of the n x d FP32 points (host or device)
+ * and the initial centroids C^0.
+ *   init = KNOR_INIT_FORGY: C^0 = rows idx[0..k-1] in drawn order, where idx
+ *     are k distinct indices of [0, n) drawn by Floyd's sampling algorithm
+ *     (for j = n-k .. n-1: t = floor(r * (j+1) / 2^64) with r the next
+ *     SplitMix64 output of state `seed`; keep t unless already kept, else j).
+ *     The paper states no initialisation; this one is reproducible.
+ *   init = KNOR_INIT_EXPLICIT: C^0 must be set with knor_set_init_centroids
+ *     before the first iteration (KNOR_ERR_STATE otherwise).
+ * Errors: KNOR_ERR_ARG if points or out is NULL, n < 1, d < 1, k < 1, k > n,
+ * n*d > 2^40, or any coordinate is NaN, infinite or of magnitude above 1e15
+ * (so no squared distance can overflow FP32).  opts may be NULL (defaults).
+ * On success *out owns the context; free it with knor_destroy. */
+knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, knor_init init,
+                        uint64_t seed, const knor_opts *opts, knor_ctx **out);
+
+/* Sets C^0 (k x d FP64, host or device) and resets the run: no assignment, u
+ * unset, iteration 0.  Valid for any init mode.  Coordinates must be finite. */
+knor_status knor_set_init_centroids(knor_ctx *ctx, const double *c_kxd);
+
+/* Returns the context to C^0 and iteration 0 (no assignment). */
+knor_status knor_reset(knor_ctx *ctx);
+
+/* One Lloyd iteration ("Parallel Lloyd's Algorithm"): Phase I with MTI
+ * pruning (Clauses 1-3) unless no_prune, then Phase II (means; an empty
+ * cluster keeps its centroid).  `out` may be NULL. */
+knor_status knor_iterate(knor_ctx *ctx, knor_iter_stats *out);
+
+/* Iterates until an iteration changes no assignment or max_iters iterations
+ * have run in this call (the paper's "repeat until converged").  The loop
+ * runs on the device (one CUDA graph launch).  *iters_done (may be NULL)
+ * receives the number of iterations executed, including the final one that
+ * changed nothing; per_iter (may be NULL) must hold max_iters records. */
+knor_status knor_run(knor_ctx *ctx, int32_t max_iters, int32_t *iters_done,
+                     knor_iter_stats *per_iter);
+
+/* Current assignments, n int32 (host or device buffer).  -1 before the first
+ * iteration. */
+knor_status knor_get_assignments(const knor_ctx *ctx, int32_t *out_n);
+
+/* Current centroids: the FP64 master copy (k x d) or the FP32 copy (k x d,
+ * each the FP64 value rounded to nearest) that the next scan uses.  Host or
+ * device buffers. */
+knor_status knor_get_centroids(const knor_ctx *ctx, double *out_kxd);
+knor_status knor_get_centroids_f32(const knor_ctx *ctx, float *out_kxd);
+
+/* The Forgy row indices (k int64, host buffer).  KNOR_ERR_STATE for
+ * KNOR_INIT_EXPLICIT contexts. */
+knor_status knor_get_init_indices(const knor_ctx *ctx, int64_t *out_k);
+
+/* Iterations completed since the last reset. */
+knor_status knor_get_iteration(const knor_ctx *ctx, int32_t *out);
+
+/* The CUDA stream (a cudaStream_t) every kernel of this context runs on. */
+void *knor_stream(const knor_ctx *ctx);
+
+/* Per-kernel timing.  With profiling on, knor_iterate and knor_run launch the
+ * iteration's kernels one by one (no graph; the run loop moves to the host,
+ * one synchronisation per iteration) and bracket each with CUDA events on the
+ * context's stream.  knor_get_profile returns the launches and the summed
+ * event durations per kernel since the last reset of the profile
+ * (reset_after = 1 clears them after reading). */
+typedef enum {
+    KNOR_KERNEL_DENSE = 0,  /* full scan + fresh sums (plain Lloyd, MTI iteration 1) */
+    KNOR_KERNEL_MTI = 1,    /* Clause-1 test + pruned scan + delta sums */
+    KNOR_KERNEL_REDUCE = 2, /* ordered FP64 merge of per-CTA sums, new centroids */
+    KNOR_KERNEL_TABLE = 3,  /* drift, k x k half-distance table, s(c) */
+    KNOR_KERNEL_COUNT = 4
+} knor_kernel;
+typedef struct {
+    int64_t launches[KNOR_KERNEL_COUNT];
+    double ms[KNOR_KERNEL_COUNT];
+} knor_profile;
+knor_status knor_set_profiling(knor_ctx *ctx, int32_t on);
+knor_status knor_get_profile(knor_ctx *ctx, knor_profile *out, int32_t reset_after);
+
+/* Checkpoint.  knor_get_state with buf == NULL stores the needed size in
+ * *size; otherwise it writes the state (header, FP64 centroids and sums,
+ * counts, drift table, assignments and bounds) into the host buffer buf of
+ * *size bytes.  knor_set_state restores a state taken from a context with the
+ * same n, d, k and options; continuing from it reproduces the original run
+ * bit for bit. */
+knor_status knor_get_state(const knor_ctx *ctx, void *buf, size_t *size);
+knor_status knor_set_state(knor_ctx *ctx, const void *buf, size_t size);
+
+/* Message for the last error on this context ("" if none).  Valid until the
+ * next call on the context.  ctx may be NULL for errors of knor_create. */
+const char *knor_last_error(const knor_ctx *ctx);
+
+/* Frees the context and all its device memory.  NULL is ignored. */
+void knor_destroy(knor_ctx *ctx);
+
+/* Library version, "major.minor.patch". */
+const char *knor_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNOR_H */

@@ -1,0 +1,738 @@
+// knor_ctx.cu -- host runtime of libknor.so: the C ABI of include/knor.h.
+//
+// A context owns the points, the per-point MTI state, the centroid tables and
+// one CUDA stream.  One Lloyd iteration is the launch sequence
+//   k_dense | k_mti  ->  k_reduce  ->  k_table  [-> k_check_bounds]
+// captured once into a CUDA graph (knor_iterate) and once into the body of a
+// conditional WHILE node (knor_run), so a whole run is a single graph launch
+// and the loop stops on the device when an iteration changes nothing.
+#include "knor.h"
+#include "knor_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+using namespace knor;
+
+namespace {
+
+constexpr int kStatsCap = 1 << 16; // records per knor_run call
+constexpr uint32_t kStateMagic = 0x4b4e4f52u; // "KNOR"
+constexpr uint32_t kStateVersion = 1;
+
+// Device flags (int32 each).
+enum Flag { F_RUN_ITER = 0, F_TOTAL_ITER, F_MAX_ITERS, F_MODE_DENSE, F_NSLOTS, F_FRESH, F_COUNT };
+
+// SplitMix64 (Steele, Lea and Flood 2014): golden-ratio increment, then the
+// published finaliser.
+uint64_t splitmix64(uint64_t &state) {
+    state += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Floyd's sampling (Bentley and Floyd 1987): k distinct indices of [0, n) in
+// the order they are kept; the uniform draw on [0, j] is the high word of
+// r * (j + 1).
+std::vector<int64_t> forgy_indices(int64_t n, int32_t k, uint64_t seed) {
+    std::vector<int64_t> out;
+    out.reserve((size_t)k);
+    std::unordered_set<int64_t> kept;
+    uint64_t state = seed;
+    for (int64_t j = n - k; j < n; ++j) {
+        const uint64_t r = splitmix64(state);
+        const int64_t t = (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)(j + 1)) >> 64);
+        const int64_t v = kept.count(t) ? j : t;
+        kept.insert(v);
+        out.push_back(v);
+    }
+    return out;
+}
+
+float f32_up(double v) { // smallest float >= v
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct StateHeader {
+    uint32_t magic, version;
+    int64_t n;
+    int32_t d, k;
+    int32_t no_prune, precision, recompute, total_iter, mode_dense, pad;
+};
+
+} // namespace
+
+struct knor_ctx {
+    int dev = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int32_t d = 0, k = 0;
+    knor_opts opts{};
+    knor_init init = KNOR_INIT_FORGY;
+    uint64_t seed = 0;
+    std::vector<int64_t> init_idx;
+    bool c0_set = false;
+    mutable std::string err;
+
+    float *X = nullptr;
+    PtState *st = nullptr;
+    double *C0 = nullptr, *C64 = nullptr, *S = nullptr, *part_S = nullptr;
+    float *C32 = nullptr, *C32n = nullptr, *halfD = nullptr, *s = nullptr, *F = nullptr;
+    long long *cnt = nullptr, *cnt_next = nullptr, *part_cnt = nullptr;
+    Counters *ctr = nullptr;
+    IterStats *stats = nullptr;
+    int32_t *flags = nullptr;
+    int64_t *d_idx = nullptr;
+    unsigned long long *d_bad = nullptr;
+    IterStats *h_stats = nullptr; // pinned
+
+    int dv = 0;
+    int part_stride = 1;
+    size_t smem_dense = 0, smem_mti = 0;
+    int grid_dense = 0, grid_mti = 0;
+    IterParams ip_dense{}, ip_mti{};
+    FinParams fp{};
+
+    cudaGraphExec_t iter_exec = nullptr, run_exec = nullptr;
+
+    // profiling (host-driven loop, CUDA events around every kernel)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    knor_profile prof{};
+    int32_t host_total_iter = 0;
+};
+
+static thread_local std::string g_create_err;
+
+#define KNOR_CUDA(ctx, call)                                                                    \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+            return e_ == cudaErrorMemoryAllocation ? KNOR_ERR_OOM : KNOR_ERR_CUDA;              \
+        }                                                                                       \
+    } while (0)
+
+static knor_status fail(const knor_ctx *c, knor_status st, const std::string &msg) {
+    c->err = msg;
+    return st;
+}
+
+template <class T>
+static knor_status dalloc(knor_ctx *c, T **p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, KNOR_ERR_OOM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) +
+                                         " bytes): " + cudaGetErrorString(e));
+    }
+    return KNOR_OK;
+}
+
+static void free_all(knor_ctx *c) {
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
+    if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+    void *bufs[] = {c->X, c->st, c->C0, c->C64, c->S, c->part_S, c->C32, c->C32n, c->halfD, c->s,
+                    c->F, c->cnt, c->cnt_next, c->part_cnt, c->ctr, c->stats, c->flags, c->d_idx, c->d_bad};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+// Shared-memory layout of a point kernel; returns the byte size.
+static size_t plan_layout(const knor_ctx *c, bool mti, IterParams &p) {
+    const int d = c->d, k = c->k, dv = c->dv;
+    const size_t kd = (size_t)k * d;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> int32_t {
+        const size_t o = off;
+        off = (off + bytes + 15) & ~(size_t)15;
+        return (int32_t)o;
+    };
+    const size_t budget = 200 * 1024;
+    // fixed parts first
+    p.dpad = d + 4;
+    size_t tile_bytes = 0;
+    p.stages = 1;
+    if (dv > 0) {
+        const size_t one = (size_t)NT * p.dpad * sizeof(float);
+        p.stages = (!mti && 2 * one <= 110 * 1024) ? 2 : 1;
+        tile_bytes = p.stages * one;
+    }
+    size_t fixed = tile_bytes + 3 * NT * sizeof(int) + 256 + (mti ? QCAP * sizeof(int2) : 0);
+    p.cent_smem = (kd * sizeof(float) <= 64 * 1024 && fixed + kd * 4 <= budget) ? 1 : 0;
+    if (p.cent_smem) fixed += kd * 4;
+    p.halfD_smem = 0;
+    if (mti && (size_t)k * k * 4 <= 48 * 1024 && fixed + (size_t)k * k * 4 <= budget) {
+        p.halfD_smem = 1;
+        fixed += (size_t)k * k * 4;
+    }
+    const bool sf = (size_t)k * 8 <= 32 * 1024 && fixed + (size_t)k * 8 <= budget;
+    if (sf) fixed += (size_t)k * 8;
+    p.acc_global = (fixed + 2 * kd * 4 + (size_t)k * 4 > budget) ? 1 : 0;
+
+    p.off_acc_hi = take(p.acc_global ? 0 : kd * 4);
+    p.off_acc_lo = take(p.acc_global ? 0 : kd * 4);
+    p.off_cnt = take(p.acc_global ? 0 : (size_t)k * 4);
+    p.off_cent = take(p.cent_smem ? kd * 4 : 0);
+    p.off_halfD = take(p.halfD_smem ? (size_t)k * k * 4 : 0);
+    p.off_s = sf ? take((size_t)k * 4) : -1;
+    p.off_F = sf ? take((size_t)k * 4) : -1;
+    p.off_tb = take(NT * 4);
+    p.off_ta = take(NT * 4);
+    p.off_ti = take(NT * 4);
+    p.off_tile = take(tile_bytes);
+    p.off_queue = take(mti ? QCAP * sizeof(int2) : 0);
+    p.off_misc = take(256);
+    return off;
+}
+
+static void fill_common(knor_ctx *c, IterParams &p) {
+    p.X = c->X;
+    p.n = c->n;
+    p.d = c->d;
+    p.k = c->k;
+    p.st = c->st;
+    p.C32 = c->C32;
+    p.halfD = c->halfD;
+    p.s = c->s;
+    p.F = c->F;
+    p.part_S = c->part_S;
+    p.part_cnt = c->part_cnt;
+    p.ctr = c->ctr;
+    // FP32 error bound of the direct-form squared distance: relative
+    // (1 - (d+2) u)^-1 - 1 with u = 2^-24, plus d 2^-150 absolute.
+    const double u = std::ldexp(1.0, -24);
+    const double g = (c->d + 2) * u / (1.0 - (c->d + 2) * u);
+    p.g_up = f32_up(1.0 / (1.0 - (c->d + 2) * u));
+    p.onepk = f32_up(1.0 + g);
+    p.tau = std::ldexp(1.0f, -40);
+    p.tiny = (float)std::ldexp((double)std::min(c->d, 1 << 20), -149);
+    p.mti = c->opts.no_prune ? 0 : 1;
+}
+
+static knor_status enqueue_iteration(knor_ctx *c, cudaStream_t s, unsigned long long cond) {
+    int32_t *fl = c->flags;
+    if (c->ip_dense.acc_global) { // one slot, accumulated by atomics: start from zero
+        KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
+        KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
+    }
+    KNOR_CUDA(c, launch_dense(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE,
+                              fl + F_NSLOTS, fl + F_FRESH));
+    if (!c->opts.no_prune) {
+        KNOR_CUDA(c, launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE,
+                                fl + F_NSLOTS, fl + F_FRESH));
+    }
+    KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
+    FinParams f = c->fp;
+    f.snapshot = 1;
+    f.cond_handle = cond;
+    KNOR_CUDA(c, launch_table(f, fl + F_MODE_DENSE, c->opts.no_prune ? 0 : 1, c->opts.full_recompute_every,
+                              c->opts.no_prune ? 1 : 0, s));
+    if (c->opts.debug_invariants && !c->opts.no_prune)
+        KNOR_CUDA(c, launch_check_bounds(c->X, c->n, c->d, c->st, c->C32, c->F, c->stats, fl + F_RUN_ITER, s));
+    return KNOR_OK;
+}
+
+// One iteration launched kernel by kernel with events around each (profiling
+// mode).  The host decides which scan runs with the same rule k_table writes
+// into the device flag, so the launched scan is the one that does the work.
+static knor_status profiled_iteration(knor_ctx *c) {
+    cudaStream_t s = c->stream;
+    int32_t *fl = c->flags;
+    if (c->ev.empty()) {
+        c->ev.resize(2 * KNOR_KERNEL_COUNT);
+        for (auto &e : c->ev) KNOR_CUDA(c, cudaEventCreate(&e));
+    }
+    const int m = c->opts.full_recompute_every;
+    const int tot = c->host_total_iter;
+    const bool dense = c->opts.no_prune || tot == 0 || (m > 0 && (tot + 1) % m == 0);
+    bool used[KNOR_KERNEL_COUNT] = {false, false, false, false};
+    if (c->ip_dense.acc_global) {
+        KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
+        KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
+    }
+    if (dense) {
+        KNOR_CUDA(c, cudaEventRecord(c->ev[0], s));
+        KNOR_CUDA(c, launch_dense(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE,
+                                  fl + F_NSLOTS, fl + F_FRESH));
+        KNOR_CUDA(c, cudaEventRecord(c->ev[1], s));
+        used[KNOR_KERNEL_DENSE] = true;
+    } else {
+        KNOR_CUDA(c, cudaEventRecord(c->ev[2], s));
+        KNOR_CUDA(c, launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE,
+                                fl + F_NSLOTS, fl + F_FRESH));
+        KNOR_CUDA(c, cudaEventRecord(c->ev[3], s));
+        used[KNOR_KERNEL_MTI] = true;
+    }
+    KNOR_CUDA(c, cudaEventRecord(c->ev[4], s));
+    KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
+    KNOR_CUDA(c, cudaEventRecord(c->ev[5], s));
+    FinParams f = c->fp;
+    f.snapshot = 1;
+    f.cond_handle = 0;
+    KNOR_CUDA(c, cudaEventRecord(c->ev[6], s));
+    KNOR_CUDA(c, launch_table(f, fl + F_MODE_DENSE, c->opts.no_prune ? 0 : 1, m, c->opts.no_prune ? 1 : 0, s));
+    KNOR_CUDA(c, cudaEventRecord(c->ev[7], s));
+    used[KNOR_KERNEL_REDUCE] = used[KNOR_KERNEL_TABLE] = true;
+    if (c->opts.debug_invariants && !c->opts.no_prune)
+        KNOR_CUDA(c, launch_check_bounds(c->X, c->n, c->d, c->st, c->C32, c->F, c->stats, fl + F_RUN_ITER, s));
+    KNOR_CUDA(c, cudaStreamSynchronize(s));
+    for (int kk = 0; kk < KNOR_KERNEL_COUNT; ++kk) {
+        if (!used[kk]) continue;
+        float ms = 0.0f;
+        KNOR_CUDA(c, cudaEventElapsedTime(&ms, c->ev[2 * kk], c->ev[2 * kk + 1]));
+        c->prof.ms[kk] += ms;
+        c->prof.launches[kk] += 1;
+    }
+    c->host_total_iter += 1;
+    return KNOR_OK;
+}
+
+static knor_status build_graphs(knor_ctx *c) {
+    // single iteration
+    {
+        cudaGraph_t g = nullptr;
+        KNOR_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        knor_status st = enqueue_iteration(c, c->stream, 0);
+        cudaGraph_t got = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &got);
+        if (st != KNOR_OK) {
+            if (got) cudaGraphDestroy(got);
+            return st;
+        }
+        KNOR_CUDA(c, e);
+        g = got;
+        e = cudaGraphInstantiate(&c->iter_exec, g, 0);
+        cudaGraphDestroy(g);
+        KNOR_CUDA(c, e);
+    }
+    // whole run: WHILE node whose body is one iteration; k_table sets the
+    // condition from the iteration's changed count and the run limit.
+    {
+        cudaGraph_t g = nullptr;
+        KNOR_CUDA(c, cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); KNOR_CUDA(c, e); }
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); KNOR_CUDA(c, e); }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); KNOR_CUDA(c, e); }
+        knor_status st = enqueue_iteration(c, c->stream, (unsigned long long)h);
+        cudaGraph_t got = nullptr;
+        e = cudaStreamEndCapture(c->stream, &got);
+        if (st != KNOR_OK) { cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) { cudaGraphDestroy(g); KNOR_CUDA(c, e); }
+        e = cudaGraphInstantiate(&c->run_exec, g, 0);
+        cudaGraphDestroy(g);
+        KNOR_CUDA(c, e);
+    }
+    return KNOR_OK;
+}
+
+// C^0 is in c->C0: reset centroids, sums, bounds and tables to iteration 0.
+static knor_status reset_run(knor_ctx *c) {
+    cudaStream_t s = c->stream;
+    const size_t kd = (size_t)c->k * c->d;
+    KNOR_CUDA(c, cudaMemcpyAsync(c->C64, c->C0, kd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    KNOR_CUDA(c, launch_round_c32(c->C0, c->C32, (int64_t)kd, s));
+    KNOR_CUDA(c, cudaMemcpyAsync(c->C32n, c->C32, kd * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->S, 0, kd * sizeof(double), s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->cnt, 0, (size_t)c->k * sizeof(long long), s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->cnt_next, 0, (size_t)c->k * sizeof(long long), s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->F, 0, (size_t)c->k * sizeof(float), s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    KNOR_CUDA(c, launch_init_state(c->st, c->n, s));
+    int32_t fl[F_COUNT] = {0, 0, 1, 1, 1, 1};
+    KNOR_CUDA(c, cudaMemcpyAsync(c->flags, fl, sizeof(fl), cudaMemcpyHostToDevice, s));
+    c->host_total_iter = 0;
+    // tables for C^0 (drift 0, no record)
+    FinParams f = c->fp;
+    f.snapshot = 0;
+    f.cond_handle = 0;
+    KNOR_CUDA(c, launch_table(f, c->flags + F_MODE_DENSE, c->opts.no_prune ? 0 : 1, 0, 1, s));
+    KNOR_CUDA(c, cudaStreamSynchronize(s));
+    return KNOR_OK;
+}
+
+extern "C" {
+
+const char *knor_version(void) { return "0.1.0"; }
+
+const char *knor_last_error(const knor_ctx *ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+void *knor_stream(const knor_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
+
+void knor_destroy(knor_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, knor_init init, uint64_t seed,
+                        const knor_opts *opts, knor_ctx **out) {
+    g_create_err.clear();
+    if (!out) { g_create_err = "knor_create: out is NULL"; return KNOR_ERR_ARG; }
+    *out = nullptr;
+    if (!points) { g_create_err = "knor_create: points is NULL"; return KNOR_ERR_ARG; }
+    if (n < 1 || d < 1 || k < 1) { g_create_err = "knor_create: need n >= 1, d >= 1, k >= 1"; return KNOR_ERR_ARG; }
+    if ((int64_t)k > n) { g_create_err = "knor_create: k > n"; return KNOR_ERR_ARG; }
+    if ((double)n * (double)d > std::ldexp(1.0, 40)) { g_create_err = "knor_create: n*d above 2^40"; return KNOR_ERR_ARG; }
+    if (n > (int64_t)1 << 31) { g_create_err = "knor_create: n above 2^31"; return KNOR_ERR_ARG; }
+    if ((double)k * (double)d > (double)(1 << 28)) { g_create_err = "knor_create: k*d above 2^28"; return KNOR_ERR_ARG; }
+    if (init != KNOR_INIT_FORGY && init != KNOR_INIT_EXPLICIT) { g_create_err = "knor_create: bad init"; return KNOR_ERR_ARG; }
+    knor_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != KNOR_PREC_FP32) {
+        g_create_err = "knor_create: this build implements precision KNOR_PREC_FP32 only";
+        return KNOR_ERR_ARG;
+    }
+    if (o.full_recompute_every < 0) { g_create_err = "knor_create: full_recompute_every < 0"; return KNOR_ERR_ARG; }
+
+    knor_ctx *c = new knor_ctx();
+    c->n = n; c->d = d; c->k = k; c->opts = o; c->init = init; c->seed = seed;
+    auto bail = [&](knor_status st) {
+        g_create_err = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    };
+#define KC(call) do { knor_status s_ = (call); if (s_ != KNOR_OK) return bail(s_); } while (0)
+#define KCU(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { c->err = std::string(#call) + ": " + cudaGetErrorString(e_); cudaGetLastError(); return bail(e_ == cudaErrorMemoryAllocation ? KNOR_ERR_OOM : KNOR_ERR_CUDA); } } while (0)
+    KCU(cudaGetDevice(&c->dev));
+    KCU(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+    KCU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    const size_t nd = (size_t)n * d, kd = (size_t)k * d;
+    KC(dalloc(c, &c->X, nd));
+    KCU(cudaMemcpyAsync(c->X, points, nd * sizeof(float),
+                        is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    KC(dalloc(c, &c->d_bad, 1));
+    KCU(cudaMemsetAsync(c->d_bad, 0, sizeof(unsigned long long), c->stream));
+    KCU(launch_validate(c->X, (int64_t)nd, c->d_bad, c->stream));
+    unsigned long long bad = 0;
+    KCU(cudaMemcpyAsync(&bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    if (bad) {
+        c->err = "knor_create: " + std::to_string(bad) + " coordinates are NaN, infinite or above 1e15 in magnitude";
+        return bail(KNOR_ERR_ARG);
+    }
+    KC(dalloc(c, &c->st, (size_t)n));
+    KC(dalloc(c, &c->C0, kd));
+    KC(dalloc(c, &c->C64, kd));
+    KC(dalloc(c, &c->S, kd));
+    KC(dalloc(c, &c->C32, kd));
+    KC(dalloc(c, &c->C32n, kd));
+    KC(dalloc(c, &c->halfD, (size_t)k * k));
+    KC(dalloc(c, &c->s, (size_t)k));
+    KC(dalloc(c, &c->F, (size_t)k));
+    KC(dalloc(c, &c->cnt, (size_t)k));
+    KC(dalloc(c, &c->cnt_next, (size_t)k));
+    KC(dalloc(c, &c->ctr, 1));
+    KC(dalloc(c, &c->stats, kStatsCap));
+    KC(dalloc(c, &c->flags, F_COUNT));
+    KCU(cudaMallocHost((void **)&c->h_stats, sizeof(IterStats) * kStatsCap));
+
+    // kernel configurations and persistent grids
+    c->dv = supported_dv(d);
+    c->smem_dense = plan_layout(c, false, c->ip_dense);
+    c->smem_mti = plan_layout(c, true, c->ip_mti);
+    int bd = 0, bm = 0;
+    KCU(dense_attr(c->dv, c->smem_dense, &bd));
+    KCU(mti_attr(c->dv, c->smem_mti, &bm));
+    if (bd < 1 || bm < 1) { c->err = "knor_create: kernel does not fit on an SM"; return bail(KNOR_ERR_CUDA); }
+    c->grid_dense = bd * c->num_sms;
+    c->grid_mti = bm * c->num_sms;
+    // Both scans use the same accumulation mode: per-CTA partial slots, or,
+    // when k x d sums do not fit in shared memory, one slot updated by FP64
+    // atomics.
+    const int acc_global = (c->ip_dense.acc_global || c->ip_mti.acc_global) ? 1 : 0;
+    c->part_stride = acc_global ? 1 : std::max(c->grid_dense, c->grid_mti);
+    KC(dalloc(c, &c->part_S, kd * c->part_stride));
+    KC(dalloc(c, &c->part_cnt, (size_t)k * c->part_stride));
+    fill_common(c, c->ip_dense);
+    fill_common(c, c->ip_mti);
+    c->ip_dense.part_stride = c->part_stride;
+    c->ip_mti.part_stride = c->part_stride;
+    c->ip_dense.acc_global = c->ip_mti.acc_global = acc_global;
+    FinParams &f = c->fp;
+    f.part_S = c->part_S; f.part_cnt = c->part_cnt; f.part_stride = c->part_stride;
+    f.k = k; f.d = d;
+    f.S = c->S; f.cnt = c->cnt; f.cnt_next = c->cnt_next; f.C64 = c->C64; f.C32 = c->C32; f.C32n = c->C32n;
+    f.halfD = c->halfD; f.s = c->s; f.F = c->F; f.cnt_out = c->cnt; f.ctr = c->ctr; f.stats = c->stats;
+    f.run_iter = c->flags + F_RUN_ITER; f.total_iter = c->flags + F_TOTAL_ITER;
+    f.max_iters_dev = c->flags + F_MAX_ITERS;
+
+    // C^0
+    if (init == KNOR_INIT_FORGY) {
+        c->init_idx = forgy_indices(n, k, seed);
+        KC(dalloc(c, &c->d_idx, (size_t)k));
+        KCU(cudaMemcpyAsync(c->d_idx, c->init_idx.data(), sizeof(int64_t) * k, cudaMemcpyHostToDevice, c->stream));
+        KCU(launch_gather_rows(c->X, d, c->d_idx, k, c->C0, c->stream));
+        c->c0_set = true;
+    } else {
+        KCU(cudaMemsetAsync(c->C0, 0, kd * sizeof(double), c->stream));
+    }
+    KC(reset_run(c));
+    KC(build_graphs(c));
+    *out = c;
+    return KNOR_OK;
+#undef KC
+#undef KCU
+}
+
+knor_status knor_set_init_centroids(knor_ctx *c, const double *c_kxd) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (!c_kxd) return fail(c, KNOR_ERR_ARG, "knor_set_init_centroids: NULL centroids");
+    const size_t kd = (size_t)c->k * c->d;
+    std::vector<double> h(kd);
+    if (is_device_ptr(c_kxd)) KNOR_CUDA(c, cudaMemcpy(h.data(), c_kxd, kd * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memcpy(h.data(), c_kxd, kd * sizeof(double));
+    for (double v : h)
+        if (!std::isfinite(v) || std::fabs(v) > 1e15)
+            return fail(c, KNOR_ERR_ARG, "knor_set_init_centroids: coordinate not finite or above 1e15");
+    KNOR_CUDA(c, cudaMemcpyAsync(c->C0, h.data(), kd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->c0_set = true;
+    return reset_run(c);
+}
+
+knor_status knor_reset(knor_ctx *c) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    return reset_run(c);
+}
+
+static knor_status read_stats(knor_ctx *c, int count, knor_iter_stats *out) {
+    if (count <= 0 || !out) return KNOR_OK;
+    KNOR_CUDA(c, cudaMemcpyAsync(c->h_stats, c->stats, sizeof(IterStats) * count, cudaMemcpyDeviceToHost, c->stream));
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    static_assert(sizeof(IterStats) == sizeof(knor_iter_stats), "stats layout");
+    std::memcpy(out, c->h_stats, sizeof(IterStats) * count);
+    return KNOR_OK;
+}
+
+knor_status knor_iterate(knor_ctx *c, knor_iter_stats *out) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (!c->c0_set) return fail(c, KNOR_ERR_STATE, "knor_iterate: explicit init centroids not set");
+    KNOR_CUDA(c, cudaMemsetAsync(c->flags + F_RUN_ITER, 0, sizeof(int32_t), c->stream));
+    if (c->profiling) {
+        knor_status st = profiled_iteration(c);
+        if (st != KNOR_OK) return st;
+    } else {
+        KNOR_CUDA(c, cudaGraphLaunch(c->iter_exec, c->stream));
+        KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->host_total_iter += 1;
+    }
+    return read_stats(c, 1, out);
+}
+
+knor_status knor_run(knor_ctx *c, int32_t max_iters, int32_t *iters_done, knor_iter_stats *per_iter) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (iters_done) *iters_done = 0;
+    if (max_iters < 0 || max_iters > kStatsCap)
+        return fail(c, KNOR_ERR_ARG, "knor_run: max_iters must be in [0, 65536]");
+    if (!c->c0_set) return fail(c, KNOR_ERR_STATE, "knor_run: explicit init centroids not set");
+    if (max_iters == 0) return KNOR_OK;
+    int32_t hv[3] = {0, 0, max_iters};
+    KNOR_CUDA(c, cudaMemsetAsync(c->flags + F_RUN_ITER, 0, sizeof(int32_t), c->stream));
+    if (c->profiling) {
+        int32_t done = 0;
+        for (int t = 0; t < max_iters; ++t) {
+            knor_status st = profiled_iteration(c);
+            if (st != KNOR_OK) return st;
+            done = t + 1;
+            IterStats r;
+            KNOR_CUDA(c, cudaMemcpy(&r, c->stats + t, sizeof(r), cudaMemcpyDeviceToHost));
+            if (r.changed == 0) break;
+        }
+        if (iters_done) *iters_done = done;
+        return read_stats(c, done, per_iter);
+    }
+    KNOR_CUDA(c, cudaMemcpyAsync(c->flags + F_MAX_ITERS, &hv[2], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    KNOR_CUDA(c, cudaGraphLaunch(c->run_exec, c->stream));
+    int32_t done = 0;
+    KNOR_CUDA(c, cudaMemcpyAsync(&done, c->flags + F_RUN_ITER, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->host_total_iter += done;
+    if (iters_done) *iters_done = done;
+    return read_stats(c, done, per_iter);
+}
+
+knor_status knor_set_profiling(knor_ctx *c, int32_t on) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    c->profiling = on != 0;
+    return KNOR_OK;
+}
+
+knor_status knor_get_profile(knor_ctx *c, knor_profile *out, int32_t reset_after) {
+    if (!c || !out) return KNOR_ERR_ARG;
+    c->err.clear();
+    *out = c->prof;
+    if (reset_after) c->prof = knor_profile{};
+    return KNOR_OK;
+}
+
+knor_status knor_get_assignments(const knor_ctx *cc, int32_t *out_n) {
+    knor_ctx *c = const_cast<knor_ctx *>(cc);
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (!out_n) return fail(c, KNOR_ERR_ARG, "knor_get_assignments: NULL output");
+    if (is_device_ptr(out_n)) {
+        KNOR_CUDA(c, launch_extract_assign(c->st, c->n, out_n, c->stream));
+        KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+        return KNOR_OK;
+    }
+    int32_t *tmp = nullptr;
+    knor_status s = dalloc(c, &tmp, (size_t)c->n);
+    if (s != KNOR_OK) return s;
+    cudaError_t e = launch_extract_assign(c->st, c->n, tmp, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_n, tmp, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    KNOR_CUDA(c, e);
+    return KNOR_OK;
+}
+
+static knor_status copy_out(knor_ctx *c, void *dst, const void *src, size_t bytes) {
+    KNOR_CUDA(c, cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KNOR_OK;
+}
+
+knor_status knor_get_centroids(const knor_ctx *cc, double *out) {
+    knor_ctx *c = const_cast<knor_ctx *>(cc);
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (!out) return fail(c, KNOR_ERR_ARG, "knor_get_centroids: NULL output");
+    return copy_out(c, out, c->C64, sizeof(double) * (size_t)c->k * c->d);
+}
+
+knor_status knor_get_centroids_f32(const knor_ctx *cc, float *out) {
+    knor_ctx *c = const_cast<knor_ctx *>(cc);
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (!out) return fail(c, KNOR_ERR_ARG, "knor_get_centroids_f32: NULL output");
+    return copy_out(c, out, c->C32, sizeof(float) * (size_t)c->k * c->d);
+}
+
+knor_status knor_get_init_indices(const knor_ctx *c, int64_t *out_k) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (!out_k) return fail(c, KNOR_ERR_ARG, "knor_get_init_indices: NULL output");
+    if (c->init != KNOR_INIT_FORGY) return fail(c, KNOR_ERR_STATE, "knor_get_init_indices: context uses explicit init");
+    std::memcpy(out_k, c->init_idx.data(), sizeof(int64_t) * c->k);
+    return KNOR_OK;
+}
+
+knor_status knor_get_iteration(const knor_ctx *cc, int32_t *out) {
+    knor_ctx *c = const_cast<knor_ctx *>(cc);
+    if (!c || !out) return KNOR_ERR_ARG;
+    c->err.clear();
+    KNOR_CUDA(c, cudaMemcpyAsync(out, c->flags + F_TOTAL_ITER, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KNOR_OK;
+}
+
+// State image: header | C0 | C64 | S | cnt | C32 | F | halfD | s | st
+static size_t state_size(const knor_ctx *c) {
+    const size_t kd = (size_t)c->k * c->d, k = (size_t)c->k;
+    return sizeof(StateHeader) + 3 * kd * sizeof(double) + k * sizeof(long long) + kd * sizeof(float) +
+           k * sizeof(float) + k * k * sizeof(float) + k * sizeof(float) + (size_t)c->n * sizeof(PtState);
+}
+
+knor_status knor_get_state(const knor_ctx *cc, void *buf, size_t *size) {
+    knor_ctx *c = const_cast<knor_ctx *>(cc);
+    if (!c || !size) return KNOR_ERR_ARG;
+    c->err.clear();
+    const size_t need = state_size(c);
+    if (!buf) { *size = need; return KNOR_OK; }
+    if (*size < need) return fail(c, KNOR_ERR_ARG, "knor_get_state: buffer too small");
+    int32_t fl[F_COUNT];
+    KNOR_CUDA(c, cudaMemcpy(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost));
+    StateHeader h{kStateMagic, kStateVersion, c->n, c->d, c->k, c->opts.no_prune, c->opts.precision,
+                  c->opts.full_recompute_every, fl[F_TOTAL_ITER], fl[F_MODE_DENSE], 0};
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t kd = (size_t)c->k * c->d, k = (size_t)c->k;
+    struct Part { const void *src; size_t bytes; } parts[] = {
+        {c->C0, kd * 8}, {c->C64, kd * 8}, {c->S, kd * 8}, {c->cnt, k * 8}, {c->C32, kd * 4}, {c->F, k * 4},
+        {c->halfD, k * k * 4}, {c->s, k * 4}, {c->st, (size_t)c->n * sizeof(PtState)}};
+    for (auto &pt : parts) {
+        KNOR_CUDA(c, cudaMemcpyAsync(p, pt.src, pt.bytes, cudaMemcpyDeviceToHost, c->stream));
+        p += pt.bytes;
+    }
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    *size = need;
+    return KNOR_OK;
+}
+
+knor_status knor_set_state(knor_ctx *c, const void *buf, size_t size) {
+    if (!c || !buf) return KNOR_ERR_ARG;
+    c->err.clear();
+    if (size != state_size(c)) return fail(c, KNOR_ERR_ARG, "knor_set_state: size does not match this context");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic || h.version != kStateVersion || h.n != c->n || h.d != c->d || h.k != c->k ||
+        h.no_prune != c->opts.no_prune || h.precision != c->opts.precision ||
+        h.recompute != c->opts.full_recompute_every)
+        return fail(c, KNOR_ERR_ARG, "knor_set_state: state is from a context with other sizes or options");
+    const char *p = static_cast<const char *>(buf) + sizeof(h);
+    const size_t kd = (size_t)c->k * c->d, k = (size_t)c->k;
+    struct Part { void *dst; size_t bytes; } parts[] = {
+        {c->C0, kd * 8}, {c->C64, kd * 8}, {c->S, kd * 8}, {c->cnt, k * 8}, {c->C32, kd * 4}, {c->F, k * 4},
+        {c->halfD, k * k * 4}, {c->s, k * 4}, {c->st, (size_t)c->n * sizeof(PtState)}};
+    for (auto &pt : parts) {
+        KNOR_CUDA(c, cudaMemcpyAsync(pt.dst, p, pt.bytes, cudaMemcpyHostToDevice, c->stream));
+        p += pt.bytes;
+    }
+    int32_t fl[F_COUNT] = {0, h.total_iter, 1, h.mode_dense, 1, 1};
+    c->host_total_iter = h.total_iter;
+    KNOR_CUDA(c, cudaMemcpyAsync(c->flags, fl, sizeof(fl), cudaMemcpyHostToDevice, c->stream));
+    KNOR_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream));
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->c0_set = true;
+    return KNOR_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,126 @@
+// knor_internal.cuh -- types and launch parameters shared by the kernels and
+// the host runtime of libknor.so.  Not part of the public ABI (include/knor.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace knor {
+
+// Threads per CTA of the point kernels, and points per row tile.
+constexpr int NT = 256;
+// Points tested per thread and step by the MTI bound test (phase A).
+constexpr int PA = 8;
+// Capacity of the MTI active-point ring queue (leftover < NT plus one chunk).
+constexpr int QCAP = NT * PA + NT;
+
+// Per-point MTI state, packed so that the bound test reads 8 bytes per point.
+//   a   assignment (-1 before the first iteration)
+//   ub  u - F[a] rounded up, where u >= d(x, c_a) was exact-plus-rounding when
+//       stored and F[a] is the cluster's cumulative drift at that time.  The
+//       current bound is u^t = ub + F^t[a] (rounded up): the paper's running
+//       update u^t = u^{t-1} + f(c_a) without rewriting ub every iteration.
+struct __align__(8) PtState {
+    float ub;
+    int32_t a;
+};
+
+// Device counters of the iteration in flight (zeroed when snapshotted).
+struct Counters {
+    unsigned long long changed;
+    unsigned long long skipped;
+    unsigned long long evals;
+    unsigned long long rechecked;
+    unsigned long long empty;
+    unsigned long long violations;
+};
+
+// One record per completed iteration; layout identical to knor_iter_stats.
+struct IterStats {
+    long long changed;
+    long long clause1_skipped;
+    long long dist_evals;
+    long long rechecked;
+    int32_t empty;
+    int32_t iteration;
+    long long violations;
+};
+
+// Parameters of the point kernels (dense scan and MTI scan).
+struct IterParams {
+    const float *X;        // n x d points
+    int64_t n;
+    int32_t d, k;
+    PtState *st;           // n
+    const float *C32;      // k x d current centroids (FP32 scan copy)
+    const float *halfD;    // k x k, lower bounds on 1/2 d(c_a, c)
+    const float *s;        // k, lower bounds on 1/2 min_{c != a} d(c_a, c)
+    const float *F;        // k, cumulative drift (upper bound)
+    double *part_S;        // [k*d][part_stride] per-CTA FP64 partial sums
+    long long *part_cnt;   // [k][part_stride]  per-CTA member-count partials
+    int32_t part_stride;   // = number of partial slots (grid size, or 1)
+    Counters *ctr;
+    float onepk;           // 1 + kappa, rounded up: pruning slack
+    float tau;             // absolute pruning floor
+    float g_up;            // >= 1 / (1 - (d+2) 2^-24): FP32 distance error bound
+    float tiny;            // >= d * 2^-149: underflow allowance
+    int32_t acc_global;    // 1: cluster sums go straight to part_S slot 0 by FP64 atomics
+    int32_t cent_smem;     // 1: centroids staged in shared memory
+    int32_t halfD_smem;    // 1: k x k table staged in shared memory
+    int32_t mti;           // dense kernel: also write the MTI bound
+    // shared-memory layout (byte offsets; off_s / off_F are -1 when the
+    // per-cluster arrays are read from global memory instead)
+    int32_t off_acc_hi, off_acc_lo, off_cnt, off_cent, off_halfD, off_s, off_F;
+    int32_t off_tb, off_ta, off_ti, off_tile, off_queue, off_misc;
+    int32_t dpad;          // floats per staged row (d + 4)
+    int32_t stages;        // row tiles in flight (dense kernel)
+};
+
+// Parameters of the reduction / finalize kernels.
+struct FinParams {
+    const double *part_S;
+    const long long *part_cnt;
+    int32_t part_stride;
+    int32_t k, d;
+    double *S;              // k x d running sums
+    const long long *cnt;   // k member counts before this iteration
+    long long *cnt_next;    // k member counts after
+    double *C64;            // k x d master centroids
+    float *C32;             // k x d scan copy (current; replaced by K1)
+    float *C32n;            // k x d scan copy (next)
+    float *halfD, *s, *F;
+    long long *cnt_out;     // where K1 commits cnt_next
+    Counters *ctr;
+    IterStats *stats;       // per-run records
+    int32_t *run_iter;      // iterations done in this run
+    int32_t *total_iter;    // iterations since reset
+    const int32_t *max_iters_dev; // run limit (for the device-side loop)
+    int32_t snapshot;       // 1: record stats (0 for the table at reset)
+    unsigned long long cond_handle; // cudaGraphConditionalHandle, 0 if none
+};
+
+// Launchers implemented in kernels.cu.
+// mode_dense selects which scan runs (the other returns at once); the scan
+// that runs records how many partial slots it wrote and whether the sums are
+// fresh (dense) or deltas (MTI).
+cudaError_t launch_dense(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                         const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
+cudaError_t launch_mti(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                       const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
+cudaError_t dense_attr(int dv, size_t smem, int *blocks_per_sm);
+cudaError_t mti_attr(int dv, size_t smem, int *blocks_per_sm);
+cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32_t *fresh, cudaStream_t s);
+cudaError_t launch_table(const FinParams &f, int32_t *mode_dense, int need_table, int recompute_every,
+                         int always_dense, cudaStream_t s);
+cudaError_t launch_validate(const float *X, int64_t count, unsigned long long *bad, cudaStream_t s);
+cudaError_t launch_init_state(PtState *st, int64_t n, cudaStream_t s);
+cudaError_t launch_gather_rows(const float *X, int32_t d, const int64_t *idx, int32_t k, double *C64,
+                               cudaStream_t s);
+cudaError_t launch_round_c32(const double *C64, float *C32, int64_t kd, cudaStream_t s);
+cudaError_t launch_extract_assign(const PtState *st, int64_t n, int32_t *out, cudaStream_t s);
+cudaError_t launch_check_bounds(const float *X, int64_t n, int32_t d, const PtState *st,
+                                const float *C32, const float *F, IterStats *stats,
+                                const int32_t *run_iter, cudaStream_t s);
+int supported_dv(int d); // template width used for d (0 = generic)
+
+} // namespace knor

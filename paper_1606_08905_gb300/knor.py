@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libknor.so (include/knor.h).
+
+Argument marshalling only: every step of Lloyd's iteration runs in the CUDA
+kernels of libknor.so.  Tensors may live on the GPU (their device pointer is
+passed through) or on the host.  There is no fallback: if libknor.so has not
+been built, or cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libknor.so")
+_lib = None
+
+KNOR_OK, KNOR_ERR_ARG, KNOR_ERR_OOM, KNOR_ERR_CUDA, KNOR_ERR_TIMEOUT, KNOR_ERR_STATE = 0, -1, -2, -3, -4, -5
+KNOR_INIT_FORGY, KNOR_INIT_EXPLICIT = 0, 1
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+
+class KnorError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"knor status {status}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("no_prune", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("full_recompute_every", ctypes.c_int32), ("debug_invariants", ctypes.c_int32)]
+
+
+class IterStats(ctypes.Structure):
+    _fields_ = [("changed", ctypes.c_int64), ("clause1_skipped", ctypes.c_int64),
+                ("dist_evals", ctypes.c_int64), ("rechecked", ctypes.c_int64),
+                ("empty", ctypes.c_int32), ("iteration", ctypes.c_int32),
+                ("violations", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4)]
+
+
+KERNELS = ("dense", "mti", "reduce", "table")
+
+_SIGS = {
+    "knor_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Opts),
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "knor_set_init_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "knor_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(IterStats)]),
+    "knor_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(IterStats)]),
+    "knor_get_assignments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_get_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_get_centroids_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_get_init_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_get_iteration": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "knor_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "knor_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "knor_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "knor_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "knor_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int32]),
+    "knor_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "knor_destroy": (None, [ctypes.c_void_p]),
+    "knor_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str | None = None):
+    """Loads libknor.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is not built; run paper_1606_08905_gb300.build.build() "
+                           "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, ctx=None):
+    if st != KNOR_OK:
+        msg = load().knor_last_error(ctx)
+        raise KnorError(st, msg.decode() if msg else "")
+
+
+def _ptr(obj, dtype):
+    """(pointer, keepalive) for a torch tensor or numpy array of `dtype`."""
+    try:
+        import torch
+        if isinstance(obj, torch.Tensor):
+            want = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                    np.int64: torch.int64}[dtype]
+            if obj.dtype != want:
+                raise TypeError(f"expected {want}, got {obj.dtype}")
+            if not obj.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return obj.data_ptr(), obj
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(obj, dtype=dtype)
+    return arr.ctypes.data, arr
+
+
+class Context:
+    """One k-means problem on the GPU (a knor_ctx)."""
+
+    def __init__(self, points, k: int, init: str = "forgy", seed: int = 0, prune: bool = True,
+                 precision: str = "fp32", full_recompute_every: int = 0,
+                 debug_invariants: bool = False):
+        lib = load()
+        shape = tuple(points.shape)
+        if len(shape) != 2:
+            raise ValueError("points must be n x d")
+        self.n, self.d = int(shape[0]), int(shape[1])
+        self.k = int(k)
+        ptr, keep = _ptr(points, np.float32)
+        opts = Opts(0 if prune else 1, PRECISIONS[precision], int(full_recompute_every),
+                    1 if debug_invariants else 0)
+        out = ctypes.c_void_p()
+        st = lib.knor_create(ptr, self.n, self.d, self.k,
+                             KNOR_INIT_FORGY if init == "forgy" else KNOR_INIT_EXPLICIT,
+                             int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opts), ctypes.byref(out))
+        del keep
+        _check(st, None)
+        self._ctx = out.value
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().knor_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- iteration
+    def set_init_centroids(self, C):
+        ptr, keep = _ptr(C, np.float64)
+        _check(load().knor_set_init_centroids(self._ctx, ptr), self._ctx)
+
+    def reset(self):
+        _check(load().knor_reset(self._ctx), self._ctx)
+
+    def iterate(self) -> dict:
+        s = IterStats()
+        _check(load().knor_iterate(self._ctx, ctypes.byref(s)), self._ctx)
+        return s.as_dict()
+
+    def run(self, max_iters: int):
+        recs = (IterStats * max(1, max_iters))()
+        done = ctypes.c_int32(0)
+        _check(load().knor_run(self._ctx, int(max_iters), ctypes.byref(done), recs), self._ctx)
+        return int(done.value), [recs[i].as_dict() for i in range(done.value)]
+
+    # -- results
+    def assignments(self, out=None):
+        """int32[n]; `out` may be a device tensor (filled in place)."""
+        if out is None:
+            out = np.empty(self.n, np.int32)
+        ptr, _ = _ptr(out, np.int32)
+        _check(load().knor_get_assignments(self._ctx, ptr), self._ctx)
+        return out
+
+    def centroids(self, out=None):
+        if out is None:
+            out = np.empty((self.k, self.d), np.float64)
+        ptr, _ = _ptr(out, np.float64)
+        _check(load().knor_get_centroids(self._ctx, ptr), self._ctx)
+        return out
+
+    def centroids_f32(self, out=None):
+        if out is None:
+            out = np.empty((self.k, self.d), np.float32)
+        ptr, _ = _ptr(out, np.float32)
+        _check(load().knor_get_centroids_f32(self._ctx, ptr), self._ctx)
+        return out
+
+    def init_indices(self):
+        out = np.empty(self.k, np.int64)
+        _check(load().knor_get_init_indices(self._ctx, out.ctypes.data), self._ctx)
+        return out
+
+    def iteration(self) -> int:
+        v = ctypes.c_int32(0)
+        _check(load().knor_get_iteration(self._ctx, ctypes.byref(v)), self._ctx)
+        return int(v.value)
+
+    def set_profiling(self, on: bool):
+        _check(load().knor_set_profiling(self._ctx, 1 if on else 0), self._ctx)
+
+    def profile(self, reset: bool = False) -> dict:
+        """{kernel: (launches, summed CUDA-event ms)} since the last reset."""
+        pr = Profile()
+        _check(load().knor_get_profile(self._ctx, ctypes.byref(pr), 1 if reset else 0), self._ctx)
+        return {name: (int(pr.launches[i]), float(pr.ms[i])) for i, name in enumerate(KERNELS)}
+
+    @property
+    def stream(self) -> int:
+        return int(load().knor_stream(self._ctx) or 0)
+
+    # -- checkpoint
+    def get_state(self) -> bytes:
+        size = ctypes.c_size_t(0)
+        _check(load().knor_get_state(self._ctx, None, ctypes.byref(size)), self._ctx)
+        buf = ctypes.create_string_buffer(size.value)
+        _check(load().knor_get_state(self._ctx, buf, ctypes.byref(size)), self._ctx)
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(load().knor_set_state(self._ctx, buf, len(blob)), self._ctx)
+
+
+def version() -> str:
+    return load().knor_version().decode()

@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Every test runs the library on seeded synthetic inputs and compares, at every
+iteration, (1) its assignments with the oracle's assignment from the same
+centroids (teacher forcing, near-tie rule), (2) its assignments with the
+oracle's FP32 restatement of the argmin on the very FP32 centroids the scan
+used (bit-exact), and (3) its new centroids with the oracle's means of its
+assignments.  Free-running trajectories are compared too where no near-tie
+flip occurred.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1606_08905_gb300 import build as kbuild
+from paper_1606_08905_gb300 import knor, synth
+from parity import check_assignments, check_centroids
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    knor.load()
+
+
+def _dev(X):
+    return torch.as_tensor(X).to("cuda").contiguous()
+
+
+def step_and_check(X, ctx, iters, label, check_f32=True):
+    """Runs up to `iters` single iterations, checking each one.  Returns the
+    per-iteration stats and the total of exempt near-tie mismatches."""
+    ties = 0
+    stats = []
+    for t in range(iters):
+        C_before = ctx.centroids()
+        C32_before = ctx.centroids_f32()
+        s = ctx.iterate()
+        stats.append(s)
+        a = ctx.assignments()
+        ties += check_assignments(X, C_before, a, f"{label} it {t + 1}")
+        if check_f32:
+            a32 = oracle.assign_f32(X, C32_before)
+            assert np.array_equal(a, a32), f"{label} it {t + 1}: FP32 argmin differs at {np.flatnonzero(a != a32)[:5]}"
+        C_ref, cnt = oracle.means(X, a, C_before)
+        check_centroids(ctx.centroids(), C_ref, f"{label} it {t + 1}")
+        assert s["empty"] == int((cnt == 0).sum())
+        if s["changed"] == 0:
+            break
+    return stats, ties
+
+
+def _datasets():
+    return [
+        ("iso_d8", lambda: synth.isotropic_mixture(6000, 8, 10, 11).numpy(), 10),
+        ("spd_d32", lambda: synth.spd_mixture(9000, 32, 20, 12).numpy(), 20),
+        ("spd_d16_k37", lambda: synth.spd_mixture(7777, 16, 37, 13).numpy(), 37),
+        ("uniform_d4", lambda: synth.uniform_cube(5000, 4, 14).numpy(), 25),
+        ("aniso_d64", lambda: synth.aniso_mixture(4000, 64, 30, 15).numpy(), 30),
+        ("aniso_d128", lambda: synth.aniso_mixture(3000, 128, 17, 16).numpy(), 17),
+        ("generic_d3", lambda: synth.spd_mixture(5000, 3, 9, 17).numpy(), 9),
+        ("generic_d33", lambda: synth.aniso_mixture(3000, 33, 12, 18).numpy(), 12),
+        ("generic_d1", lambda: synth.uniform_cube(3000, 1, 19).numpy(), 6),
+    ]
+
+
+@pytest.mark.parametrize("prune", [True, False], ids=["mti", "plain"])
+@pytest.mark.parametrize("name,make,k", _datasets(), ids=[d[0] for d in _datasets()])
+def test_iterations_match_oracle(name, make, k, prune):
+    X = make()
+    with knor.Context(_dev(X), k, seed=42, prune=prune) as ctx:
+        idx = ctx.init_indices()
+        assert np.array_equal(idx, oracle.forgy_indices(X.shape[0], k, 42))
+        assert np.array_equal(ctx.centroids(), X[idx].astype(np.float64))
+        stats, ties = step_and_check(X, ctx, 40, name)
+    assert stats[0]["changed"] == X.shape[0] and stats[0]["iteration"] == 1
+    # free-running oracle trajectory from the same C^0
+    ref = oracle.run(X, X[idx].astype(np.float64), 40, prune=False)
+    if ties == 0:
+        assert [s["changed"] for s in stats] == list(ref.changed[:len(stats)])
+
+
+@pytest.mark.parametrize("name,make,k", _datasets()[:6], ids=[d[0] for d in _datasets()[:6]])
+def test_mti_assigns_exactly_like_plain(name, make, k):
+    """Pruning is conservative: at every iteration the MTI scan returns the
+    same assignments as the full scan, and the same centroids."""
+    X = _dev(make())
+    with knor.Context(X, k, seed=7, prune=True) as p, knor.Context(X, k, seed=7, prune=False) as q:
+        for t in range(40):
+            sp, sq = p.iterate(), q.iterate()
+            assert sp["changed"] == sq["changed"], f"it {t + 1}"
+            assert np.array_equal(p.assignments(), q.assignments()), f"it {t + 1}"
+            assert np.array_equal(p.centroids_f32(), q.centroids_f32()), f"it {t + 1}"
+            assert sq["dist_evals"] == X.shape[0] * k
+            if t > 0:
+                assert sp["clause1_skipped"] + 0 <= X.shape[0]
+            if sp["changed"] == 0:
+                break
+
+
+def test_plain_workload_full_trajectory():
+    """The 100k x 8, k = 10 plain-Lloyd workload, Forgy seed 42, 20
+    iterations: the whole trajectory against the oracle's."""
+    X = synth.make("isotropic", 100_000, 8, 10, 1001).numpy()
+    ref = oracle.run(X, oracle.forgy_centroids(X, 10, 42), 20, prune=False, history=True)
+    with knor.Context(_dev(X), 10, seed=42, prune=False) as ctx:
+        done, recs = ctx.run(20)
+        assert done == ref.iters
+        assert [r["changed"] for r in recs] == list(ref.changed)
+        assert np.array_equal(ctx.assignments(), ref.a)
+        check_centroids(ctx.centroids(), ref.C, "final")
+
+
+@pytest.mark.parametrize("prune", [True, False], ids=["mti", "plain"])
+def test_run_equals_iterate(prune):
+    """The device-side loop (one graph launch) equals single iterations."""
+    X = _dev(synth.spd_mixture(20000, 16, 12, 21))
+    with knor.Context(X, 12, seed=3, prune=prune) as a, knor.Context(X, 12, seed=3, prune=prune) as b:
+        done, recs = a.run(30)
+        singles = []
+        for _ in range(30):
+            singles.append(b.iterate())
+            if singles[-1]["changed"] == 0:
+                break
+        assert done == len(singles)
+        assert recs == singles
+        assert np.array_equal(a.centroids(), b.centroids())
+        assert np.array_equal(a.assignments(), b.assignments())
+        # a second run continues from where the first stopped
+        done2, recs2 = a.run(5)
+        assert done2 == 1 and recs2[0]["changed"] == 0 and recs2[0]["iteration"] == done + 1
+
+
+def test_deterministic_rerun():
+    X = _dev(synth.spd_mixture(50000, 32, 20, 22))
+    out = []
+    for _ in range(2):
+        with knor.Context(X, 20, seed=5) as c:
+            c.run(15)
+            out.append((c.centroids(), c.assignments()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_checkpoint_resume_is_bit_identical():
+    X = _dev(synth.spd_mixture(30000, 16, 15, 23))
+    with knor.Context(X, 15, seed=9) as a:
+        a.run(4)
+        blob = a.get_state()
+        _, tail_a = a.run(6)
+        Ca, aa = a.centroids(), a.assignments()
+    with knor.Context(X, 15, seed=1234) as b:
+        b.set_state(blob)
+        assert b.iteration() == 4
+        _, tail_b = b.run(6)
+        assert tail_a == tail_b
+        assert np.array_equal(b.centroids(), Ca)
+        assert np.array_equal(b.assignments(), aa)
+
+
+def test_debug_invariants_hold():
+    X = _dev(synth.spd_mixture(40000, 8, 16, 24))
+    with knor.Context(X, 16, seed=2, debug_invariants=True) as c:
+        done, recs = c.run(40)
+    assert all(r["violations"] == 0 for r in recs)
+    assert sum(r["clause1_skipped"] for r in recs) > 0
+
+
+@pytest.mark.parametrize("n,d,k", [(1, 1, 1), (1, 5, 1), (2, 3, 2), (257, 8, 257), (300, 32, 1),
+                                   (2049, 16, 5), (4097, 7, 3), (10000, 2, 64)])
+def test_edge_sizes(n, d, k):
+    rng = np.random.default_rng(n * 31 + d)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    for prune in (True, False):
+        with knor.Context(_dev(X), k, seed=1, prune=prune) as c:
+            step_and_check(X, c, 12, f"n{n} d{d} k{k}")
+
+
+def test_duplicates_ties_and_empty_clusters():
+    rng = np.random.default_rng(5)
+    base = rng.integers(-3, 4, (30, 2)).astype(np.float32)
+    X = base[rng.integers(0, 30, 5000)]
+    C0 = np.concatenate([X[:6].astype(np.float64), np.array([[500.0, 500.0], [0.5, 0.5]])])
+    C0[3] = C0[1]  # duplicated centroid: index 1 must win every tie
+    for prune in (True, False):
+        with knor.Context(_dev(X), 8, init="explicit", prune=prune) as c:
+            c.set_init_centroids(C0)
+            stats, _ = step_and_check(X, c, 20, f"dups prune={prune}")
+            assert stats[0]["empty"] >= 2  # the far centroid and the duplicate
+            assert np.array_equal(c.centroids()[6], [500.0, 500.0])
+
+
+def test_host_and_device_inputs_agree():
+    X = synth.spd_mixture(20000, 32, 8, 25)
+    with knor.Context(X.numpy(), 8, seed=4) as h, knor.Context(_dev(X), 8, seed=4) as g:
+        h.run(10)
+        g.run(10)
+        assert np.array_equal(h.centroids(), g.centroids())
+        out = torch.empty(20000, dtype=torch.int32, device="cuda")
+        g.assignments(out)
+        assert np.array_equal(out.cpu().numpy(), h.assignments())
+
+
+def test_bad_inputs_are_rejected():
+    X = np.zeros((100, 4), np.float32)
+    X[7, 2] = np.nan
+    with pytest.raises(knor.KnorError) as e:
+        knor.Context(_dev(X), 3)
+    assert e.value.status == knor.KNOR_ERR_ARG
+    X[7, 2] = 1e30
+    with pytest.raises(knor.KnorError):
+        knor.Context(_dev(X), 3)
+    with knor.Context(_dev(np.ones((10, 4), np.float32)), 2, init="explicit") as c:
+        with pytest.raises(knor.KnorError) as e:
+            c.iterate()
+        assert e.value.status == knor.KNOR_ERR_STATE
+
+
+def test_mti_workload_full_size_sampled():
+    """The 66M x 32, k = 20 MTI workload at full size, in the configuration
+    the benchmark times: teacher-forced parity on a 20k-point sample at
+    iterations 1, 2, 5 and the last, and the means of the GPU's assignments
+    over all points (the oracle on the host) at the last iteration."""
+    n, d, k = 66_000_000, 32, 20
+    X = synth.make("spd", n, d, k, 1002, device="cuda")
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(n, 20000, replace=False))
+    Xs = X[torch.as_tensor(sample, device="cuda")].cpu().numpy()
+    with knor.Context(X, k, seed=synth.INIT_SEED) as c:
+        check_at = {1, 2, 5}
+        last = None
+        for t in range(1, 51):
+            C_before = c.centroids()
+            s = c.iterate()
+            if t in check_at or s["changed"] == 0 or t == 50:
+                a = torch.empty(n, dtype=torch.int32, device="cuda")
+                c.assignments(a)
+                check_assignments(Xs, C_before, a[torch.as_tensor(sample, device="cuda")].cpu().numpy(),
+                                  f"66M it {t}")
+                last = (t, C_before, a)
+            if s["changed"] == 0:
+                break
+        t, C_before, a = last
+        C_ref, _ = oracle.means(X.cpu().numpy(), a.cpu().numpy(), C_before)
+        check_centroids(c.centroids(), C_ref, f"66M it {t}")
