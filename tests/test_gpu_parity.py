@@ -133,7 +133,13 @@ def test_run_equals_iterate(prune):
         assert np.array_equal(a.assignments(), b.assignments())
         # a second run continues from where the first stopped
         done2, recs2 = a.run(5)
-        assert done2 == 1 and recs2[0]["changed"] == 0 and recs2[0]["iteration"] == done + 1
+        assert recs2[0]["iteration"] == done + 1
+        if recs[-1]["changed"] == 0:
+            assert done2 == 1 and recs2[0]["changed"] == 0
+        more = []
+        for _ in range(done2):
+            more.append(b.iterate())
+        assert recs2 == more
 
 
 def test_deterministic_rerun():
