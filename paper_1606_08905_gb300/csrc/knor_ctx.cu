@@ -210,6 +210,48 @@ static size_t plan_layout(const knor_ctx *c, bool mti, IterParams &p) {
     return off;
 }
 
+// Shared-memory layout of a warp-autonomous kernel (CTA tables, then WPC
+// private warp regions); returns 0 when the variant does not apply.
+static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
+    const int d = c->d, k = c->k, dv = c->dv;
+    if (dv == 0) return 0;
+    const size_t kd = (size_t)k * d;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> int32_t {
+        const size_t o = off;
+        off = (off + bytes + 15) & ~(size_t)15;
+        return (int32_t)o;
+    };
+    p.dpad = d + 4;
+    p.cent_smem = kd * 4 <= 32 * 1024 ? 1 : 0;
+    p.off_cent = take(p.cent_smem ? kd * 4 : 0);
+    p.halfD_smem = (mti && (size_t)k * k * 4 <= 16 * 1024) ? 1 : 0;
+    p.off_halfD = take(p.halfD_smem ? (size_t)k * k * 4 : 0);
+    const bool sf = (size_t)k * 8 <= 8 * 1024;
+    p.off_s = sf ? take((size_t)k * 4) : -1;
+    p.off_F = sf ? take((size_t)k * 4) : -1;
+    p.w_base = take(0);
+    size_t woff = 0;
+    auto wtake = [&](size_t bytes) -> int32_t {
+        const size_t o = woff;
+        woff = (woff + bytes + 15) & ~(size_t)15;
+        return (int32_t)o;
+    };
+    p.w_acc_hi = wtake(kd * 4);
+    p.w_acc_lo = wtake(kd * 4);
+    p.w_cnt = wtake((size_t)k * 4);
+    p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4);
+    p.w_queue = wtake(mti ? WQCAP * sizeof(int2) : 0);
+    p.w_state = wtake(mti ? (size_t)WSTAGES * WCH * sizeof(PtState) : 0);
+    p.w_stride = (int32_t)woff;
+    const size_t total = off + (size_t)WPC * woff;
+    if (total > 110 * 1024) return 0; // keep at least two CTAs per SM
+    p.warp_kernels = 1;
+    p.acc_global = 0;
+    p.stages = 2;
+    return total;
+}
+
 static void fill_common(knor_ctx *c, IterParams &p) {
     p.X = c->X;
     p.n = c->n;
@@ -234,18 +276,32 @@ static void fill_common(knor_ctx *c, IterParams &p) {
     p.mti = c->opts.no_prune ? 0 : 1;
 }
 
+static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
+    int32_t *fl = c->flags;
+    if (c->ip_dense.warp_kernels)
+        return launch_dense_w(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE,
+                              fl + F_NSLOTS, fl + F_FRESH);
+    return launch_dense(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
+                        fl + F_FRESH);
+}
+
+static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
+    int32_t *fl = c->flags;
+    if (c->ip_mti.warp_kernels)
+        return launch_mti_w(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
+                            fl + F_FRESH);
+    return launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
+                      fl + F_FRESH);
+}
+
 static knor_status enqueue_iteration(knor_ctx *c, cudaStream_t s, unsigned long long cond) {
     int32_t *fl = c->flags;
     if (c->ip_dense.acc_global) { // one slot, accumulated by atomics: start from zero
         KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
         KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
     }
-    KNOR_CUDA(c, launch_dense(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE,
-                              fl + F_NSLOTS, fl + F_FRESH));
-    if (!c->opts.no_prune) {
-        KNOR_CUDA(c, launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE,
-                                fl + F_NSLOTS, fl + F_FRESH));
-    }
+    KNOR_CUDA(c, scan_dense(c, s));
+    if (!c->opts.no_prune) KNOR_CUDA(c, scan_mti(c, s));
     KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
     FinParams f = c->fp;
     f.snapshot = 1;
@@ -277,14 +333,12 @@ static knor_status profiled_iteration(knor_ctx *c) {
     }
     if (dense) {
         KNOR_CUDA(c, cudaEventRecord(c->ev[0], s));
-        KNOR_CUDA(c, launch_dense(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE,
-                                  fl + F_NSLOTS, fl + F_FRESH));
+        KNOR_CUDA(c, scan_dense(c, s));
         KNOR_CUDA(c, cudaEventRecord(c->ev[1], s));
         used[KNOR_KERNEL_DENSE] = true;
     } else {
         KNOR_CUDA(c, cudaEventRecord(c->ev[2], s));
-        KNOR_CUDA(c, launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE,
-                                fl + F_NSLOTS, fl + F_FRESH));
+        KNOR_CUDA(c, scan_mti(c, s));
         KNOR_CUDA(c, cudaEventRecord(c->ev[3], s));
         used[KNOR_KERNEL_MTI] = true;
     }
@@ -470,11 +524,17 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
 
     // kernel configurations and persistent grids
     c->dv = supported_dv(d);
-    c->smem_dense = plan_layout(c, false, c->ip_dense);
-    c->smem_mti = plan_layout(c, true, c->ip_mti);
     int bd = 0, bm = 0;
-    KCU(dense_attr(c->dv, c->smem_dense, &bd));
-    KCU(mti_attr(c->dv, c->smem_mti, &bm));
+    {
+        IterParams pw{};
+        const size_t sw = plan_layout_warp(c, false, pw);
+        if (sw) { c->ip_dense = pw; c->smem_dense = sw; KCU(dense_w_attr(c->dv, sw, &bd)); }
+        else { c->smem_dense = plan_layout(c, false, c->ip_dense); KCU(dense_attr(c->dv, c->smem_dense, &bd)); }
+        IterParams pm{};
+        const size_t sm = plan_layout_warp(c, true, pm);
+        if (sm) { c->ip_mti = pm; c->smem_mti = sm; KCU(mti_w_attr(c->dv, sm, &bm)); }
+        else { c->smem_mti = plan_layout(c, true, c->ip_mti); KCU(mti_attr(c->dv, c->smem_mti, &bm)); }
+    }
     if (bd < 1 || bm < 1) { c->err = "knor_create: kernel does not fit on an SM"; return bail(KNOR_ERR_CUDA); }
     c->grid_dense = bd * c->num_sms;
     c->grid_mti = bm * c->num_sms;
@@ -482,6 +542,17 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     // when k x d sums do not fit in shared memory, one slot updated by FP64
     // atomics.
     const int acc_global = (c->ip_dense.acc_global || c->ip_mti.acc_global) ? 1 : 0;
+    if (acc_global && (c->ip_dense.warp_kernels || c->ip_mti.warp_kernels)) {
+        // the warp kernels always write per-CTA slots: use the CTA kernels for both
+        c->ip_dense = IterParams{};
+        c->ip_mti = IterParams{};
+        c->smem_dense = plan_layout(c, false, c->ip_dense);
+        c->smem_mti = plan_layout(c, true, c->ip_mti);
+        KCU(dense_attr(c->dv, c->smem_dense, &bd));
+        KCU(mti_attr(c->dv, c->smem_mti, &bm));
+        c->grid_dense = bd * c->num_sms;
+        c->grid_mti = bm * c->num_sms;
+    }
     c->part_stride = acc_global ? 1 : std::max(c->grid_dense, c->grid_mti);
     KC(dalloc(c, &c->part_S, kd * c->part_stride));
     KC(dalloc(c, &c->part_cnt, (size_t)k * c->part_stride));

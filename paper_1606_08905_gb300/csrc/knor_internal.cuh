@@ -14,6 +14,14 @@ constexpr int PA = 8;
 // Capacity of the MTI active-point ring queue (leftover < NT plus one chunk).
 constexpr int QCAP = NT * PA + NT;
 
+// Warp-autonomous kernels (k_dense_w, k_mti_w): warps per CTA, points per
+// warp chunk of the bound test (PA per lane), per-warp queue capacity and
+// state chunks in flight per warp.
+constexpr int WPC = 4;
+constexpr int WCH = 32 * PA;
+constexpr int WQCAP = 32 + WCH;
+constexpr int WSTAGES = 2;
+
 // Per-point MTI state, packed so that the bound test reads 8 bytes per point.
 //   a   assignment (-1 before the first iteration)
 //   ub  u - F[a] rounded up, where u >= d(x, c_a) was exact-plus-rounding when
@@ -74,6 +82,11 @@ struct IterParams {
     int32_t off_tb, off_ta, off_ti, off_tile, off_queue, off_misc;
     int32_t dpad;          // floats per staged row (d + 4)
     int32_t stages;        // row tiles in flight (dense kernel)
+    // warp-autonomous kernels: warp w's private region starts at
+    // w_base + w * w_stride; offsets below are within that region
+    int32_t warp_kernels;  // 1: k_dense_w / k_mti_w; 0: the CTA kernels
+    int32_t w_base, w_stride;
+    int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_queue, w_state;
 };
 
 // Parameters of the reduction / finalize kernels.
@@ -109,6 +122,13 @@ cudaError_t launch_mti(int dv, const IterParams &p, int grid, size_t smem, cudaS
                        const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
 cudaError_t dense_attr(int dv, size_t smem, int *blocks_per_sm);
 cudaError_t mti_attr(int dv, size_t smem, int *blocks_per_sm);
+// warp-autonomous variants (templated widths only), WPC warps per CTA
+cudaError_t launch_dense_w(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                           const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
+cudaError_t launch_mti_w(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                         const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
+cudaError_t dense_w_attr(int dv, size_t smem, int *blocks_per_sm);
+cudaError_t mti_w_attr(int dv, size_t smem, int *blocks_per_sm);
 cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32_t *fresh, cudaStream_t s);
 cudaError_t launch_table(const FinParams &f, int32_t *mode_dense, int need_table, int recompute_every,
                          int always_dense, cudaStream_t s);
