@@ -168,6 +168,34 @@ knor_status knor_get_profile(knor_ctx *ctx, knor_profile *out, int32_t reset_aft
 knor_status knor_get_state(const knor_ctx *ctx, void *buf, size_t *size);
 knor_status knor_set_state(knor_ctx *ctx, const void *buf, size_t size);
 
+/* One plain Lloyd step on caller-owned device buffers, allocating no device
+ * memory.  (Not from the paper, which has no counterpart: it exists for
+ * callers that cannot allocate, such as code whose device memory belongs to
+ * another allocator that has reserved most of HBM, or loops that must not
+ * call cudaMalloc/cudaFree because those calls synchronise the device.)
+ *   points      n x d FP32, device
+ *   centroids   k x d FP32, device: the centroids of this step
+ *   assign_out  n int32, device: nearest centroid of each point (FP32
+ *               direct-form distance, lowest index on ties; the same values
+ *               knor_iterate computes from the same FP32 centroids)
+ *   sums_out    k x d FP64, device: per-cluster sums of the assigned points
+ *   counts_out  k int64, device: per-cluster member counts
+ *   stream      cudaStream_t to run on (NULL: the legacy default stream);
+ *               the call returns after the stream has finished the step.
+ * The means are sums_out / counts_out (the caller keeps the old centroid of
+ * an empty cluster).  Working memory is a fixed 8 MiB array inside the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits; it limits k * (d + 1) to 4096 (larger sizes return
+ * KNOR_ERR_ARG).  The first call on each device looks the array's device
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture on that device.  All calls share the array: calls that overlap on
+ * the GPU (other streams, other threads) race and give wrong results.
+ * Errors: KNOR_ERR_ARG for NULL or non-device buffers and bad sizes,
+ * KNOR_ERR_CUDA for CUDA failures; the message is knor_last_error(NULL). */
+knor_status knor_lloyd_step_noalloc(const float *points, int64_t n, int32_t d, int32_t k,
+                                    const float *centroids, int32_t *assign_out, double *sums_out,
+                                    int64_t *counts_out, void *stream);
+
 /* Message for the last error on this context ("" if none).  Valid until the
  * next call on the context.  ctx may be NULL for errors of knor_create. */
 const char *knor_last_error(const knor_ctx *ctx);

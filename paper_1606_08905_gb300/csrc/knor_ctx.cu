@@ -122,6 +122,11 @@ struct knor_ctx {
 
 static thread_local std::string g_create_err;
 
+namespace knor {
+// Error message for calls that have no context (read by knor_last_error(NULL)).
+void set_global_error(const char *msg) { g_create_err = msg ? msg : ""; }
+} // namespace knor
+
 #define KNOR_CUDA(ctx, call)                                                                    \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \

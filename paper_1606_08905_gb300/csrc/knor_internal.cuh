@@ -142,5 +142,6 @@ cudaError_t launch_check_bounds(const float *X, int64_t n, int32_t d, const PtSt
                                 const float *C32, const float *F, IterStats *stats,
                                 const int32_t *run_iter, cudaStream_t s);
 int supported_dv(int d); // template width used for d (0 = generic)
+void set_global_error(const char *msg); // message for knor_last_error(NULL)
 
 } // namespace knor

@@ -68,6 +68,9 @@ _SIGS = {
     "knor_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "knor_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "knor_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int32]),
+    "knor_lloyd_step_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
     "knor_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "knor_destroy": (None, [ctypes.c_void_p]),
     "knor_version": (ctypes.c_char_p, []),
@@ -233,6 +236,22 @@ class Context:
     def set_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(load().knor_set_state(self._ctx, buf, len(blob)), self._ctx)
+
+
+def lloyd_step_noalloc(points, centroids, assign_out, sums_out, counts_out, stream: int = 0):
+    """One plain Lloyd step on caller-owned device tensors with no device
+    allocation (knor_lloyd_step_noalloc): points n x d FP32, centroids k x d
+    FP32; fills assign_out (n int32), sums_out (k x d FP64) and counts_out
+    (k int64).  For callers that cannot allocate device memory; all tensors
+    must be on the GPU."""
+    n, d = int(points.shape[0]), int(points.shape[1])
+    k = int(centroids.shape[0])
+    p0, _ = _ptr(points, np.float32)
+    p1, _ = _ptr(centroids, np.float32)
+    p2, _ = _ptr(assign_out, np.int32)
+    p3, _ = _ptr(sums_out, np.float64)
+    p4, _ = _ptr(counts_out, np.int64)
+    _check(load().knor_lloyd_step_noalloc(p0, n, d, k, p1, p2, p3, p4, stream or None), None)
 
 
 def version() -> str:
