@@ -15,18 +15,10 @@
 namespace knor {
 
 constexpr int WT = WPC * 32; // threads per CTA
-// Row tiles per warp in the dense kernel's ring, and row slots per warp in the
-// MTI kernel's gather ring.
-#define DENSE_STAGES(DV) ((DV) <= 32 ? 4 : 2)
-constexpr int RSLOTS = 2;
 
 // Adds (sign = +1) or subtracts (sign = -1) the rows of the lanes with
 // has = true into the warp's accumulators, cluster cl of each lane.  Rows are
-// read from `rowsrc(p, j)` (member lane p, dimension j).  Members are taken
-// four at a time (their loads issue together) into two interleaved TwoSum
-// pairs, merged at the end; the order is fixed, so the sums are
-// deterministic.  A missing member contributes +0, which TwoSum adds
-// exactly.
+// read from `rowsrc(p, j)` (member lane p, dimension j).
 template <int DV, class RowFn>
 __device__ __forceinline__ void warp_group_accumulate(RowFn rowsrc, int cl, bool has, float sign, float *acc_hi,
                                                       float *acc_lo, int *cnt) {
@@ -37,106 +29,53 @@ __device__ __forceinline__ void warp_group_accumulate(RowFn rowsrc, int cl, bool
         const int c = __shfl_sync(FULL_MASK, cl, leader);
         const unsigned grp = __ballot_sync(FULL_MASK, has && cl == c);
         rem &= ~grp;
-        constexpr int R = DV > 32 ? DV / 32 : 1;
-        constexpr int G = DV < 32 ? 32 / DV : 1; // member sub-streams side by side
-        const int sub = DV < 32 ? lane / DV : 0;
-        const int j0 = DV < 32 ? lane % DV : lane;
-        // this lane's members: every G-th member of the group, from `sub`
-        unsigned m = grp;
-        if (G > 1) {
-            unsigned mine = 0;
+        if constexpr (DV <= 32) {
+            constexpr int G = 32 / DV; // members summed side by side
+            const int sub = lane / DV, j = lane % DV;
+            float h = 0.0f, l = 0.0f;
+            unsigned m = grp;
             int idx = 0;
             while (m) {
                 const int pl = __ffs(m) - 1;
                 m &= m - 1;
-                if (idx % G == sub) mine |= 1u << pl;
+                if (idx % G == sub) two_sum_reg(h, l, rowsrc(pl, j) * sign);
                 ++idx;
             }
-            m = mine;
-        }
-        float h0[R], l0[R], h1[R], l1[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) { h0[r] = 0.0f; l0[r] = 0.0f; h1[r] = 0.0f; l1[r] = 0.0f; }
-        while (m) {
-            int q[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                q[t] = m ? __ffs(m) - 1 : -1;
-                m &= m - 1;
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float x[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) x[t] = q[t] >= 0 ? rowsrc(q[t], j0 + 32 * r) * sign : 0.0f;
-                two_sum_reg(h0[r], l0[r], x[0]);
-                two_sum_reg(h1[r], l1[r], x[1]);
-                two_sum_reg(h0[r], l0[r], x[2]);
-                two_sum_reg(h1[r], l1[r], x[3]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) two_sum_merge(h0[r], l0[r], h1[r], l1[r]);
-        if (G > 1) {
 #pragma unroll
             for (int o = DV; o < 32; o <<= 1) {
-                const float h2 = __shfl_xor_sync(FULL_MASK, h0[0], o);
-                const float l2 = __shfl_xor_sync(FULL_MASK, l0[0], o);
-                two_sum_merge(h0[0], l0[0], h2, l2);
+                const float h2 = __shfl_xor_sync(FULL_MASK, h, o);
+                const float l2 = __shfl_xor_sync(FULL_MASK, l, o);
+                two_sum_merge(h, l, h2, l2);
             }
-        }
-        if (sub == 0) {
+            if (sub == 0) {
+                float H = acc_hi[c * DV + j], L = acc_lo[c * DV + j];
+                two_sum_merge(H, L, h, l);
+                acc_hi[c * DV + j] = H;
+                acc_lo[c * DV + j] = L;
+            }
+        } else {
+            constexpr int R = DV / 32;
+            float h[R], l[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { h[r] = 0.0f; l[r] = 0.0f; }
+            unsigned m = grp;
+            while (m) {
+                const int pl = __ffs(m) - 1;
+                m &= m - 1;
+#pragma unroll
+                for (int r = 0; r < R; ++r) two_sum_reg(h[r], l[r], rowsrc(pl, lane + 32 * r) * sign);
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int e = c * DV + j0 + 32 * r;
+                const int e = c * DV + lane + 32 * r;
                 float H = acc_hi[e], L = acc_lo[e];
-                two_sum_merge(H, L, h0[r], l0[r]);
+                two_sum_merge(H, L, h[r], l[r]);
                 acc_hi[e] = H;
                 acc_lo[e] = L;
             }
         }
         if (lane == 0) cnt[c] += (sign > 0.0f ? 1 : -1) * __popc(grp);
     }
-}
-
-// Stable counting sort of a warp's queue entries (local index, cluster) by
-// cluster, so that the points of one batch share their row of the k x k table
-// and mostly the same surviving candidates.  Stable and order-independent in
-// its counts, hence deterministic.
-__device__ __forceinline__ void warp_sort_by_cluster(int2 *q, int2 *tmp, int *hist, int qlen, int k) {
-    const int lane = threadIdx.x & 31;
-    for (int c = lane; c < k; c += 32) hist[c] = 0;
-    __syncwarp();
-    for (int e = lane; e < qlen; e += 32) atomicAdd(&hist[max(q[e].y, 0)], 1);
-    __syncwarp();
-    int carry = 0;
-    for (int c0 = 0; c0 < k; c0 += 32) {
-        const int c = c0 + lane;
-        const int v = c < k ? hist[c] : 0;
-        int incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (c < k) hist[c] = carry + incl - v;
-        carry += __shfl_sync(FULL_MASK, incl, 31);
-    }
-    __syncwarp();
-    for (int base = 0; base < qlen; base += 32) {
-        const int e = base + lane;
-        const bool valid = e < qlen;
-        const int2 ent = valid ? q[e] : make_int2(0, 0);
-        const int key = valid ? max(ent.y, 0) : -1 - lane;
-        const unsigned m = __match_any_sync(FULL_MASK, key);
-        const int rank = __popc(m & ((1u << lane) - 1u));
-        if (valid) tmp[hist[key] + rank] = ent;
-        __syncwarp();
-        if (valid && rank == 0) hist[key] += __popc(m);
-        __syncwarp();
-    }
-    for (int e = lane; e < qlen; e += 32) q[e] = tmp[e];
-    __syncwarp();
 }
 
 // The CTA's partial slot: its warps' accumulators added in warp order.
@@ -213,14 +152,6 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     const Shared sh = stage_shared(p, sm, false);
-    // pair-major copy of the centroids for d2_pairs; an odd k repeats the last
-    float2 *cpair = reinterpret_cast<float2 *>(sm + p.off_halfD);
-    const int npair = (k + 1) / 2;
-    for (int e = tid; e < npair * DV; e += WT) {
-        const int g = e / DV, j = e % DV;
-        const int c0 = 2 * g, c1 = min(2 * g + 1, k - 1);
-        cpair[e] = make_float2(p.C32[(size_t)c0 * DV + j], p.C32[(size_t)c1 * DV + j]);
-    }
     __syncthreads();
     int64_t lo, hi;
     block_range(p.n, 1, lo, hi);
@@ -238,21 +169,16 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
         cp_async_commit();
     };
 
-    // ring of DST tiles per warp: DST - 1 tiles in flight while one is scored
-    constexpr int DST = DENSE_STAGES(DV);
     long long my_changed = 0;
-#pragma unroll
-    for (int s0 = 0; s0 < DST - 1; ++s0) {
-        const int64_t t0 = w + (int64_t)s0 * WPC;
-        if (t0 < ntile) load_tile(s0, t0);
-        else cp_async_commit();
-    }
     int stage = 0;
+    if (w < ntile) load_tile(0, w);
     for (int64_t t = w; t < ntile; t += WPC) {
-        const int64_t tn = t + (int64_t)(DST - 1) * WPC;
-        if (tn < ntile) load_tile((stage + DST - 1) % DST, tn);
-        else cp_async_commit();
-        cp_async_wait<DST - 1>();
+        if (t + WPC < ntile) {
+            load_tile(stage ^ 1, t + WPC);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncwarp();
         const float *tl = tile + stage * 32 * dpad;
         const int64_t base = lo + t * 32;
@@ -260,29 +186,26 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
         const bool valid = lane < rows;
         int best = -1;
         if (valid) {
-            unsigned long long xx[DV];
+            float x[DV];
 #pragma unroll
             for (int j = 0; j < DV; j += 4) {
                 const float4 v = *reinterpret_cast<const float4 *>(tl + lane * dpad + j);
-                xx[j] = pack2(v.x, v.x); xx[j + 1] = pack2(v.y, v.y);
-                xx[j + 2] = pack2(v.z, v.z); xx[j + 3] = pack2(v.w, v.w);
+                x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
             }
             float bd = CUDART_INF_F;
             best = 0;
             int c = 0;
-            constexpr int PG = DV <= 32 ? 4 : 2;
-            for (; c + 2 * PG <= k; c += 2 * PG) {
-                float r[2 * PG];
-                d2_pairs<DV, PG>(xx, cpair + (size_t)(c / 2) * DV, r);
-#pragma unroll
-                for (int q = 0; q < 2 * PG; ++q)
-                    if (r[q] < bd) { bd = r[q]; best = c + q; }
+            for (; c + 4 <= k; c += 4) {
+                float r0, r1, r2, r3;
+                d2_reg4<DV>(x, sh.cent + (size_t)c * DV, r0, r1, r2, r3);
+                if (r0 < bd) { bd = r0; best = c; }
+                if (r1 < bd) { bd = r1; best = c + 1; }
+                if (r2 < bd) { bd = r2; best = c + 2; }
+                if (r3 < bd) { bd = r3; best = c + 3; }
             }
-            for (; c < k; c += 2) {
-                float r[2];
-                d2_pairs<DV, 1>(xx, cpair + (size_t)(c / 2) * DV, r);
-                if (r[0] < bd) { bd = r[0]; best = c; }
-                if (c + 1 < k && r[1] < bd) { bd = r[1]; best = c + 1; }
+            for (; c < k; ++c) {
+                const float r = d2_reg<DV>(x, sh.cent + (size_t)c * DV);
+                if (r < bd) { bd = r; best = c; }
             }
             const int64_t i = base + lane;
             const PtState old = p.st[i];
@@ -295,9 +218,8 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
         warp_group_accumulate<DV>([&](int pl, int j) { return tl[pl * dpad + j]; }, best, valid, 1.0f,
                                   acc_hi, acc_lo, cnt);
         __syncwarp();
-        stage = (stage + 1) % DST;
+        stage ^= 1;
     }
-    cp_async_wait<0>();
     const long long ch = warp_sum_ll(my_changed);
     if (lane == 0) {
         atomicAdd(&p.ctr->changed, (unsigned long long)ch);
@@ -327,11 +249,7 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
     float *acc_lo = reinterpret_cast<float *>(wr + p.w_acc_lo);
     int *cnt = reinterpret_cast<int *>(wr + p.w_cnt);
     int2 *queue = reinterpret_cast<int2 *>(wr + p.w_queue);
-    int2 *queue2 = queue + WQCAP;
-    int *hist = reinterpret_cast<int *>(queue2 + WQCAP);
     PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
-    float *rows = reinterpret_cast<float *>(wr + p.w_tile);
-    const int dpad = p.dpad;
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
@@ -420,84 +338,47 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
 
         // ---- phases B and C on every full batch of 32 (and the rest at the end)
         const bool last = m + WPC >= nchunk;
-        if (p.sort_queue && (qlen >= 32 || last)) warp_sort_by_cluster(queue, queue2, hist, qlen, k);
-        // Batches of 32 queued points; each batch's rows are gathered with
-        // cp.async into a ring of RSLOTS row slots, RSLOTS - 1 batches ahead.
-        const int nbatch = last ? (qlen + 31) / 32 : qlen / 32;
-        auto issue_rows = [&](int b) {
-            if (b < nbatch) {
-                const int nbb = min(32, qlen - b * 32);
-                if (lane < nbb) {
-                    const int2 e = queue[b * 32 + lane];
-                    const float *src = p.X + (lo + e.x) * DV;
-                    float *dst = rows + (b % RSLOTS) * 32 * dpad + lane * dpad;
-#pragma unroll
-                    for (int v = 0; v < DV / 4; ++v) cp_async16(dst + 4 * v, src + 4 * v);
-                }
-            }
-            cp_async_commit();
-        };
-#pragma unroll
-        for (int b0 = 0; b0 < RSLOTS - 1; ++b0) issue_rows(b0);
-        for (int b = 0; b < nbatch; ++b) {
-            issue_rows(b + RSLOTS - 1);
-            cp_async_wait<RSLOTS - 1>();
-            __syncwarp();
-            const int nb = min(32, qlen - b * 32);
-            const float *rs = rows + (b % RSLOTS) * 32 * dpad;
+        int qhead = 0;
+        while (qlen >= 32 || (last && qlen > 0)) {
+            const int nb = min(32, qlen);
             int best = -1, a = -1;
             int64_t i = 0;
             bool changed = false;
-            float xk[DV];
-            float bd = CUDART_INF_F, tst = 0.0f;
             if (lane < nb) {
-                const int2 e = queue[b * 32 + lane];
+                const int2 e = queue[qhead + lane];
                 i = lo + e.x;
                 a = e.y;
+                float x[DV];
+                const float4 *xr = reinterpret_cast<const float4 *>(p.X + i * DV);
 #pragma unroll
-                for (int j = 0; j < DV; j += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(rs + lane * dpad + j);
-                    xk[j] = v.x; xk[j + 1] = v.y; xk[j + 2] = v.z; xk[j + 3] = v.w;
+                for (int j = 0; j < DV / 4; ++j) {
+                    const float4 v = __ldg(xr + j);
+                    x[4 * j] = v.x; x[4 * j + 1] = v.y; x[4 * j + 2] = v.z; x[4 * j + 3] = v.w;
                 }
+                float bd;
                 if (a < 0) {
+                    bd = CUDART_INF_F;
                     best = 0;
                     for (int c = 0; c < k; ++c) {
-                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
+                        const float r = d2_reg<DV>(x, sh.cent + (size_t)c * DV);
                         if (r < bd) { bd = r; best = c; }
                     }
                     my_evals += k;
                 } else {
                     // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
-                    bd = d2_reg<DV>(xk, sh.cent + (size_t)a * DV);
+                    bd = d2_reg<DV>(x, sh.cent + (size_t)a * DV);
                     best = a;
                     ++my_evals;
-                }
-                tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
-            }
-            // Clause 2 per centroid, 32 centroids per word: the lane's survivors
-            // form a bit mask; the warp walks only the union of the masks, in
-            // index order, and each lane scores its own survivors.
-            for (int cw = 0; cw < k; cw += 32) {
-                unsigned mask = 0;
-                if (lane < nb && a >= 0) {
-                    const float *hrow = sh.halfD + (size_t)a * k + cw;
-                    const int lim = min(32, k - cw);
-                    for (int bb = 0; bb < lim; ++bb)
-                        mask |= (!(tst < hrow[bb]) && cw + bb != a ? 1u : 0u) << bb;
-                }
-                unsigned uni = __reduce_or_sync(FULL_MASK, mask);
-                while (uni) {
-                    const int bb = __ffs(uni) - 1;
-                    uni &= uni - 1;
-                    if ((mask >> bb) & 1u) {
-                        const int c = cw + bb;
-                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
+                    const float test = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
+                    const float *hrow = sh.halfD + (size_t)a * k;
+                    for (int c = 0; c < k; ++c) {
+                        if (c == a) continue;
+                        if (test < hrow[c]) continue; // Clause 2: c cannot be nearer
+                        const float r = d2_reg<DV>(x, sh.cent + (size_t)c * DV);
                         ++my_evals;
                         if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
                     }
                 }
-            }
-            if (lane < nb) {
                 PtState ns;
                 ns.a = best;
                 ns.ub = __fsub_ru(bound_up(bd, p.g_up, p.tiny), sh.F[best]);
@@ -505,13 +386,16 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
                 changed = best != a;
                 my_changed += changed ? 1 : 0;
             }
-            auto row = [&](int pl, int j) { return rs[pl * dpad + j]; };
+            // member pl's row, by its queue entry (no shuffles: the member
+            // loop of warp_group_accumulate is lane-divergent)
+            const float *X = p.X;
+            const int2 *qb = queue + qhead;
+            auto row = [&](int pl, int j) { return __ldg(X + (lo + qb[pl].x) * DV + j); };
             warp_group_accumulate<DV>(row, best, changed, 1.0f, acc_hi, acc_lo, cnt);
             warp_group_accumulate<DV>(row, a, changed && a >= 0, -1.0f, acc_hi, acc_lo, cnt);
-            __syncwarp();
+            qhead += nb;
+            qlen -= nb;
         }
-        const int qhead = min(qlen, nbatch * 32);
-        qlen -= qhead;
         if (qhead > 0 && qlen > 0) { // qlen < 32: move the rest to the front
             int2 v = make_int2(0, 0);
             if (lane < qlen) v = queue[qhead + lane];

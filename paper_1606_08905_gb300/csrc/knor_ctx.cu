@@ -231,9 +231,7 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.cent_smem = kd * 4 <= 32 * 1024 ? 1 : 0;
     p.off_cent = take(p.cent_smem ? kd * 4 : 0);
     p.halfD_smem = (mti && (size_t)k * k * 4 <= 16 * 1024) ? 1 : 0;
-    // dense: off_halfD holds the pair-major centroid copy instead
-    if (!mti && (size_t)(k + 1) * d * 4 > 32 * 1024) return 0;
-    p.off_halfD = take(mti ? (p.halfD_smem ? (size_t)k * k * 4 : 0) : (size_t)(k + 1) * d * 4);
+    p.off_halfD = take(p.halfD_smem ? (size_t)k * k * 4 : 0);
     const bool sf = (size_t)k * 8 <= 8 * 1024;
     p.off_s = sf ? take((size_t)k * 4) : -1;
     p.off_F = sf ? take((size_t)k * 4) : -1;
@@ -247,14 +245,12 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.w_acc_hi = wtake(kd * 4);
     p.w_acc_lo = wtake(kd * 4);
     p.w_cnt = wtake((size_t)k * 4);
-    const int dstages = d <= 32 ? 4 : 2; // DENSE_STAGES in kernels_warp.cu
-    p.w_tile = wtake((mti ? 2 : dstages) * 32 * (size_t)p.dpad * 4); // MTI: RSLOTS row slots
-    p.sort_queue = (mti && k <= 1024) ? 1 : 0;
-    p.w_queue = wtake(mti ? 2 * WQCAP * sizeof(int2) + (p.sort_queue ? (size_t)k * 4 : 0) : 0);
+    p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4);
+    p.w_queue = wtake(mti ? WQCAP * sizeof(int2) : 0);
     p.w_state = wtake(mti ? (size_t)WSTAGES * WCH * sizeof(PtState) : 0);
     p.w_stride = (int32_t)woff;
     const size_t total = off + (size_t)WPC * woff;
-    if (total > 150 * 1024) return 0;
+    if (total > 110 * 1024) return 0; // keep at least two CTAs per SM
     p.warp_kernels = 1;
     p.acc_global = 0;
     p.stages = 2;
