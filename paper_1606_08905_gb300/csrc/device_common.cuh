@@ -61,6 +61,44 @@ __device__ __forceinline__ void d2_reg4(const float (&x)[DV], const float *c, fl
     r0 = a0; r1 = a1; r2 = a2; r3 = a3;
 }
 
+// Packed pair of FP32 values in one 64-bit register (for the f32x2 ops).
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+// Squared distances from one point to PG pairs of centroids with the packed
+// sub.rn.f32x2 / fma.rn.f32x2 instructions.  Each lane of a pair performs
+// exactly the operations of d2_reg (x_j - c_j rounded, then fma into its own
+// accumulator, j = 0..DV-1 in order), so the results are bit-identical to
+// d2_reg; two centroids per instruction halve the instruction count.
+//   xx   x_j duplicated into both halves, j = 0..DV-1
+//   cp   pair-major centroid copy: cp[(g*DV + j)] = (c_{2g}[j], c_{2g+1}[j])
+template <int DV, int PG>
+__device__ __forceinline__ void d2_pairs(const unsigned long long (&xx)[DV], const float2 *cp, float (&r)[2 * PG]) {
+    unsigned long long acc[PG];
+#pragma unroll
+    for (int g = 0; g < PG; ++g) acc[g] = 0ULL; // (+0.0f, +0.0f)
+#pragma unroll
+    for (int j = 0; j < DV; j += 2) {
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            const float4 v = *reinterpret_cast<const float4 *>(cp + (size_t)g * DV + j);
+            unsigned long long t;
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(xx[j]), "l"(pack2(v.x, v.y)));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[g]) : "l"(t));
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(xx[j + 1]), "l"(pack2(v.z, v.w)));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[g]) : "l"(t));
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < PG; ++g) unpack2(acc[g], r[2 * g], r[2 * g + 1]);
+}
+
 // Generic width: the same operation sequence with a runtime d.
 __device__ __forceinline__ float d2_gen(const float *x, const float *c, int d) {
     float acc = 0.0f;

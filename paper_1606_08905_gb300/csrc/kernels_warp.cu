@@ -78,6 +78,46 @@ __device__ __forceinline__ void warp_group_accumulate(RowFn rowsrc, int cl, bool
     }
 }
 
+// Stable counting sort of a warp's queue entries (local index, cluster) by
+// cluster, so that the points of one batch share their row of the k x k table
+// and mostly the same surviving candidates.  Stable and order-independent in
+// its counts, hence deterministic.
+__device__ __forceinline__ void warp_sort_by_cluster(int2 *q, int2 *tmp, int *hist, int qlen, int k) {
+    const int lane = threadIdx.x & 31;
+    for (int c = lane; c < k; c += 32) hist[c] = 0;
+    __syncwarp();
+    for (int e = lane; e < qlen; e += 32) atomicAdd(&hist[max(q[e].y, 0)], 1);
+    __syncwarp();
+    int carry = 0;
+    for (int c0 = 0; c0 < k; c0 += 32) {
+        const int c = c0 + lane;
+        const int v = c < k ? hist[c] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (c < k) hist[c] = carry + incl - v;
+        carry += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    __syncwarp();
+    for (int base = 0; base < qlen; base += 32) {
+        const int e = base + lane;
+        const bool valid = e < qlen;
+        const int2 ent = valid ? q[e] : make_int2(0, 0);
+        const int key = valid ? max(ent.y, 0) : -1 - lane;
+        const unsigned m = __match_any_sync(FULL_MASK, key);
+        const int rank = __popc(m & ((1u << lane) - 1u));
+        if (valid) tmp[hist[key] + rank] = ent;
+        __syncwarp();
+        if (valid && rank == 0) hist[key] += __popc(m);
+        __syncwarp();
+    }
+    for (int e = lane; e < qlen; e += 32) q[e] = tmp[e];
+    __syncwarp();
+}
+
 // The CTA's partial slot: its warps' accumulators added in warp order.
 __device__ __forceinline__ void flush_warp_partials(const IterParams &p, unsigned char *sm) {
     const int kd = p.k * p.d;
@@ -152,6 +192,14 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     const Shared sh = stage_shared(p, sm, false);
+    // pair-major copy of the centroids for d2_pairs; an odd k repeats the last
+    float2 *cpair = reinterpret_cast<float2 *>(sm + p.off_halfD);
+    const int npair = (k + 1) / 2;
+    for (int e = tid; e < npair * DV; e += WT) {
+        const int g = e / DV, j = e % DV;
+        const int c0 = 2 * g, c1 = min(2 * g + 1, k - 1);
+        cpair[e] = make_float2(p.C32[(size_t)c0 * DV + j], p.C32[(size_t)c1 * DV + j]);
+    }
     __syncthreads();
     int64_t lo, hi;
     block_range(p.n, 1, lo, hi);
@@ -186,26 +234,29 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
         const bool valid = lane < rows;
         int best = -1;
         if (valid) {
-            float x[DV];
+            unsigned long long xx[DV];
 #pragma unroll
             for (int j = 0; j < DV; j += 4) {
                 const float4 v = *reinterpret_cast<const float4 *>(tl + lane * dpad + j);
-                x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
+                xx[j] = pack2(v.x, v.x); xx[j + 1] = pack2(v.y, v.y);
+                xx[j + 2] = pack2(v.z, v.z); xx[j + 3] = pack2(v.w, v.w);
             }
             float bd = CUDART_INF_F;
             best = 0;
             int c = 0;
-            for (; c + 4 <= k; c += 4) {
-                float r0, r1, r2, r3;
-                d2_reg4<DV>(x, sh.cent + (size_t)c * DV, r0, r1, r2, r3);
-                if (r0 < bd) { bd = r0; best = c; }
-                if (r1 < bd) { bd = r1; best = c + 1; }
-                if (r2 < bd) { bd = r2; best = c + 2; }
-                if (r3 < bd) { bd = r3; best = c + 3; }
+            constexpr int PG = DV <= 32 ? 4 : 2;
+            for (; c + 2 * PG <= k; c += 2 * PG) {
+                float r[2 * PG];
+                d2_pairs<DV, PG>(xx, cpair + (size_t)(c / 2) * DV, r);
+#pragma unroll
+                for (int q = 0; q < 2 * PG; ++q)
+                    if (r[q] < bd) { bd = r[q]; best = c + q; }
             }
-            for (; c < k; ++c) {
-                const float r = d2_reg<DV>(x, sh.cent + (size_t)c * DV);
-                if (r < bd) { bd = r; best = c; }
+            for (; c < k; c += 2) {
+                float r[2];
+                d2_pairs<DV, 1>(xx, cpair + (size_t)(c / 2) * DV, r);
+                if (r[0] < bd) { bd = r[0]; best = c; }
+                if (c + 1 < k && r[1] < bd) { bd = r[1]; best = c + 1; }
             }
             const int64_t i = base + lane;
             const PtState old = p.st[i];
@@ -249,6 +300,8 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
     float *acc_lo = reinterpret_cast<float *>(wr + p.w_acc_lo);
     int *cnt = reinterpret_cast<int *>(wr + p.w_cnt);
     int2 *queue = reinterpret_cast<int2 *>(wr + p.w_queue);
+    int2 *queue2 = queue + WQCAP;
+    int *hist = reinterpret_cast<int *>(queue2 + WQCAP);
     PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
@@ -338,47 +391,64 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
 
         // ---- phases B and C on every full batch of 32 (and the rest at the end)
         const bool last = m + WPC >= nchunk;
+        if (p.sort_queue && (qlen >= 32 || last)) warp_sort_by_cluster(queue, queue2, hist, qlen, k);
         int qhead = 0;
         while (qlen >= 32 || (last && qlen > 0)) {
             const int nb = min(32, qlen);
             int best = -1, a = -1;
             int64_t i = 0;
             bool changed = false;
+            float xk[DV];
+            float bd = CUDART_INF_F, tst = 0.0f;
             if (lane < nb) {
                 const int2 e = queue[qhead + lane];
                 i = lo + e.x;
                 a = e.y;
-                float x[DV];
                 const float4 *xr = reinterpret_cast<const float4 *>(p.X + i * DV);
 #pragma unroll
                 for (int j = 0; j < DV / 4; ++j) {
                     const float4 v = __ldg(xr + j);
-                    x[4 * j] = v.x; x[4 * j + 1] = v.y; x[4 * j + 2] = v.z; x[4 * j + 3] = v.w;
+                    xk[4 * j] = v.x; xk[4 * j + 1] = v.y; xk[4 * j + 2] = v.z; xk[4 * j + 3] = v.w;
                 }
-                float bd;
                 if (a < 0) {
-                    bd = CUDART_INF_F;
                     best = 0;
                     for (int c = 0; c < k; ++c) {
-                        const float r = d2_reg<DV>(x, sh.cent + (size_t)c * DV);
+                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
                         if (r < bd) { bd = r; best = c; }
                     }
                     my_evals += k;
                 } else {
                     // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
-                    bd = d2_reg<DV>(x, sh.cent + (size_t)a * DV);
+                    bd = d2_reg<DV>(xk, sh.cent + (size_t)a * DV);
                     best = a;
                     ++my_evals;
-                    const float test = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
-                    const float *hrow = sh.halfD + (size_t)a * k;
-                    for (int c = 0; c < k; ++c) {
-                        if (c == a) continue;
-                        if (test < hrow[c]) continue; // Clause 2: c cannot be nearer
-                        const float r = d2_reg<DV>(x, sh.cent + (size_t)c * DV);
+                }
+                tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
+            }
+            // Clause 2 per centroid, 32 centroids per word: the lane's survivors
+            // form a bit mask; the warp walks only the union of the masks, in
+            // index order, and each lane scores its own survivors.
+            for (int cw = 0; cw < k; cw += 32) {
+                unsigned mask = 0;
+                if (lane < nb && a >= 0) {
+                    const float *hrow = sh.halfD + (size_t)a * k + cw;
+                    const int lim = min(32, k - cw);
+                    for (int b = 0; b < lim; ++b)
+                        mask |= (!(tst < hrow[b]) && cw + b != a ? 1u : 0u) << b;
+                }
+                unsigned uni = __reduce_or_sync(FULL_MASK, mask);
+                while (uni) {
+                    const int b = __ffs(uni) - 1;
+                    uni &= uni - 1;
+                    if ((mask >> b) & 1u) {
+                        const int c = cw + b;
+                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
                         ++my_evals;
                         if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
                     }
                 }
+            }
+            if (lane < nb) {
                 PtState ns;
                 ns.a = best;
                 ns.ub = __fsub_ru(bound_up(bd, p.g_up, p.tiny), sh.F[best]);

@@ -231,7 +231,9 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.cent_smem = kd * 4 <= 32 * 1024 ? 1 : 0;
     p.off_cent = take(p.cent_smem ? kd * 4 : 0);
     p.halfD_smem = (mti && (size_t)k * k * 4 <= 16 * 1024) ? 1 : 0;
-    p.off_halfD = take(p.halfD_smem ? (size_t)k * k * 4 : 0);
+    // dense: off_halfD holds the pair-major centroid copy instead
+    if (!mti && (size_t)(k + 1) * d * 4 > 32 * 1024) return 0;
+    p.off_halfD = take(mti ? (p.halfD_smem ? (size_t)k * k * 4 : 0) : (size_t)(k + 1) * d * 4);
     const bool sf = (size_t)k * 8 <= 8 * 1024;
     p.off_s = sf ? take((size_t)k * 4) : -1;
     p.off_F = sf ? take((size_t)k * 4) : -1;
@@ -246,7 +248,8 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.w_acc_lo = wtake(kd * 4);
     p.w_cnt = wtake((size_t)k * 4);
     p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4);
-    p.w_queue = wtake(mti ? WQCAP * sizeof(int2) : 0);
+    p.sort_queue = (mti && k <= 1024) ? 1 : 0;
+    p.w_queue = wtake(mti ? 2 * WQCAP * sizeof(int2) + (p.sort_queue ? (size_t)k * 4 : 0) : 0);
     p.w_state = wtake(mti ? (size_t)WSTAGES * WCH * sizeof(PtState) : 0);
     p.w_stride = (int32_t)woff;
     const size_t total = off + (size_t)WPC * woff;

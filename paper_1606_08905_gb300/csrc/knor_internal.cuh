@@ -87,6 +87,7 @@ struct IterParams {
     int32_t warp_kernels;  // 1: k_dense_w / k_mti_w; 0: the CTA kernels
     int32_t w_base, w_stride;
     int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_queue, w_state;
+    int32_t sort_queue;    // k_mti_w: sort each warp's queue by cluster (k <= 1024)
 };
 
 // Parameters of the reduction / finalize kernels.
