@@ -78,15 +78,17 @@ __device__ __forceinline__ void warp_group_accumulate(RowFn rowsrc, int cl, bool
     }
 }
 
-// Stable counting sort of a warp's queue entries (local index, cluster) by
-// cluster, so that the points of one batch share their row of the k x k table
-// and mostly the same surviving candidates.  Stable and order-independent in
-// its counts, hence deterministic.
+// Stable counting sort of a warp's queue entries (local index, key) by key
+// modulo nkeys.  The key is a * UBINS + bin(u / s(a)): the points of a batch
+// then share their row of the k x k table, and since for a fixed a the
+// centroids that survive Clause 2 are exactly those with 1/2 d(c_a, c) below
+// the point's bound, points with similar u keep nearly the same candidates.
+// Stable and order-independent in its counts, hence deterministic.
 __device__ __forceinline__ void warp_sort_by_cluster(int2 *q, int2 *tmp, int *hist, int qlen, int k) {
     const int lane = threadIdx.x & 31;
     for (int c = lane; c < k; c += 32) hist[c] = 0;
     __syncwarp();
-    for (int e = lane; e < qlen; e += 32) atomicAdd(&hist[max(q[e].y, 0)], 1);
+    for (int e = lane; e < qlen; e += 32) atomicAdd(&hist[max(q[e].y, 0) % k], 1);
     __syncwarp();
     int carry = 0;
     for (int c0 = 0; c0 < k; c0 += 32) {
@@ -106,7 +108,7 @@ __device__ __forceinline__ void warp_sort_by_cluster(int2 *q, int2 *tmp, int *hi
         const int e = base + lane;
         const bool valid = e < qlen;
         const int2 ent = valid ? q[e] : make_int2(0, 0);
-        const int key = valid ? max(ent.y, 0) : -1 - lane;
+        const int key = valid ? max(ent.y, 0) % k : -1 - lane;
         const unsigned m = __match_any_sync(FULL_MASK, key);
         const int rank = __popc(m & ((1u << lane) - 1u));
         if (valid) tmp[hist[key] + rank] = ent;
@@ -356,15 +358,22 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
         }
         unsigned amask = 0;
         int nvalid = 0;
+        int ubin[PA];
 #pragma unroll
         for (int u = 0; u < PA; ++u) {
             const int a = ps[u].a;
+            ubin[u] = 0;
             if (a == -2) continue;
             ++nvalid;
             bool act = true;
             if (a >= 0) {
                 const float uu = __fadd_ru(ps[u].ub, sh.F[a]); // u^t = ub + F^t(a)
                 act = !(__fmaf_ru(uu, p.onepk, p.tau) < sh.s[a]);
+                // bin of u / s(a) on a quarter-octave scale (sort key only)
+                if (p.ubins > 1) {
+                    const float r = __fdividef(uu, fmaxf(sh.s[a], 1e-30f));
+                    ubin[u] = min(p.ubins - 1, max(0, (int)(4.0f * __log2f(fmaxf(r, 1.0f)))));
+                }
             }
             amask |= (act ? 1u : 0u) << u;
         }
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
 #pragma unroll
         for (int u = 0; u < PA; ++u) {
             if ((amask >> u) & 1u) {
-                queue[pos] = make_int2((int)(i0 + u - lo), ps[u].a);
+                queue[pos] = make_int2((int)(i0 + u - lo), ps[u].a < 0 ? -1 : ps[u].a * p.ubins + ubin[u]);
                 ++pos;
             }
         }
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
 
         // ---- phases B and C on every full batch of 32 (and the rest at the end)
         const bool last = m + WPC >= nchunk;
-        if (p.sort_queue && (qlen >= 32 || last)) warp_sort_by_cluster(queue, queue2, hist, qlen, k);
+        if (p.sort_queue && (qlen >= 32 || last)) warp_sort_by_cluster(queue, queue2, hist, qlen, k * p.ubins);
         int qhead = 0;
         while (qlen >= 32 || (last && qlen > 0)) {
             const int nb = min(32, qlen);
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
             if (lane < nb) {
                 const int2 e = queue[qhead + lane];
                 i = lo + e.x;
-                a = e.y;
+                a = e.y < 0 ? -1 : e.y / p.ubins;
                 const float4 *xr = reinterpret_cast<const float4 *>(p.X + i * DV);
 #pragma unroll
                 for (int j = 0; j < DV / 4; ++j) {

@@ -249,7 +249,8 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.w_cnt = wtake((size_t)k * 4);
     p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4);
     p.sort_queue = (mti && k <= 1024) ? 1 : 0;
-    p.w_queue = wtake(mti ? 2 * WQCAP * sizeof(int2) + (p.sort_queue ? (size_t)k * 4 : 0) : 0);
+    p.ubins = k <= 128 ? 8 : 1;
+    p.w_queue = wtake(mti ? 2 * WQCAP * sizeof(int2) + (p.sort_queue ? (size_t)k * p.ubins * 4 : 0) : 0);
     p.w_state = wtake(mti ? (size_t)WSTAGES * WCH * sizeof(PtState) : 0);
     p.w_stride = (int32_t)woff;
     const size_t total = off + (size_t)WPC * woff;

@@ -88,6 +88,7 @@ struct IterParams {
     int32_t w_base, w_stride;
     int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_queue, w_state;
     int32_t sort_queue;    // k_mti_w: sort each warp's queue by cluster (k <= 1024)
+    int32_t ubins;         // k_mti_w: bins of u / s(a) in the sort key (1 = by cluster only)
 };
 
 // Parameters of the reduction / finalize kernels.
