@@ -138,7 +138,8 @@ def assign(X, C, nthreads: int = 0):
 
 
 def assign_f32(X, C32, nthreads: int = 0) -> np.ndarray:
-    """The argmin taken in FP32 (index-order fmaf chain), lowest index on ties."""
+    """The argmin taken in FP32 (even/odd fmaf chains, then their sum), lowest
+    index on ties."""
     X = _X(X)
     n, d = X.shape
     C32 = np.ascontiguousarray(C32, dtype=np.float32)

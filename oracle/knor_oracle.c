@@ -463,9 +463,12 @@ int oracle_run(const float *X, int64_t n, int32_t d, int32_t k, const double *C0
 }
 
 /* The assignment decision restated in FP32, for callers that want to compare
- * an FP32 argmin in the same precision: d^2 = sum over i = 0..d-1, in index
- * order, of fmaf(x_i - c_i, x_i - c_i, acc), every operation rounded to
- * nearest FP32; lowest index wins ties. */
+ * an FP32 argmin in the same precision.  The paper computes in FP64 and fixes
+ * no FP32 summation order; this restates the order the library documents for
+ * its FP32 distance: two chains, e over even i and o over odd i, each in
+ * increasing i with e (or o) = fmaf(x_i - c_i, x_i - c_i, e), then
+ * d^2 = e + o; every operation rounded to nearest FP32; lowest index wins
+ * ties. */
 void oracle_assign_f32(const float *X, int64_t n, int32_t d, int32_t k, const float *C32,
                        int32_t *a_out, int nthreads) {
     int64_t i;
@@ -478,11 +481,13 @@ void oracle_assign_f32(const float *X, int64_t n, int32_t d, int32_t k, const fl
         int32_t c, q, best = 0;
         float bd = INFINITY;
         for (c = 0; c < k; ++c) {
-            float acc = 0.0f;
+            float e = 0.0f, o = 0.0f, acc;
             for (q = 0; q < d; ++q) {
                 float t = x[q] - C32[(size_t)c * d + q];
-                acc = fmaf(t, t, acc);
+                if (q % 2 == 0) e = fmaf(t, t, e);
+                else o = fmaf(t, t, o);
             }
+            acc = e + o;
             if (acc < bd) { bd = acc; best = c; }
         }
         a_out[i] = best;
