@@ -22,46 +22,16 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Squared distance, row in registers, centroid 16-byte aligned (smem or global).
-template <int DV>
-__device__ __forceinline__ float d2_reg(const float (&x)[DV], const float *c) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int j = 0; j < DV; j += 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(c + j);
-        float t;
-        t = __fsub_rn(x[j + 0], v.x); acc = __fmaf_rn(t, t, acc);
-        t = __fsub_rn(x[j + 1], v.y); acc = __fmaf_rn(t, t, acc);
-        t = __fsub_rn(x[j + 2], v.z); acc = __fmaf_rn(t, t, acc);
-        t = __fsub_rn(x[j + 3], v.w); acc = __fmaf_rn(t, t, acc);
-    }
-    return acc;
-}
+// The FP32 squared distance used by every scan of this library:
+//   e = sum over even j, o = sum over odd j (each in increasing j, each term
+//   t_j = x_j - c_j rounded, then e or o = fma(t_j, t_j, e or o) rounded),
+//   d^2 = e + o rounded.
+// Even and odd dimensions sit side by side in one 64-bit register, so a
+// packed sub.rn.f32x2 / fma.rn.f32x2 does a step of both chains; every lane
+// of a packed op rounds exactly like the scalar op.  Relative error of d^2:
+// at most ceil(d/2) + 2 roundings on each chain plus the final add, within
+// (1 - (d + 2) 2^-24)^-1 - 1 (see bound_up).
 
-// Four centroids at once (independent chains for ILP); each chain performs
-// exactly the operations of d2_reg, so the values are identical.
-template <int DV>
-__device__ __forceinline__ void d2_reg4(const float (&x)[DV], const float *c, float &r0, float &r1,
-                                        float &r2, float &r3) {
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-#pragma unroll
-    for (int j = 0; j < DV; j += 4) {
-        const float4 v0 = *reinterpret_cast<const float4 *>(c + j);
-        const float4 v1 = *reinterpret_cast<const float4 *>(c + DV + j);
-        const float4 v2 = *reinterpret_cast<const float4 *>(c + 2 * DV + j);
-        const float4 v3 = *reinterpret_cast<const float4 *>(c + 3 * DV + j);
-        float t;
-#define KNOR_STEP(acc, xv, cv) t = __fsub_rn(xv, cv); acc = __fmaf_rn(t, t, acc);
-        KNOR_STEP(a0, x[j], v0.x) KNOR_STEP(a1, x[j], v1.x) KNOR_STEP(a2, x[j], v2.x) KNOR_STEP(a3, x[j], v3.x)
-        KNOR_STEP(a0, x[j + 1], v0.y) KNOR_STEP(a1, x[j + 1], v1.y) KNOR_STEP(a2, x[j + 1], v2.y) KNOR_STEP(a3, x[j + 1], v3.y)
-        KNOR_STEP(a0, x[j + 2], v0.z) KNOR_STEP(a1, x[j + 2], v1.z) KNOR_STEP(a2, x[j + 2], v2.z) KNOR_STEP(a3, x[j + 2], v3.z)
-        KNOR_STEP(a0, x[j + 3], v0.w) KNOR_STEP(a1, x[j + 3], v1.w) KNOR_STEP(a2, x[j + 3], v2.w) KNOR_STEP(a3, x[j + 3], v3.w)
-#undef KNOR_STEP
-    }
-    r0 = a0; r1 = a1; r2 = a2; r3 = a3;
-}
-
-// Packed pair of FP32 values in one 64-bit register (for the f32x2 ops).
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
@@ -70,43 +40,89 @@ __device__ __forceinline__ unsigned long long pack2(float a, float b) {
 __device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
 }
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sqacc2(unsigned long long t, unsigned long long acc) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(t), "l"(acc));
+    return r;
+}
+__device__ __forceinline__ float fold2(unsigned long long acc) {
+    float e, o;
+    unpack2(acc, e, o);
+    return __fadd_rn(e, o);
+}
 
-// Squared distances from one point to PG pairs of centroids with the packed
-// sub.rn.f32x2 / fma.rn.f32x2 instructions.  Each lane of a pair performs
-// exactly the operations of d2_reg (x_j - c_j rounded, then fma into its own
-// accumulator, j = 0..DV-1 in order), so the results are bit-identical to
-// d2_reg; two centroids per instruction halve the instruction count.
-//   xx   x_j duplicated into both halves, j = 0..DV-1
-//   cp   pair-major centroid copy: cp[(g*DV + j)] = (c_{2g}[j], c_{2g+1}[j])
-template <int DV, int PG>
-__device__ __forceinline__ void d2_pairs(const unsigned long long (&xx)[DV], const float2 *cp, float (&r)[2 * PG]) {
-    unsigned long long acc[PG];
+// Point as DV/2 packed (x_j, x_{j+1}) pairs, from a 16-byte-aligned row.
+template <int DV>
+__device__ __forceinline__ void load_x2(unsigned long long (&x2)[DV / 2], const float *row) {
 #pragma unroll
-    for (int g = 0; g < PG; ++g) acc[g] = 0ULL; // (+0.0f, +0.0f)
+    for (int j = 0; j < DV; j += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(row + j);
+        x2[j / 2] = pack2(v.x, v.y);
+        x2[j / 2 + 1] = pack2(v.z, v.w);
+    }
+}
+template <int DV>
+__device__ __forceinline__ void ldg_x2(unsigned long long (&x2)[DV / 2], const float *row) {
 #pragma unroll
-    for (int j = 0; j < DV; j += 2) {
+    for (int j = 0; j < DV; j += 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(row + j));
+        x2[j / 2] = pack2(v.x, v.y);
+        x2[j / 2 + 1] = pack2(v.z, v.w);
+    }
+}
+
+// d^2 to one centroid (16-byte aligned, smem or global).
+template <int DV>
+__device__ __forceinline__ float d2_reg(const unsigned long long (&x2)[DV / 2], const float *c) {
+    unsigned long long acc = 0ULL; // (+0, +0)
 #pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            const float4 v = *reinterpret_cast<const float4 *>(cp + (size_t)g * DV + j);
-            unsigned long long t;
-            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(xx[j]), "l"(pack2(v.x, v.y)));
-            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[g]) : "l"(t));
-            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(xx[j + 1]), "l"(pack2(v.z, v.w)));
-            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[g]) : "l"(t));
+    for (int j = 0; j < DV; j += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(c + j);
+        acc = sqacc2(sub2(x2[j / 2], pack2(v.x, v.y)), acc);
+        acc = sqacc2(sub2(x2[j / 2 + 1], pack2(v.z, v.w)), acc);
+    }
+    return fold2(acc);
+}
+
+// d^2 to NC consecutive centroids at once (independent chains, same values).
+template <int DV, int NC>
+__device__ __forceinline__ void d2_regN(const unsigned long long (&x2)[DV / 2], const float *c, float (&r)[NC]) {
+    unsigned long long acc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = 0ULL;
+#pragma unroll
+    for (int j = 0; j < DV; j += 4) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const float4 v = *reinterpret_cast<const float4 *>(c + (size_t)q * DV + j);
+            acc[q] = sqacc2(sub2(x2[j / 2], pack2(v.x, v.y)), acc[q]);
+            acc[q] = sqacc2(sub2(x2[j / 2 + 1], pack2(v.z, v.w)), acc[q]);
         }
     }
 #pragma unroll
-    for (int g = 0; g < PG; ++g) unpack2(acc[g], r[2 * g], r[2 * g + 1]);
+    for (int q = 0; q < NC; ++q) r[q] = fold2(acc[q]);
 }
 
-// Generic width: the same operation sequence with a runtime d.
+// Generic width: the same definition with scalar operations and a runtime d.
 __device__ __forceinline__ float d2_gen(const float *x, const float *c, int d) {
-    float acc = 0.0f;
-    for (int j = 0; j < d; ++j) {
-        const float t = __fsub_rn(x[j], c[j]);
-        acc = __fmaf_rn(t, t, acc);
+    float e = 0.0f, o = 0.0f;
+    int j = 0;
+    for (; j + 1 < d; j += 2) {
+        const float t0 = __fsub_rn(x[j], c[j]);
+        const float t1 = __fsub_rn(x[j + 1], c[j + 1]);
+        e = __fmaf_rn(t0, t0, e);
+        o = __fmaf_rn(t1, t1, o);
     }
-    return acc;
+    if (j < d) {
+        const float t0 = __fsub_rn(x[j], c[j]);
+        e = __fmaf_rn(t0, t0, e);
+    }
+    return __fadd_rn(e, o);
 }
 
 // Upper bound on the exact distance whose square was computed as d2:

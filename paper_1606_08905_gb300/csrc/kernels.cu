@@ -171,20 +171,16 @@ __global__ void __launch_bounds__(NT) k_dense(const IterParams p, const int32_t 
             float bd = CUDART_INF_F;
             best = 0;
             if constexpr (DV > 0) {
-                float x[DV];
-#pragma unroll
-                for (int j = 0; j < DV; j += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(tl + tid * p.dpad + j);
-                    x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
-                }
+                unsigned long long x[DV / 2];
+                load_x2<DV>(x, tl + tid * p.dpad);
                 int c = 0;
                 for (; c + 4 <= k; c += 4) {
-                    float r0, r1, r2, r3;
-                    d2_reg4<DV>(x, cent + (size_t)c * DV, r0, r1, r2, r3);
-                    if (r0 < bd) { bd = r0; best = c; }
-                    if (r1 < bd) { bd = r1; best = c + 1; }
-                    if (r2 < bd) { bd = r2; best = c + 2; }
-                    if (r3 < bd) { bd = r3; best = c + 3; }
+                    float r[4];
+                    d2_regN<DV, 4>(x, cent + (size_t)c * DV, r);
+                    if (r[0] < bd) { bd = r[0]; best = c; }
+                    if (r[1] < bd) { bd = r[1]; best = c + 1; }
+                    if (r[2] < bd) { bd = r[2]; best = c + 2; }
+                    if (r[3] < bd) { bd = r[3]; best = c + 3; }
                 }
                 for (; c < k; ++c) {
                     const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
@@ -360,13 +356,8 @@ __global__ void __launch_bounds__(NT) k_mti(const IterParams p, const int32_t *m
                 int best;
                 float bd;
                 if constexpr (DV > 0) {
-                    float x[DV];
-                    const float4 *xr = reinterpret_cast<const float4 *>(p.X + i * DV);
-#pragma unroll
-                    for (int j = 0; j < DV / 4; ++j) {
-                        const float4 v = __ldg(xr + j);
-                        x[4 * j] = v.x; x[4 * j + 1] = v.y; x[4 * j + 2] = v.z; x[4 * j + 3] = v.w;
-                    }
+                    unsigned long long x[DV / 2];
+                    ldg_x2<DV>(x, p.X + i * DV);
                     if (a < 0) {
                         bd = CUDART_INF_F;
                         best = 0;
@@ -392,9 +383,9 @@ __global__ void __launch_bounds__(NT) k_mti(const IterParams p, const int32_t *m
                     }
                     if (best != a) {
                         float *dst = tile + tid * p.dpad;
+                        const float4 *src = reinterpret_cast<const float4 *>(p.X + i * DV);
 #pragma unroll
-                        for (int j = 0; j < DV; j += 4)
-                            *reinterpret_cast<float4 *>(dst + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                        for (int j = 0; j < DV; j += 4) *reinterpret_cast<float4 *>(dst + j) = __ldg(src + j / 4);
                     }
                 } else {
                     const float *xg = p.X + i * d;

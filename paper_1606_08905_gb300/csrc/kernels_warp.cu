@@ -194,14 +194,6 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     const Shared sh = stage_shared(p, sm, false);
-    // pair-major copy of the centroids for d2_pairs; an odd k repeats the last
-    float2 *cpair = reinterpret_cast<float2 *>(sm + p.off_halfD);
-    const int npair = (k + 1) / 2;
-    for (int e = tid; e < npair * DV; e += WT) {
-        const int g = e / DV, j = e % DV;
-        const int c0 = 2 * g, c1 = min(2 * g + 1, k - 1);
-        cpair[e] = make_float2(p.C32[(size_t)c0 * DV + j], p.C32[(size_t)c1 * DV + j]);
-    }
     __syncthreads();
     int64_t lo, hi;
     block_range(p.n, 1, lo, hi);
@@ -236,29 +228,22 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
         const bool valid = lane < rows;
         int best = -1;
         if (valid) {
-            unsigned long long xx[DV];
-#pragma unroll
-            for (int j = 0; j < DV; j += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(tl + lane * dpad + j);
-                xx[j] = pack2(v.x, v.x); xx[j + 1] = pack2(v.y, v.y);
-                xx[j + 2] = pack2(v.z, v.z); xx[j + 3] = pack2(v.w, v.w);
-            }
+            unsigned long long x2[DV / 2];
+            load_x2<DV>(x2, tl + lane * dpad);
             float bd = CUDART_INF_F;
             best = 0;
             int c = 0;
-            constexpr int PG = DV <= 32 ? 4 : 2;
-            for (; c + 2 * PG <= k; c += 2 * PG) {
-                float r[2 * PG];
-                d2_pairs<DV, PG>(xx, cpair + (size_t)(c / 2) * DV, r);
+            constexpr int NC = DV <= 32 ? 4 : 2;
+            for (; c + NC <= k; c += NC) {
+                float r[NC];
+                d2_regN<DV, NC>(x2, sh.cent + (size_t)c * DV, r);
 #pragma unroll
-                for (int q = 0; q < 2 * PG; ++q)
+                for (int q = 0; q < NC; ++q)
                     if (r[q] < bd) { bd = r[q]; best = c + q; }
             }
-            for (; c < k; c += 2) {
-                float r[2];
-                d2_pairs<DV, 1>(xx, cpair + (size_t)(c / 2) * DV, r);
-                if (r[0] < bd) { bd = r[0]; best = c; }
-                if (c + 1 < k && r[1] < bd) { bd = r[1]; best = c + 1; }
+            for (; c < k; ++c) {
+                const float r = d2_reg<DV>(x2, sh.cent + (size_t)c * DV);
+                if (r < bd) { bd = r; best = c; }
             }
             const int64_t i = base + lane;
             const PtState old = p.st[i];
@@ -407,18 +392,13 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
             int best = -1, a = -1;
             int64_t i = 0;
             bool changed = false;
-            float xk[DV];
+            unsigned long long xk[DV / 2];
             float bd = CUDART_INF_F, tst = 0.0f;
             if (lane < nb) {
                 const int2 e = queue[qhead + lane];
                 i = lo + e.x;
                 a = e.y < 0 ? -1 : e.y / p.ubins;
-                const float4 *xr = reinterpret_cast<const float4 *>(p.X + i * DV);
-#pragma unroll
-                for (int j = 0; j < DV / 4; ++j) {
-                    const float4 v = __ldg(xr + j);
-                    xk[4 * j] = v.x; xk[4 * j + 1] = v.y; xk[4 * j + 2] = v.z; xk[4 * j + 3] = v.w;
-                }
+                ldg_x2<DV>(xk, p.X + i * DV);
                 if (a < 0) {
                     best = 0;
                     for (int c = 0; c < k; ++c) {

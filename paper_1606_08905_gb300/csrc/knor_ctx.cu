@@ -231,9 +231,7 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.cent_smem = kd * 4 <= 32 * 1024 ? 1 : 0;
     p.off_cent = take(p.cent_smem ? kd * 4 : 0);
     p.halfD_smem = (mti && (size_t)k * k * 4 <= 16 * 1024) ? 1 : 0;
-    // dense: off_halfD holds the pair-major centroid copy instead
-    if (!mti && (size_t)(k + 1) * d * 4 > 32 * 1024) return 0;
-    p.off_halfD = take(mti ? (p.halfD_smem ? (size_t)k * k * 4 : 0) : (size_t)(k + 1) * d * 4);
+    p.off_halfD = take(p.halfD_smem ? (size_t)k * k * 4 : 0);
     const bool sf = (size_t)k * 8 <= 8 * 1024;
     p.off_s = sf ? take((size_t)k * 4) : -1;
     p.off_F = sf ? take((size_t)k * 4) : -1;
