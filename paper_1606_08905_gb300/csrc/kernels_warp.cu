@@ -15,10 +15,6 @@
 namespace knor {
 
 constexpr int WT = WPC * 32; // threads per CTA
-// Pair evaluation of the MTI scan: up to PAIR_WORDS * 32 centroids, up to
-// PAIR_CAP (point, centroid) pairs per batch of 32 points.
-constexpr int PAIR_WORDS = 4;
-constexpr int PAIR_CAP = 512;
 
 // Adds (sign = +1) or subtracts (sign = -1) the rows of the lanes with
 // has = true into the warp's accumulators, cluster cl of each lane.  Rows are
@@ -151,31 +147,24 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
-// Stages the CTA-shared tables; returns pointers (smem or global).
+// Stages the CTA-shared tables into shared memory.  The warp kernels are
+// only chosen when the centroids, the k x k table and s, F fit, so these
+// pointers always address shared memory (plain shared loads, no generic
+// address resolution in the inner loops).
 struct Shared {
     const float *cent, *halfD, *s, *F;
 };
 __device__ __forceinline__ Shared stage_shared(const IterParams &p, unsigned char *sm, bool need_table) {
-    Shared r{p.C32, p.halfD, p.s, p.F};
     const int kd = p.k * p.d;
-    if (p.cent_smem) {
-        float *cs = reinterpret_cast<float *>(sm + p.off_cent);
-        for (int e = threadIdx.x; e < kd; e += WT) cs[e] = p.C32[e];
-        r.cent = cs;
-    }
-    if (need_table && p.halfD_smem) {
-        float *hs = reinterpret_cast<float *>(sm + p.off_halfD);
+    float *cs = reinterpret_cast<float *>(sm + p.off_cent);
+    for (int e = threadIdx.x; e < kd; e += WT) cs[e] = p.C32[e];
+    float *hs = reinterpret_cast<float *>(sm + p.off_halfD);
+    if (need_table)
         for (int e = threadIdx.x; e < p.k * p.k; e += WT) hs[e] = p.halfD[e];
-        r.halfD = hs;
-    }
-    if (p.off_F >= 0) {
-        float *a1 = reinterpret_cast<float *>(sm + p.off_s);
-        float *a2 = reinterpret_cast<float *>(sm + p.off_F);
-        for (int c = threadIdx.x; c < p.k; c += WT) { a1[c] = p.s[c]; a2[c] = p.F[c]; }
-        r.s = a1;
-        r.F = a2;
-    }
-    return r;
+    float *a1 = reinterpret_cast<float *>(sm + p.off_s);
+    float *a2 = reinterpret_cast<float *>(sm + p.off_F);
+    for (int c = threadIdx.x; c < p.k; c += WT) { a1[c] = p.s[c]; a2[c] = p.F[c]; }
+    return Shared{cs, hs, a1, a2};
 }
 
 // ------------------------------------------------------------ dense scan
@@ -294,21 +283,10 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
     int2 *queue2 = queue + WQCAP;
     int *hist = reinterpret_cast<int *>(queue2 + WQCAP);
     PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
-    // pair evaluation: prefix of survivor counts, survivor masks, results
-    int *pref = reinterpret_cast<int *>(wr + p.w_tile);
-    unsigned *msk = reinterpret_cast<unsigned *>(pref + 33);
-    float *res = reinterpret_cast<float *>(msk + 32 * PAIR_WORDS);
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     const Shared sh = stage_shared(p, sm, true);
-    // centroid rows padded to DV + 4 floats, so that lanes reading different
-    // centroids hit different banks
-    constexpr int CST = DV + 4;
-    const bool pairs = p.pair_eval != 0;
-    float *centp = reinterpret_cast<float *>(sm + p.off_centp);
-    if (pairs)
-        for (int e = tid; e < k * DV; e += WT) centp[(e / DV) * CST + e % DV] = p.C32[e];
     __syncthreads();
     int64_t lo, hi;
     block_range(p.n, PA, lo, hi);
@@ -429,80 +407,11 @@ __global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t 
                 }
                 tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
             }
-            // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives.
-            bool done = false;
-            if (pairs) {
-                // each lane's survivors as bit masks; the (point, centroid)
-                // pairs are dealt 32 per round, every lane scoring one pair
-                // with the owning lane's point (shuffled in), and each owner
-                // then walks its own results in centroid order
-                unsigned mw[PAIR_WORDS];
-                int cntL = 0;
-#pragma unroll
-                for (int wd = 0; wd < PAIR_WORDS; ++wd) {
-                    mw[wd] = 0;
-                    if (lane < nb && a >= 0 && wd * 32 < k) {
-                        const float *hrow = sh.halfD + (size_t)a * k + wd * 32;
-                        const int lim = min(32, k - wd * 32);
-                        for (int bb = 0; bb < lim; ++bb)
-                            mw[wd] |= (!(tst < hrow[bb]) && wd * 32 + bb != a ? 1u : 0u) << bb;
-                    }
-                    cntL += __popc(mw[wd]);
-                }
-                int incl = cntL;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(FULL_MASK, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int excl = incl - cntL;
-                const int P = __shfl_sync(FULL_MASK, incl, 31);
-                if (P <= PAIR_CAP) {
-                    pref[lane] = excl;
-#pragma unroll
-                    for (int wd = 0; wd < PAIR_WORDS; ++wd) msk[lane * PAIR_WORDS + wd] = mw[wd];
-                    __syncwarp();
-                    for (int q0 = 0; q0 < P; q0 += 32) {
-                        const int q = q0 + lane;
-                        const bool v = q < P;
-                        int own = 0, c = 0;
-                        if (v) {
-#pragma unroll
-                            for (int st = 16; st > 0; st >>= 1)
-                                if (own + st < 32 && pref[own + st] <= q) own += st;
-                            int nth = q - pref[own];
-#pragma unroll
-                            for (int wd = 0; wd < PAIR_WORDS; ++wd) {
-                                const unsigned m = msk[own * PAIR_WORDS + wd];
-                                const int cn = __popc(m);
-                                if (nth >= 0 && nth < cn) c = wd * 32 + (int)__fns(m, 0, nth + 1);
-                                nth -= cn;
-                            }
-                        }
-                        unsigned long long xp[DV / 2];
-#pragma unroll
-                        for (int j = 0; j < DV / 2; ++j) xp[j] = __shfl_sync(FULL_MASK, xk[j], own);
-                        if (v) res[q] = d2_reg<DV>(xp, centp + (size_t)c * CST);
-                    }
-                    __syncwarp();
-                    my_evals += cntL;
-                    int t = excl;
-#pragma unroll
-                    for (int wd = 0; wd < PAIR_WORDS; ++wd) {
-                        unsigned m = mw[wd];
-                        while (m) {
-                            const int c = wd * 32 + __ffs(m) - 1;
-                            m &= m - 1;
-                            const float r = res[t++];
-                            if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
-                        }
-                    }
-                    done = true;
-                }
-            }
-            // otherwise: the warp walks the union of the lanes' survivors, in
-            // index order, and each lane scores its own
-            for (int cw = 0; cw < k && !done; cw += 32) {
+            // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives;
+            // each lane's survivors form a bit mask per 32 centroids, the warp
+            // walks the union of the masks in index order, and each lane
+            // scores its own survivors.
+            for (int cw = 0; cw < k; cw += 32) {
                 unsigned mask = 0;
                 if (lane < nb && a >= 0) {
                     const float *hrow = sh.halfD + (size_t)a * k + cw;

@@ -228,15 +228,14 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
         return (int32_t)o;
     };
     p.dpad = d + 4;
-    p.cent_smem = kd * 4 <= 32 * 1024 ? 1 : 0;
-    p.off_cent = take(p.cent_smem ? kd * 4 : 0);
-    p.halfD_smem = (mti && (size_t)k * k * 4 <= 16 * 1024) ? 1 : 0;
-    p.off_halfD = take(p.halfD_smem ? (size_t)k * k * 4 : 0);
-    p.pair_eval = (mti && k <= 128 && (size_t)k * (d + 4) * 4 <= 16 * 1024) ? 1 : 0;
-    p.off_centp = take(p.pair_eval ? (size_t)k * (d + 4) * 4 : 0);
-    const bool sf = (size_t)k * 8 <= 8 * 1024;
-    p.off_s = sf ? take((size_t)k * 4) : -1;
-    p.off_F = sf ? take((size_t)k * 4) : -1;
+    // the warp kernels keep every table in shared memory (else: CTA kernels)
+    if (kd * 4 > 32 * 1024 || (mti && (size_t)k * k * 4 > 16 * 1024) || (size_t)k * 8 > 8 * 1024) return 0;
+    p.cent_smem = 1;
+    p.off_cent = take(kd * 4);
+    p.halfD_smem = mti ? 1 : 0;
+    p.off_halfD = take(mti ? (size_t)k * k * 4 : 0);
+    p.off_s = take((size_t)k * 4);
+    p.off_F = take((size_t)k * 4);
     p.w_base = take(0);
     size_t woff = 0;
     auto wtake = [&](size_t bytes) -> int32_t {
@@ -247,8 +246,7 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.w_acc_hi = wtake(kd * 4);
     p.w_acc_lo = wtake(kd * 4);
     p.w_cnt = wtake((size_t)k * 4);
-    // dense: two row tiles; MTI: pair buffers (prefix 33, masks 32 x 4, results 512)
-    p.w_tile = wtake(mti ? (33 + 32 * 4 + 512) * 4 : 2 * 32 * (size_t)p.dpad * 4);
+    p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4); // dense: two row tiles
     p.sort_queue = (mti && k <= 1024) ? 1 : 0;
     p.ubins = k <= 128 ? 8 : 1;
     p.w_queue = wtake(mti ? 2 * WQCAP * sizeof(int2) + (p.sort_queue ? (size_t)k * p.ubins * 4 : 0) : 0);

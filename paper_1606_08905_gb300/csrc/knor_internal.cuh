@@ -89,8 +89,6 @@ struct IterParams {
     int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_queue, w_state;
     int32_t sort_queue;    // k_mti_w: sort each warp's queue by cluster (k <= 1024)
     int32_t ubins;         // k_mti_w: bins of u / s(a) in the sort key (1 = by cluster only)
-    int32_t pair_eval;     // k_mti_w: score (point, centroid) pairs (k <= 128), else the union walk
-    int32_t off_centp;     // k_mti_w: centroid copy with rows padded to d + 4 floats
 };
 
 // Parameters of the reduction / finalize kernels.
