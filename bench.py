@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--n", type=int, default=0, help="override the workload's n (profiling runs)")
     return ap.parse_args()
 
 
@@ -122,19 +123,29 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def csrc_sha256() -> str:
+    """Hash of every CUDA source and header of the library."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1606_08905_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
 def ncu_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    kernel source has not changed since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    """Per-launch DRAM bytes of `kernel` (scaled to this workload) from the
+    committed ncu summary profiles/<kernel>_<workload>.md, if the CUDA sources
+    have not changed since the capture (else None)."""
+    base = re.sub(r"[<>]", "", kernel)
+    path = os.path.join(ROOT, "profiles", f"{base}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"kernels_cu_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h:
-        return None
-    src = os.path.join(ROOT, "paper_1606_08905_gb300", "csrc", "kernels.cu")
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+    h = re.search(r"csrc_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != csrc_sha256():
         return None
     return float(m.group(1))
 
@@ -199,8 +210,13 @@ def reference_arm(args, wl, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def synth_n(name):
+    from paper_1606_08905_gb300 import synth
+    return synth.WORKLOADS[name]["n"]
+
+
 def config_of(wl, name, world):
-    return {"workload": name, "n": wl["n"], "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
+    return {"workload": name if wl["n"] == synth_n(name) else f"{name} (n overridden)", "n": wl["n"], "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
             "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42",
             "data_seed": wl["data_seed"], "points_dtype": "f32",
             "l2": f"inputs larger than L2 ({wl['n'] * wl['d'] * 4 / 1e9:.2f} GB of points)",
@@ -290,11 +306,13 @@ def our_arm(args, wl, world, rank, local):
                          "frac_of_" + peak_src + "_hbm": gbs / peaks["hbm_gbs"]}
     total_prof_ms = sum(v[1] for v in prof.values())
     dom = max(kernels, key=lambda kk: kernels[kk]["ms_total"])
-    kname = {"dense": "k_dense", "mti": "k_mti"}[dom]
-    roof = {"kernel": f"{kname}<{d}>", "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"],
+    kname = ctx.kernel_name(dom)
+    for kk in kernels:
+        kernels[kk]["kernel"] = ctx.kernel_name(kk)
+    roof = {"kernel": kname, "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"],
             "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
             "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"],
-            "traffic": ncu_traffic(kname, args.workload),
+            "traffic": ncu_traffic(kname, args.workload) if not args.n else None,
             "share_of_kernel_time": kernels[dom]["ms_total"] / total_prof_ms}
 
     # ---- plain FP32 Lloyd on the same points: speed, and identical assignments
@@ -380,7 +398,9 @@ def main():
     from paper_1606_08905_gb300 import synth
     if args.workload not in synth.WORKLOADS:
         raise SystemExit(f"unknown workload {args.workload}; one of {sorted(synth.WORKLOADS)}")
-    wl = synth.WORKLOADS[args.workload]
+    wl = dict(synth.WORKLOADS[args.workload])
+    if args.n:
+        wl["n"] = args.n
     if args.impl == "reference":
         reference_arm(args, wl, world, rank)
         return

@@ -157,6 +157,10 @@ typedef struct {
     double ms[KNOR_KERNEL_COUNT];
 } knor_profile;
 knor_status knor_set_profiling(knor_ctx *ctx, int32_t on);
+/* Name of the CUDA kernel that implements `kernel` (a knor_kernel) for this
+ * context, e.g. "k_mti_w<32>": the variant chosen from d and the shared-memory
+ * footprint of k x d.  Valid for the context's lifetime; "" for bad input. */
+const char *knor_kernel_name(const knor_ctx *ctx, int32_t kernel);
 knor_status knor_get_profile(knor_ctx *ctx, knor_profile *out, int32_t reset_after);
 
 /* Checkpoint.  knor_get_state with buf == NULL stores the needed size in

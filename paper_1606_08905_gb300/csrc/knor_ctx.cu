@@ -118,6 +118,7 @@ struct knor_ctx {
     std::vector<cudaEvent_t> ev;
     knor_profile prof{};
     int32_t host_total_iter = 0;
+    std::string kname[KNOR_KERNEL_COUNT];
 };
 
 static thread_local std::string g_create_err;
@@ -569,6 +570,13 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     c->ip_dense.part_stride = c->part_stride;
     c->ip_mti.part_stride = c->part_stride;
     c->ip_dense.acc_global = c->ip_mti.acc_global = acc_global;
+    {
+        const std::string w = "<" + std::to_string(c->dv) + ">";
+        c->kname[KNOR_KERNEL_DENSE] = (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
+        c->kname[KNOR_KERNEL_MTI] = (c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
+        c->kname[KNOR_KERNEL_REDUCE] = "k_reduce";
+        c->kname[KNOR_KERNEL_TABLE] = "k_table";
+    }
     FinParams &f = c->fp;
     f.part_S = c->part_S; f.part_cnt = c->part_cnt; f.part_stride = c->part_stride;
     f.k = k; f.d = d;
@@ -673,6 +681,11 @@ knor_status knor_run(knor_ctx *c, int32_t max_iters, int32_t *iters_done, knor_i
     c->host_total_iter += done;
     if (iters_done) *iters_done = done;
     return read_stats(c, done, per_iter);
+}
+
+const char *knor_kernel_name(const knor_ctx *c, int32_t kernel) {
+    if (!c || kernel < 0 || kernel >= KNOR_KERNEL_COUNT) return "";
+    return c->kname[kernel].c_str();
 }
 
 knor_status knor_set_profiling(knor_ctx *c, int32_t on) {

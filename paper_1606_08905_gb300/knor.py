@@ -67,6 +67,7 @@ _SIGS = {
     "knor_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "knor_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "knor_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "knor_kernel_name": (ctypes.c_char_p, [ctypes.c_void_p, ctypes.c_int32]),
     "knor_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int32]),
     "knor_lloyd_step_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -211,6 +212,10 @@ class Context:
         v = ctypes.c_int32(0)
         _check(load().knor_get_iteration(self._ctx, ctypes.byref(v)), self._ctx)
         return int(v.value)
+
+    def kernel_name(self, kernel: str) -> str:
+        """The CUDA kernel behind 'dense', 'mti', 'reduce' or 'table'."""
+        return load().knor_kernel_name(self._ctx, KERNELS.index(kernel)).decode()
 
     def set_profiling(self, on: bool):
         _check(load().knor_set_profiling(self._ctx, 1 if on else 0), self._ctx)
