@@ -164,11 +164,19 @@ def cpu_oracle_run(Xs, k, max_iters, prune, threads):
     return Xs.shape[0] * r.iters, dt, r.iters
 
 
-def cpu_sample_rows(wl, seconds):
-    # the FP64 oracle does ~4e7 MTI point-iterations/s or ~1.4e7 plain on 8 x86 cores
-    rate = 2.0e7 if wl["prune"] else 0.7e7
-    per_run = rate * seconds / wl["max_iters"]
-    return int(max(20_000, min(wl["n"], per_run)))
+def cpu_sample_rows(wl, seconds, X=None, threads=1):
+    """Rows of the workload that the FP64 oracle runs through in about
+    `seconds`, from a short probe run on the first rows (or the workload's
+    distribution drawn on the CPU when X is None)."""
+    probe = int(min(wl["n"], 200_000))
+    if X is not None:
+        Xp = X[:probe].cpu().numpy()
+    else:
+        from paper_1606_08905_gb300 import synth
+        Xp = synth.make(wl["kind"], probe, wl["d"], wl["k"], wl["data_seed"], device="cpu").numpy()
+    p, dt, _ = cpu_oracle_run(Xp, wl["k"], wl["max_iters"], wl["prune"], threads)
+    rate = p / max(dt, 1e-3)
+    return int(max(20_000, min(wl["n"], rate * seconds / wl["max_iters"])))
 
 
 def reference_arm(args, wl, world, rank):
@@ -183,7 +191,7 @@ def reference_arm(args, wl, world, rank):
     threads = os.cpu_count() or 1
     total_budget = 150.0
     per_step = max(2.0, total_budget / max(1, args.steps + args.warmup))
-    ns = cpu_sample_rows(wl, per_step)
+    ns = cpu_sample_rows(wl, per_step, None, threads)
     Xs = synth.make(wl["kind"], ns, wl["d"], wl["k"], wl["data_seed"], device="cpu").numpy()
     for _ in range(args.warmup):
         cpu_oracle_run(Xs, wl["k"], wl["max_iters"], wl["prune"], threads)
@@ -373,7 +381,7 @@ def our_arm(args, wl, world, rank, local):
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         threads = os.cpu_count() or 1
-        ns = cpu_sample_rows(wl, args.cpu_seconds)
+        ns = cpu_sample_rows(wl, args.cpu_seconds, X, threads)
         Xs = X[:ns].cpu().numpy()
         p, dt, it = cpu_oracle_run(Xs, k, T, wl["prune"], threads)
         cpu = {"value": p / dt, "unit": "point-iterations/s", "cores": threads, "kind": "oracle",
@@ -386,7 +394,10 @@ def our_arm(args, wl, world, rank, local):
                 "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(wl, args.workload, world),
-                "iterations_per_step": iters, "roofline": roof, "kernels": kernels,
+                "iterations_per_step": iters,
+                "active_fraction_per_iteration": [round(1.0 - r["clause1_skipped"] / n, 4)
+                                                  for r in prof_recs[:prof_iters[0]]] if wl["prune"] else None,
+                "roofline": roof, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "vs_plain_fp32": plain,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
