@@ -9,6 +9,9 @@
 #include "knor.h"
 #include "knor_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -26,7 +29,7 @@ constexpr uint32_t kStateMagic = 0x4b4e4f52u; // "KNOR"
 constexpr uint32_t kStateVersion = 1;
 
 // Device flags (int32 each).
-enum Flag { F_RUN_ITER = 0, F_TOTAL_ITER, F_MAX_ITERS, F_MODE_DENSE, F_NSLOTS, F_FRESH, F_COUNT };
+enum Flag { F_RUN_ITER = 0, F_TOTAL_ITER, F_MAX_ITERS, F_MODE_DENSE, F_NSLOTS, F_FRESH, F_ERR, F_COUNT };
 
 // SplitMix64 (Steele, Lea and Flood 2014): golden-ratio increment, then the
 // published finaliser.
@@ -113,6 +116,17 @@ struct knor_ctx {
 
     cudaGraphExec_t iter_exec = nullptr, run_exec = nullptr;
 
+    // precision form (BF16 tensor-core distances + exact FP32 recheck)
+    bool prec = false;
+    void *Xb = nullptr, *Cb = nullptr;
+    float *xn = nullptr, *cn = nullptr, *cmax = nullptr;
+    int32_t *a_next = nullptr, *rlist = nullptr;
+    unsigned *rcount = nullptr;
+    alignas(64) unsigned char tmX[128] = {}, tmC[128] = {}; // CUtensorMap
+    PrecParams pp{};
+    int prec_grid = 0;
+    size_t prec_smem = 0;
+
     // profiling (host-driven loop, CUDA events around every kernel)
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
@@ -160,12 +174,38 @@ static void free_all(knor_ctx *c) {
     c->ev.clear();
     if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
     if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
-    void *bufs[] = {c->X, c->st, c->C0, c->C64, c->S, c->part_S, c->C32, c->C32n, c->halfD, c->s,
-                    c->F, c->cnt, c->cnt_next, c->part_cnt, c->ctr, c->stats, c->flags, c->d_idx, c->d_bad};
+    void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
+                    c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
+                    c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->cmax,
+                    c->a_next, c->rlist,  c->rcount};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+// A 2-D TMA descriptor over a row-major rows x inner BF16 matrix, boxes of
+// 64 columns (128 bytes) x box_rows rows, 128-byte swizzle, zero fill outside.
+static knor_status encode_bf16_map(knor_ctx *c, void *out, void *base, uint64_t inner, uint64_t rows,
+                                   uint32_t box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q{};
+        void *f = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+            return fail(c, KNOR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(static_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, KNOR_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return KNOR_OK;
 }
 
 // Shared-memory layout of a point kernel; returns the byte size.
@@ -303,7 +343,40 @@ static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
                       fl + F_FRESH);
 }
 
+// The precision form's iteration: BF16 centroids, tensor-core scan with
+// certification, exact FP32 re-score of the rest, delta sums, merge, table.
+// With events != nullptr each stage is bracketed by CUDA events (profiling).
+static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long cond, cudaEvent_t *ev) {
+    int32_t *fl = c->flags;
+    auto mark = [&](int i) -> cudaError_t { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
+    KNOR_CUDA(c, cudaMemsetAsync(c->rcount, 0, sizeof(unsigned), s));
+    KNOR_CUDA(c, mark(0));
+    KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->Cb, c->cn, c->cmax, s));
+    KNOR_CUDA(c, prec_assign(c->tmX, c->tmC, c->pp, c->prec_grid, c->prec_smem, s));
+    KNOR_CUDA(c, mark(1));
+    KNOR_CUDA(c, mark(8));
+    KNOR_CUDA(c, prec_recheck(c->dv, c->X, c->C32, c->k, c->rlist, c->rcount, c->a_next, c->ctr, 4 * c->num_sms, s));
+    KNOR_CUDA(c, mark(9));
+    KNOR_CUDA(c, mark(10));
+    KNOR_CUDA(c, prec_delta_sums(c->X, c->n, c->d, c->st, c->a_next, c->part_S, c->part_cnt, c->ctr, c->k,
+                                 fl + F_NSLOTS, fl + F_FRESH, 8 * c->num_sms, s));
+    KNOR_CUDA(c, mark(11));
+    KNOR_CUDA(c, mark(4));
+    KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
+    KNOR_CUDA(c, mark(5));
+    FinParams f = c->fp;
+    f.snapshot = 1;
+    f.cond_handle = cond;
+    KNOR_CUDA(c, mark(6));
+    KNOR_CUDA(c, launch_table(f, fl + F_MODE_DENSE, 0, 0, 1, s));
+    KNOR_CUDA(c, mark(7));
+    return KNOR_OK;
+}
+
 static knor_status enqueue_iteration(knor_ctx *c, cudaStream_t s, unsigned long long cond) {
+    if (c->prec) return enqueue_prec(c, s, cond, nullptr);
     int32_t *fl = c->flags;
     if (c->ip_dense.acc_global) { // one slot, accumulated by atomics: start from zero
         KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
@@ -332,10 +405,26 @@ static knor_status profiled_iteration(knor_ctx *c) {
         c->ev.resize(2 * KNOR_KERNEL_COUNT);
         for (auto &e : c->ev) KNOR_CUDA(c, cudaEventCreate(&e));
     }
+    if (c->prec) {
+        knor_status st = enqueue_prec(c, s, 0, c->ev.data());
+        if (st != KNOR_OK) return st;
+        KNOR_CUDA(c, cudaStreamSynchronize(s));
+        const int kinds[] = {KNOR_KERNEL_DENSE, KNOR_KERNEL_RECHECK, KNOR_KERNEL_SUMS, KNOR_KERNEL_REDUCE,
+                             KNOR_KERNEL_TABLE};
+        const int evs[] = {0, 8, 10, 4, 6};
+        for (int q = 0; q < 5; ++q) {
+            float ms = 0.0f;
+            KNOR_CUDA(c, cudaEventElapsedTime(&ms, c->ev[evs[q]], c->ev[evs[q] + 1]));
+            c->prof.ms[kinds[q]] += ms;
+            c->prof.launches[kinds[q]] += 1;
+        }
+        c->host_total_iter += 1;
+        return KNOR_OK;
+    }
     const int m = c->opts.full_recompute_every;
     const int tot = c->host_total_iter;
     const bool dense = c->opts.no_prune || tot == 0 || (m > 0 && (tot + 1) % m == 0);
-    bool used[KNOR_KERNEL_COUNT] = {false, false, false, false};
+    bool used[KNOR_KERNEL_COUNT] = {};
     if (c->ip_dense.acc_global) {
         KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
         KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
@@ -437,7 +526,7 @@ static knor_status reset_run(knor_ctx *c) {
     KNOR_CUDA(c, cudaMemsetAsync(c->F, 0, (size_t)c->k * sizeof(float), s));
     KNOR_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
     KNOR_CUDA(c, launch_init_state(c->st, c->n, s));
-    int32_t fl[F_COUNT] = {0, 0, 1, 1, 1, 1};
+    int32_t fl[F_COUNT] = {0, 0, 1, 1, 1, 1, 0};
     KNOR_CUDA(c, cudaMemcpyAsync(c->flags, fl, sizeof(fl), cudaMemcpyHostToDevice, s));
     c->host_total_iter = 0;
     // tables for C^0 (drift 0, no record)
@@ -482,8 +571,12 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     if (init != KNOR_INIT_FORGY && init != KNOR_INIT_EXPLICIT) { g_create_err = "knor_create: bad init"; return KNOR_ERR_ARG; }
     knor_opts o{};
     if (opts) o = *opts;
-    if (o.precision != KNOR_PREC_FP32) {
-        g_create_err = "knor_create: this build implements precision KNOR_PREC_FP32 only";
+    if (o.precision != KNOR_PREC_FP32 && o.precision != KNOR_PREC_BF16) {
+        g_create_err = "knor_create: precision must be KNOR_PREC_FP32 or KNOR_PREC_BF16 (the FP8 variant is not built)";
+        return KNOR_ERR_ARG;
+    }
+    if (o.precision == KNOR_PREC_BF16 && ((d != 64 && d != 128) || k > 8192)) {
+        g_create_err = "knor_create: the BF16 tensor-core form needs d = 64 or 128 and k <= 8192";
         return KNOR_ERR_ARG;
     }
     if (o.full_recompute_every < 0) { g_create_err = "knor_create: full_recompute_every < 0"; return KNOR_ERR_ARG; }
@@ -550,7 +643,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     // Both scans use the same accumulation mode: per-CTA partial slots, or,
     // when k x d sums do not fit in shared memory, one slot updated by FP64
     // atomics.
-    const int acc_global = (c->ip_dense.acc_global || c->ip_mti.acc_global) ? 1 : 0;
+    const int acc_global = (c->ip_dense.acc_global || c->ip_mti.acc_global || o.precision == KNOR_PREC_BF16) ? 1 : 0;
     if (acc_global && (c->ip_dense.warp_kernels || c->ip_mti.warp_kernels)) {
         // the warp kernels always write per-CTA slots: use the CTA kernels for both
         c->ip_dense = IterParams{};
@@ -585,6 +678,35 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     f.run_iter = c->flags + F_RUN_ITER; f.total_iter = c->flags + F_TOTAL_ITER;
     f.max_iters_dev = c->flags + F_MAX_ITERS;
 
+    if (o.precision == KNOR_PREC_BF16) {
+        // The precision form scans every point each iteration (no MTI bounds):
+        // its sums move by deltas through partial slot 0.
+        c->prec = true;
+        c->opts.no_prune = 1;
+        KC(dalloc(c, (uint16_t **)&c->Xb, nd));
+        KC(dalloc(c, (uint16_t **)&c->Cb, kd));
+        KC(dalloc(c, &c->xn, (size_t)n));
+        KC(dalloc(c, &c->cn, (size_t)k));
+        KC(dalloc(c, &c->cmax, 1));
+        KC(dalloc(c, &c->a_next, (size_t)n));
+        KC(dalloc(c, &c->rlist, (size_t)n));
+        KC(dalloc(c, &c->rcount, 1));
+        KCU(prec_points(c->X, n, d, c->Xb, c->xn, c->stream));
+        KC(encode_bf16_map(c, c->tmX, c->Xb, (uint64_t)d, (uint64_t)n, 128));
+        KC(encode_bf16_map(c, c->tmC, c->Cb, (uint64_t)d, (uint64_t)k, 256));
+        c->prec_smem = prec_smem_bytes(d, k);
+        KCU(prec_assign_attr(c->prec_smem));
+        const int64_t ntile = (n + 127) / 128;
+        c->prec_grid = (int)std::min<int64_t>(c->num_sms, ntile);
+        PrecParams &pp = c->pp;
+        pp.n = n; pp.d = d; pp.k = k; pp.xn = c->xn; pp.cn = c->cn; pp.cmax = c->cmax;
+        pp.a_next = c->a_next; pp.rlist = c->rlist; pp.rcount = c->rcount;
+        prec_error_constants(d, &pp.eA, &pp.eB);
+        pp.err = c->flags + F_ERR;
+        c->kname[KNOR_KERNEL_DENSE] = "k_bf16_assign";
+        c->kname[KNOR_KERNEL_RECHECK] = "k_recheck<" + std::to_string(c->dv) + ">";
+        c->kname[KNOR_KERNEL_SUMS] = "k_delta_sums";
+    }
     // C^0
     if (init == KNOR_INIT_FORGY) {
         c->init_idx = forgy_indices(n, k, seed);
@@ -625,7 +747,23 @@ knor_status knor_reset(knor_ctx *c) {
     return reset_run(c);
 }
 
+// A bounded device-side wait that gave up leaves F_ERR set.
+static knor_status check_timeout(knor_ctx *c) {
+    int32_t err = 0;
+    KNOR_CUDA(c, cudaMemcpy(&err, c->flags + F_ERR, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        cudaMemsetAsync(c->flags + F_ERR, 0, sizeof(int32_t), c->stream);
+        cudaStreamSynchronize(c->stream);
+        return fail(c, KNOR_ERR_TIMEOUT, "a device-side wait timed out (results of this iteration are invalid)");
+    }
+    return KNOR_OK;
+}
+
 static knor_status read_stats(knor_ctx *c, int count, knor_iter_stats *out) {
+    if (c->prec) {
+        knor_status st = check_timeout(c);
+        if (st != KNOR_OK) return st;
+    }
     if (count <= 0 || !out) return KNOR_OK;
     KNOR_CUDA(c, cudaMemcpyAsync(c->h_stats, c->stats, sizeof(IterStats) * count, cudaMemcpyDeviceToHost, c->stream));
     KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -818,7 +956,7 @@ knor_status knor_set_state(knor_ctx *c, const void *buf, size_t size) {
         KNOR_CUDA(c, cudaMemcpyAsync(pt.dst, p, pt.bytes, cudaMemcpyHostToDevice, c->stream));
         p += pt.bytes;
     }
-    int32_t fl[F_COUNT] = {0, h.total_iter, 1, h.mode_dense, 1, 1};
+    int32_t fl[F_COUNT] = {0, h.total_iter, 1, h.mode_dense, 1, 1, 0};
     c->host_total_iter = h.total_iter;
     KNOR_CUDA(c, cudaMemcpyAsync(c->flags, fl, sizeof(fl), cudaMemcpyHostToDevice, c->stream));
     KNOR_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(Counters), c->stream));

@@ -114,6 +114,20 @@ struct FinParams {
     unsigned long long cond_handle; // cudaGraphConditionalHandle, 0 if none
 };
 
+// Parameters of the precision-form assignment (precision.cu).
+struct PrecParams {
+    int64_t n;
+    int32_t d, k;
+    const float *xn;     // n: ||x||^2 (FP64 sum rounded to FP32)
+    const float *cn;     // k: ||c||^2
+    const float *cmax;   // max ||c|| rounded up
+    int32_t *a_next;     // n: new assignment of certified points
+    int32_t *rlist;      // points to re-score exactly
+    unsigned *rcount;
+    float eA, eB;        // E(x) = eA |x| Cmax + eB (|x|^2 + Cmax^2), rounded up
+    int32_t *err;        // set when a bounded wait gives up
+};
+
 // Launchers implemented in kernels.cu.
 // mode_dense selects which scan runs (the other returns at once); the scan
 // that runs records how many partial slots it wrote and whether the sums are
@@ -145,5 +159,19 @@ cudaError_t launch_check_bounds(const float *X, int64_t n, int32_t d, const PtSt
                                 const int32_t *run_iter, cudaStream_t s);
 int supported_dv(int d); // template width used for d (0 = generic)
 void set_global_error(const char *msg); // message for knor_last_error(NULL)
+
+// precision form (precision.cu)
+size_t prec_smem_bytes(int d, int k);
+cudaError_t prec_points(const float *X, int64_t n, int32_t d, void *Xb, float *xn, cudaStream_t s);
+cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, void *Cb, float *cn, float *cmax, cudaStream_t s);
+cudaError_t prec_assign_attr(size_t smem);
+// tmX / tmC point to CUtensorMap objects (cuda.h) over the BF16 points / centroids
+cudaError_t prec_assign(const void *tmX, const void *tmC, const PrecParams &p, int grid, size_t smem, cudaStream_t s);
+void prec_error_constants(int d, float *eA, float *eB);
+cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
+                         const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid, cudaStream_t s);
+cudaError_t prec_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next, double *S,
+                            long long *cnt, Counters *ctr, int32_t k, int32_t *nslots, int32_t *fresh, int grid,
+                            cudaStream_t s);
 
 } // namespace knor

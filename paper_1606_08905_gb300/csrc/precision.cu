@@ -1,0 +1,515 @@
+// precision.cu -- the precision form of the assignment step (BF16 tensor
+// cores with an exact FP32 recheck).
+//
+// The distance block d~^2(x, c) = ||x||^2 - 2 x~.c~ + ||c||^2 is formed with
+// x~, c~ the BF16 roundings of the FP32 point and centroid: the dot products
+// run on the 5th-generation tensor cores (tcgen05.mma, kind::f16, BF16 x BF16
+// -> FP32 in tensor memory), fed by TMA tiles in 128-byte-swizzled shared
+// memory.  The epilogue keeps each point's smallest and second smallest d~^2
+// over all centroids.  A point whose gap min2 - min1 exceeds 2 E(x) -- E(x)
+// bounds the BF16 error of d~^2 plus the error of the library's FP32 distance
+// (prec_error_constants below) -- provably has the same nearest centroid under
+// the FP32 distance of the plain path; every other point is re-scored exactly
+// in FP32 over all centroids.  The assignments are therefore identical to the
+// plain FP32 path's.  The cluster sums are then updated by the deltas of the
+// points that changed cluster.
+//
+// The paper has no GEMM path (its serial baseline table notes that GEMM codes
+// were slower on its CPUs); this form is an addition for the tensor cores.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "device_common.cuh"
+#include "knor_internal.cuh"
+
+namespace knor {
+
+// ------------------------------------------------------------ primitives
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after about a second (or as
+// soon as another role has flagged an error), sets *err and returns false.
+// No wait in these kernels can spin forever.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*reinterpret_cast<volatile int32_t *>(err)) return false;
+        if (clock64() - t0 > 2000000000LL) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int c0, int c1, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored by TMA
+// with 128-byte swizzling: rows of 128 bytes (64 BF16), 8-row atoms of 1024
+// bytes.  Fields: start address >> 4 (bits 0-13), leading byte offset >> 4
+// (16-29; unused for this layout, 1), stride byte offset >> 4 (32-45: 1024 B
+// between 8-row atoms), the fixed descriptor version 0b001 (46-48), base
+// offset 0 (atoms are 1024-aligned), layout type 2 = 128-byte swizzle (61-63).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A BF16 (7-9 = 1), B BF16 (10-12 = 1), both K-major (15, 16 = 0),
+// N >> 3 (17-22), M >> 4 (24-28).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- layout
+
+constexpr int TM = 128;              // points per tile (MMA M)
+constexpr int TN = 256;              // centroids per chunk (MMA N)
+constexpr int TKB = 64;              // BF16 elements per 128-byte row of a TMA box
+constexpr int A_BOX = TM * 128;      // bytes of one A box (16 KB)
+constexpr int B_BOX = TN * 128;      // bytes of one B box (32 KB)
+constexpr int PREC_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int TMEM_COLS = 2 * TN;    // two accumulator buffers
+
+size_t prec_smem_bytes(int d, int k) {
+    const int nkc = d / TKB;
+    return 1024 /* alignment */ + 2 * (size_t)nkc * A_BOX + 2 * (size_t)nkc * B_BOX + (size_t)k * 4 + 16 +
+           16 * 8 + 16;
+}
+
+// ------------------------------------------------------------- the kernel
+
+// Persistent: one CTA per SM walks point tiles blockIdx.x, +gridDim.x, ...;
+// per tile, ceil(k / 256) centroid chunks.  Warp 0 (one lane) issues TMA
+// loads of point tiles (two stages) and centroid chunks (two stages); warp 1
+// allocates 512 TMEM columns and one lane issues the MMAs into two
+// accumulator buffers; warps 2-5 read a finished buffer (one TMEM lane per
+// point) while the next chunk is being multiplied.
+__global__ void __launch_bounds__(PREC_THREADS, 1)
+    k_bf16_assign(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC,
+                  const PrecParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int nkc = p.d / TKB;
+    unsigned char *sA = sm;                                  // [2][nkc][A_BOX]
+    unsigned char *sB = sA + 2 * (size_t)nkc * A_BOX;        // [2][nkc][B_BOX]
+    float *cn_s = reinterpret_cast<float *>(sB + 2 * (size_t)nkc * B_BOX);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(cn_s + p.k + ((4 - (p.k & 3)) & 3)); // 16-byte aligned
+    uint64_t *fullA = bars, *emptyA = bars + 2, *fullB = bars + 4, *emptyB = bars + 6;
+    uint64_t *tfull = bars + 8, *tempty = bars + 10, *done = bars + 12;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 13);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntile = (p.n + TM - 1) / TM;
+    const int nchunk = (p.k + TN - 1) / TN;
+
+    for (int c = threadIdx.x; c < p.k; c += PREC_THREADS) cn_s[c] = p.cn[c];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&fullA[i], 1);
+            mbar_init(&emptyA[i], 1);
+            mbar_init(&fullB[i], 1);
+            mbar_init(&emptyB[i], 1);
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4); // one arrive per epilogue warp
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(tmem_holder);
+
+    // Ring bookkeeping: the u-th use of a ring slot waits for the (u-1)-th
+    // completion of its "empty" barrier (parity (u-1)&1); the consumer's u-th
+    // wait on a "full" barrier uses parity u&1.
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t ia = 0, ib = 0; // loads issued into ring A, ring B
+            for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+                const int sa = ia & 1;
+                if ((ia >> 1) >= 1 && !mbar_wait(&emptyA[sa], ((ia >> 1) - 1) & 1, p.err)) break;
+                mbar_expect_tx(&fullA[sa], (uint32_t)(nkc * A_BOX));
+                for (int kc = 0; kc < nkc; ++kc)
+                    tma_load_2d(sA + ((size_t)sa * nkc + kc) * A_BOX, &tmX, kc * TKB, (int)(t * TM), &fullA[sa]);
+                ++ia;
+                bool ok = true;
+                for (int j = 0; j < nchunk; ++j) {
+                    const int sb = ib & 1;
+                    if ((ib >> 1) >= 1 && !mbar_wait(&emptyB[sb], ((ib >> 1) - 1) & 1, p.err)) { ok = false; break; }
+                    mbar_expect_tx(&fullB[sb], (uint32_t)(nkc * B_BOX));
+                    for (int kc = 0; kc < nkc; ++kc)
+                        tma_load_2d(sB + ((size_t)sb * nkc + kc) * B_BOX, &tmC, kc * TKB, j * TN, &fullB[sb]);
+                    ++ib;
+                }
+                if (!ok) break;
+            }
+            // drain: the latest fill of each slot must land before the CTA exits
+            for (uint32_t q = ia >= 2 ? ia - 2 : 0; q < ia; ++q) mbar_wait(&fullA[q & 1], (q >> 1) & 1, p.err);
+            for (uint32_t q = ib >= 2 ? ib - 2 : 0; q < ib; ++q) mbar_wait(&fullB[q & 1], (q >> 1) & 1, p.err);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(TM, TN);
+            uint32_t ca = 0, cb = 0, cbuf = 0; // consumed A fills, B fills, accumulators issued
+            for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+                const int sa = ca & 1;
+                if (!mbar_wait(&fullA[sa], (ca >> 1) & 1, p.err)) break;
+                tc_fence_after();
+                bool ok = true;
+                for (int j = 0; j < nchunk; ++j) {
+                    const int sb = cb & 1, buf = cbuf & 1;
+                    if (!mbar_wait(&fullB[sb], (cb >> 1) & 1, p.err)) { ok = false; break; }
+                    if ((cbuf >> 1) >= 1 && !mbar_wait(&tempty[buf], ((cbuf >> 1) - 1) & 1, p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t dcol = tmem_base + (uint32_t)(buf * TN);
+                    for (int kc = 0; kc < nkc; ++kc) {
+                        const uint32_t a0 = smem_u32(sA + ((size_t)sa * nkc + kc) * A_BOX);
+                        const uint32_t b0 = smem_u32(sB + ((size_t)sb * nkc + kc) * B_BOX);
+                        for (int kk = 0; kk < TKB / 16; ++kk)
+                            mma_bf16(dcol, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                     (kc | kk) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(&emptyB[sb]); // B slot free once these MMAs are done
+                    mma_commit(&tfull[buf]); // accumulator ready for the epilogue
+                    ++cb;
+                    ++cbuf;
+                }
+                if (!ok) break;
+                mma_commit(&emptyA[sa]); // A slot free after the tile's last chunk
+                ++ca;
+            }
+            // every MMA issued by this thread completes before TMEM is freed
+            mma_commit(done);
+            mbar_wait(done, 0, p.err);
+        }
+    } else {
+        // -------------------------------------------------------- epilogue
+        const int q = warp & 3;       // TMEM lane quarter this warp may access
+        const int rloc = 32 * q + lane;
+        uint32_t cons = 0; // accumulators consumed
+        for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+            const int64_t row = t * TM + rloc;
+            const bool valid = row < p.n;
+            const float xn = valid ? p.xn[row] : 0.0f;
+            float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+            int i1 = 0;
+            bool ok = true;
+            for (int j = 0; j < nchunk; ++j) {
+                // lane 0 waits, the warp follows its outcome (the TMEM loads
+                // below are warp-synchronous)
+                int okw = 1;
+                if (lane == 0) okw = mbar_wait(&tfull[cons & 1], (cons >> 1) & 1, p.err) ? 1 : 0;
+                okw = __shfl_sync(FULL_MASK, okw, 0);
+                if (!okw) { ok = false; break; }
+                tc_fence_after();
+                const int buf = cons & 1;
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TN);
+                const int cbase = j * TN;
+                for (int cc = 0; cc < TN; cc += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)cc, r);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const int c = cbase + cc + u;
+                        if (c < p.k) {
+                            const float dd = __fmaf_rn(-2.0f, __uint_as_float(r[u]), __fadd_rn(xn, cn_s[c]));
+                            if (dd < m1) { m2 = m1; m1 = dd; i1 = c; }
+                            else if (dd < m2) { m2 = dd; }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+                ++cons;
+            }
+            if (!ok) break;
+            if (valid) {
+                // certified when the gap exceeds twice the error bound E(x)
+                const float X = __fsqrt_ru(fmaxf(xn, 0.0f));
+                const float C = *p.cmax;
+                const float E = __fmaf_ru(p.eA, __fmul_ru(X, C), __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C))));
+                if (__fsub_rd(m2, m1) > __fmul_ru(2.0f, E)) {
+                    p.a_next[row] = i1;
+                } else {
+                    const unsigned slot = atomicAdd(p.rcount, 1u);
+                    p.rlist[slot] = (int32_t)row;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Exact FP32 re-score of the points the tensor-core pass could not certify:
+// one warp per point, lanes over centroids, the library's FP32 distance,
+// lowest index on ties.
+template <int DV>
+__global__ void k_recheck(const float *X, const float *C32, int32_t k, const int32_t *rlist,
+                          const unsigned *rcount, int32_t *a_next, Counters *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = *rcount;
+    for (int64_t e = wid; e < cnt; e += nw) {
+        const int32_t i = rlist[e];
+        unsigned long long x2[DV / 2];
+        ldg_x2<DV>(x2, X + (int64_t)i * DV);
+        float bd = CUDART_INF_F;
+        int best = 0x7fffffff;
+        for (int c = lane; c < k; c += 32) {
+            const float r = d2_reg<DV>(x2, C32 + (size_t)c * DV);
+            if (r < bd) { bd = r; best = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(FULL_MASK, bd, o);
+            const int oi = __shfl_xor_sync(FULL_MASK, best, o);
+            if (ob < bd || (ob == bd && oi < best)) { bd = ob; best = oi; }
+        }
+        if (lane == 0) a_next[i] = best;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(&ctr->rechecked, (unsigned long long)cnt);
+        atomicAdd(&ctr->evals, (unsigned long long)cnt * (unsigned long long)k);
+    }
+}
+
+// Commits the new assignments and moves the rows that changed cluster
+// between the sums (FP64 atomics into partial slot 0): one warp per 32
+// points, lanes over dimensions.
+__global__ void k_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next,
+                             double *S, long long *cnt, Counters *ctr, int32_t k, int32_t *nslots,
+                             int32_t *fresh) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *nslots = 1;
+        *fresh = 0;
+        atomicAdd(&ctr->evals, (unsigned long long)n * (unsigned long long)k); // the tensor-core scan
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long changed = 0;
+    for (int64_t base = wid * 32; base < n; base += nw * 32) {
+        const int64_t i = base + lane;
+        int anew = -1, aold = -1;
+        bool ch = false;
+        if (i < n) {
+            anew = a_next[i];
+            PtState s = st[i];
+            aold = s.a;
+            ch = aold != anew;
+            if (ch) { s.a = anew; st[i] = s; }
+        }
+        unsigned m = __ballot_sync(FULL_MASK, ch);
+        changed += __popc(m);
+        while (m) {
+            const int pl = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t ip = base + pl;
+            const int cn = __shfl_sync(FULL_MASK, anew, pl);
+            const int co = __shfl_sync(FULL_MASK, aold, pl);
+            for (int j = lane; j < d; j += 32) {
+                const double x = (double)X[ip * d + j];
+                atomicAdd(&S[(size_t)cn * d + j], x);
+                if (co >= 0) atomicAdd(&S[(size_t)co * d + j], -x);
+            }
+            if (lane == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[cn]), 1ULL);
+                if (co >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[co]), (unsigned long long)-1LL);
+            }
+        }
+    }
+    if (lane == 0 && changed) atomicAdd(&ctr->changed, changed);
+}
+
+// Per iteration: BF16 centroids, ||c||^2 (FP64 sum of the FP32 values,
+// rounded to nearest FP32) and max ||c|| (rounded up), one CTA per centroid.
+__global__ void k_prec_prep(const float *C32, int32_t d, __nv_bfloat16 *Cb, float *cn, float *cmax) {
+    const int c = blockIdx.x;
+    __shared__ double red[128];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float v = C32[(size_t)c * d + j];
+        Cb[(size_t)c * d + j] = __float2bfloat16_rn(v);
+        acc += (double)v * (double)v;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+        cn[c] = __double2float_rn(t);
+        const float nrm = __double2float_ru(__dsqrt_ru(__dmul_ru(t, 1.0 + 1e-15)));
+        atomicMax(reinterpret_cast<int *>(cmax), __float_as_int(nrm)); // non-negative floats order as ints
+    }
+}
+
+// Once per context: BF16 points and ||x||^2 (FP64 sum, rounded to nearest).
+__global__ void k_prec_points(const float *X, int64_t n, int32_t d, __nv_bfloat16 *Xb, float *xn) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = wid; i < n; i += nw) {
+        double acc = 0.0;
+        for (int j = lane; j < d; j += 32) {
+            const float v = X[i * d + j];
+            Xb[i * d + j] = __float2bfloat16_rn(v);
+            acc += (double)v * (double)v;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        if (lane == 0) xn[i] = __double2float_rn(acc);
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+// Constants of the certification bound E(x) = eA |x| Cmax + eB (|x|^2 + Cmax^2)
+// on |d~^2 - d^2| plus the error of the FP32 distance, with u_b = 2^-8 (BF16
+// rounding of x and c), the tensor-core FP32 accumulation of the d products
+// allowed 2^-23 per addition (truncation) and a factor 2, u = 2^-24:
+//   |x.c - x~.c~|  <= (2 u_b + u_b^2 + g_tc (1 + u_b)^2) |x| |c|   (Cauchy-Schwarz)
+//   epilogue: ||x||^2 and ||c||^2 rounded once each, one add, one fma
+//   FP32 distance of the plain path: relative (d + 2) u / (1 - (d + 2) u) of
+//   d^2 <= 2 (|x|^2 + |c|^2)
+// so eA = 2 (2 u_b + u_b^2 + g_tc (1 + u_b)^2) + 2 u and
+//    eB = 3 u + 2 g_d, each with 1 % of slack and rounded up.
+void prec_error_constants(int d, float *eA, float *eB) {
+    const double ub = std::ldexp(1.0, -8), u = std::ldexp(1.0, -24);
+    const double gtc = 2.0 * d * std::ldexp(1.0, -23) / (1.0 - 2.0 * d * std::ldexp(1.0, -23));
+    const double g = (d + 2) * u / (1.0 - (d + 2) * u);
+    const double a1 = 2 * ub + ub * ub + gtc * (1 + ub) * (1 + ub);
+    const double A = 1.01 * (2 * a1 + 2 * u), B = 1.01 * (3 * u + 2 * g);
+    *eA = std::nextafter((float)A, INFINITY);
+    *eB = std::nextafter((float)B, INFINITY);
+}
+
+cudaError_t prec_points(const float *X, int64_t n, int32_t d, void *Xb, float *xn, cudaStream_t s) {
+    k_prec_points<<<1024, 256, 0, s>>>(X, n, d, static_cast<__nv_bfloat16 *>(Xb), xn);
+    return cudaGetLastError();
+}
+
+cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, void *Cb, float *cn, float *cmax, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    k_prec_prep<<<k, 128, 0, s>>>(C32, d, static_cast<__nv_bfloat16 *>(Cb), cn, cmax);
+    return cudaGetLastError();
+}
+
+cudaError_t prec_assign_attr(size_t smem) {
+    return cudaFuncSetAttribute(k_bf16_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prec_assign_maps(const CUtensorMap &tmX, const CUtensorMap &tmC, const PrecParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t prec_assign(const void *tmX, const void *tmC, const PrecParams &p, int grid, size_t smem,
+                        cudaStream_t s) {
+    return prec_assign_maps(*static_cast<const CUtensorMap *>(tmX), *static_cast<const CUtensorMap *>(tmC), p, grid,
+                            smem, s);
+}
+
+cudaError_t prec_assign_maps(const CUtensorMap &tmX, const CUtensorMap &tmC, const PrecParams &p, int grid,
+                             size_t smem, cudaStream_t s) {
+    k_bf16_assign<<<grid, PREC_THREADS, smem, s>>>(tmX, tmC, p);
+    return cudaGetLastError();
+}
+
+cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
+                         const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid, cudaStream_t s) {
+    switch (dv) {
+    case 64: k_recheck<64><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcount, a_next, ctr); break;
+    case 128: k_recheck<128><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcount, a_next, ctr); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t prec_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next, double *S,
+                            long long *cnt, Counters *ctr, int32_t k, int32_t *nslots, int32_t *fresh, int grid,
+                            cudaStream_t s) {
+    k_delta_sums<<<grid, 256, 0, s>>>(X, n, d, st, a_next, S, cnt, ctr, k, nslots, fresh);
+    return cudaGetLastError();
+}
+
+} // namespace knor

@@ -44,10 +44,10 @@ class IterStats(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6)]
 
 
-KERNELS = ("dense", "mti", "reduce", "table")
+KERNELS = ("dense", "mti", "reduce", "table", "recheck", "sums")
 
 _SIGS = {
     "knor_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,

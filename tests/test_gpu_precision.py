@@ -1,0 +1,82 @@
+"""GPU parity of the precision form (BF16 tensor-core distances with an exact
+FP32 recheck of the points whose top-2 gap is inside the error bound).
+
+The form is certified to return exactly the FP32 assignment of the plain path:
+at every iteration its assignments must equal, bit for bit, the oracle's FP32
+restatement of the argmin on the very FP32 centroids the context scanned; they
+must also meet the FP64 near-tie rule, and the new centroids must be the
+oracle's means of the assignments.  Planted exact ties force rechecks.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1606_08905_gb300 import build as kbuild
+from paper_1606_08905_gb300 import knor, synth
+from parity import check_assignments, check_centroids
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    knor.load()
+
+
+def _run_checked(X, k, iters, seed=42, init=None):
+    Xd = torch.as_tensor(X).cuda()
+    rechecked = 0
+    with knor.Context(Xd, k, seed=seed, precision="bf16", init="explicit" if init is not None else "forgy") as c:
+        if init is not None:
+            c.set_init_centroids(init)
+        for t in range(iters):
+            C_before = c.centroids()
+            C32 = c.centroids_f32()
+            s = c.iterate()
+            a = c.assignments()
+            a32 = oracle.assign_f32(X, C32)
+            bad = np.flatnonzero(a != a32)
+            assert bad.size == 0, f"it {t + 1}: {bad.size} assignments differ from the FP32 argmin, e.g. {bad[:5]}"
+            check_assignments(X, C_before, a, f"bf16 it {t + 1}")
+            C_ref, cnt = oracle.means(X, a, C_before)
+            check_centroids(c.centroids(), C_ref, f"bf16 it {t + 1}")
+            assert s["dist_evals"] == X.shape[0] * k + s["rechecked"] * k
+            rechecked += s["rechecked"]
+            if s["changed"] == 0:
+                break
+    return rechecked
+
+
+@pytest.mark.parametrize("n,d,k", [(5000, 128, 64), (20011, 128, 300), (9000, 64, 256), (30000, 128, 1024),
+                                   (100, 64, 3), (130, 128, 129)])
+def test_precision_form_equals_fp32_assignments(n, d, k):
+    X = synth.aniso_mixture(n, d, min(k, 64), 200 + k).numpy()
+    _run_checked(X, k, 12)
+
+
+def test_planted_ties_are_rechecked():
+    """Points exactly between two centroids have a zero top-2 gap: they must be
+    re-scored in FP32 (and land on the lower index)."""
+    rng = np.random.default_rng(3)
+    d, k = 64, 32
+    C = rng.uniform(-5, 5, (k, d)).astype(np.float32)
+    mids = ((C[0:8].astype(np.float64) + C[8:16].astype(np.float64)) / 2).astype(np.float32)
+    X = np.concatenate([mids, C + 0.01 * rng.standard_normal((k, d)).astype(np.float32),
+                        rng.uniform(-5, 5, (3000, d)).astype(np.float32)])
+    Xd = torch.as_tensor(X).cuda()
+    with knor.Context(Xd, k, init="explicit", precision="bf16") as c:
+        c.set_init_centroids(C.astype(np.float64))
+        s = c.iterate()
+        assert s["rechecked"] >= 8
+        assert np.array_equal(c.assignments(), oracle.assign_f32(X, C))
+
+
+def test_precision_form_rejects_unsupported_shapes():
+    X = torch.zeros((100, 32), device="cuda")
+    with pytest.raises(knor.KnorError) as e:
+        knor.Context(X, 4, precision="bf16")
+    assert e.value.status == knor.KNOR_ERR_ARG
