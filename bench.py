@@ -224,7 +224,9 @@ def synth_n(name):
 
 
 def config_of(wl, name, world):
-    return {"workload": name if wl["n"] == synth_n(name) else f"{name} (n overridden)", "n": wl["n"], "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
+    return {"workload": name if wl["n"] == synth_n(name) else f"{name} (n overridden)", "n": wl["n"],
+            "distance": ("BF16 tensor cores + exact FP32 recheck" if wl.get("precision", "fp32") != "fp32"
+                         else "FP32"), "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
             "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42",
             "data_seed": wl["data_seed"], "points_dtype": "f32",
             "l2": f"inputs larger than L2 ({wl['n'] * wl['d'] * 4 / 1e9:.2f} GB of points)",
@@ -244,7 +246,8 @@ def our_arm(args, wl, world, rank, local):
     n, d, k, T = wl["n"], wl["d"], wl["k"], wl["max_iters"]
     X = make_points(wl, "cuda")
     torch.cuda.synchronize()
-    ctx = knor.Context(X, k, seed=42, prune=wl["prune"])
+    prec = wl.get("precision", "fp32")
+    ctx = knor.Context(X, k, seed=42, prune=wl["prune"], precision=prec)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     def barrier():
@@ -281,7 +284,8 @@ def our_arm(args, wl, world, rank, local):
     else:
         ms_max, pts_all = ms, pts
     value = pts_all / (ms_max / 1000.0)
-    launches = sum(3 + it * (4 if wl["prune"] else 3) for it in iters)
+    per_it = 9 if wl.get("precision", "fp32") != "fp32" else (4 if wl["prune"] else 3)
+    launches = sum(3 + it * per_it for it in iters)
 
     # ---- per-kernel CUDA-event timing (profiling mode: kernel by kernel on the
     # library stream, same reset + run steps), for the roofline
@@ -296,36 +300,57 @@ def our_arm(args, wl, world, rank, local):
         prof_recs.extend(recs)
     prof = ctx.profile(reset=True)
     ctx.set_profiling(False)
-    # algorithmic bytes per launch: dense n(4d + 16);
-    # MTI 8n + active (4d + 8) with active = n - clause1_skipped
-    dense_bytes = sum(n * (4 * d + 16) for r in prof_recs if r["clause1_skipped"] == 0 and (
-        r["iteration"] == 1 or not wl["prune"]))
-    mti_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in prof_recs
-                    if wl["prune"] and r["iteration"] > 1)
+    # algorithmic work per launch: dense scan n(4d + 16) bytes;
+    # MTI scan 8n + active (4d + 8) bytes with active = n - clause1_skipped;
+    # tensor-core scan 2 n k d flops
     peaks, peak_src = measured_peaks()
     kernels = {}
-    for name, byts in (("dense", dense_bytes), ("mti", mti_bytes)):
-        launches_k, ms_k = prof[name]
-        if launches_k == 0 or ms_k <= 0:
-            continue
-        gbs = byts / (ms_k / 1000.0) / 1e9
-        kernels[name] = {"launches": launches_k, "ms_total": ms_k, "ms_per_launch": ms_k / launches_k,
-                         "algorithmic_bytes_per_launch": byts / launches_k, "achieved_gbs": gbs,
-                         "frac_of_" + peak_src + "_hbm": gbs / peaks["hbm_gbs"]}
-    total_prof_ms = sum(v[1] for v in prof.values())
-    dom = max(kernels, key=lambda kk: kernels[kk]["ms_total"])
-    kname = ctx.kernel_name(dom)
-    for kk in kernels:
-        kernels[kk]["kernel"] = ctx.kernel_name(kk)
-    roof = {"kernel": kname, "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"],
-            "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
-            "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"],
-            "traffic": ncu_traffic(kname, args.workload) if not args.n else None,
-            "share_of_kernel_time": kernels[dom]["ms_total"] / total_prof_ms}
+    if prec != "fp32":
+        launches_k, ms_k = prof["dense"]
+        flops = 2.0 * n * k * d * launches_k
+        tf = flops / (ms_k / 1000.0) / 1e12
+        kernels["dense"] = {"kernel": ctx.kernel_name("dense"), "launches": launches_k, "ms_total": ms_k,
+                            "ms_per_launch": ms_k / launches_k, "algorithmic_flops_per_launch": 2.0 * n * k * d,
+                            "achieved_tflops": tf,
+                            "frac_of_" + peak_src + "_bf16_sustained": tf / peaks["bf16_tflops_sustained"]}
+        for kk in ("recheck", "sums", "reduce", "table"):
+            lk, mk = prof[kk]
+            if lk:
+                kernels[kk] = {"kernel": ctx.kernel_name(kk), "launches": lk, "ms_total": mk,
+                               "ms_per_launch": mk / lk}
+        rechecked = sum(r["rechecked"] for r in prof_recs)
+        total_prof_ms = sum(v[1] for v in prof.values())
+        roof = {"kernel": ctx.kernel_name("dense"), "bound": "tensor", "achieved": tf,
+                "peak": peaks["bf16_tflops_sustained"], "peak_source": peak_src + " (bf16 sustained)",
+                "unit": "TFLOP/s", "frac": tf / peaks["bf16_tflops_sustained"],
+                "traffic": None, "share_of_kernel_time": ms_k / total_prof_ms,
+                "rechecked_fraction": rechecked / float(n * max(1, len(prof_recs)))}
+    else:
+        dense_bytes = sum(n * (4 * d + 16) for r in prof_recs if (r["iteration"] == 1 or not wl["prune"]))
+        mti_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in prof_recs
+                        if wl["prune"] and r["iteration"] > 1)
+        for name, byts in (("dense", dense_bytes), ("mti", mti_bytes)):
+            launches_k, ms_k = prof[name]
+            if launches_k == 0 or ms_k <= 0:
+                continue
+            gbs = byts / (ms_k / 1000.0) / 1e9
+            kernels[name] = {"launches": launches_k, "ms_total": ms_k, "ms_per_launch": ms_k / launches_k,
+                             "algorithmic_bytes_per_launch": byts / launches_k, "achieved_gbs": gbs,
+                             "frac_of_" + peak_src + "_hbm": gbs / peaks["hbm_gbs"]}
+        total_prof_ms = sum(v[1] for v in prof.values())
+        dom = max(kernels, key=lambda kk: kernels[kk]["ms_total"])
+        kname = ctx.kernel_name(dom)
+        for kk in kernels:
+            kernels[kk]["kernel"] = ctx.kernel_name(kk)
+        roof = {"kernel": kname, "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"],
+                "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
+                "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(kname, args.workload) if not args.n else None,
+                "share_of_kernel_time": kernels[dom]["ms_total"] / total_prof_ms}
 
     # ---- plain FP32 Lloyd on the same points: speed, and identical assignments
     plain = None
-    if not args.no_plain and wl["prune"]:
+    if not args.no_plain and (wl["prune"] or prec != "fp32"):
         ctx.reset()
         ctx.run(T)
         a_mti = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -334,7 +359,7 @@ def our_arm(args, wl, world, rank, local):
             pc.reset()
             pc.run(T)
             pstream = torch.cuda.ExternalStream(pc.stream)
-            ps = max(1, min(args.steps, 2))
+            ps = 1 if prec != "fp32" else max(1, min(args.steps, 2))
             q0 = torch.cuda.Event(enable_timing=True)
             q1 = torch.cuda.Event(enable_timing=True)
             q0.record(pstream)
@@ -348,7 +373,7 @@ def our_arm(args, wl, world, rank, local):
             a_plain = torch.empty(n, dtype=torch.int32, device="cuda")
             pc.assignments(a_plain)
             pv = n * pits / (q0.elapsed_time(q1) / 1000.0)
-            plain = {"value": pv, "unit": "point-iterations/s", "speedup_of_mti": (value / world) / pv,
+            plain = {"value": pv, "unit": "point-iterations/s", "speedup": (value / world) / pv,
                      "identical_assignments": bool(torch.equal(a_mti, a_plain)),
                      "iterations": pits // ps}
 
@@ -365,7 +390,7 @@ def our_arm(args, wl, world, rank, local):
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(es):
-            with knor.Context(Xh, k, seed=42, prune=wl["prune"]) as c2:
+            with knor.Context(Xh, k, seed=42, prune=wl["prune"], precision=prec) as c2:
                 done, _ = c2.run(T)
                 c2.assignments(ah)
                 c2.centroids(Ch)
