@@ -120,7 +120,7 @@ struct knor_ctx {
     bool prec = false;
     void *Xb = nullptr, *Cb = nullptr;
     float *xn = nullptr, *cn = nullptr, *cmax = nullptr;
-    int32_t *a_next = nullptr, *rlist = nullptr;
+    int32_t *a_next = nullptr, *rlist = nullptr, *rcand = nullptr;
     unsigned *rcount = nullptr;
     alignas(64) unsigned char tmX[128] = {}, tmC[128] = {}; // CUtensorMap
     PrecParams pp{};
@@ -177,7 +177,7 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->cmax,
-                    c->a_next, c->rlist,  c->rcount};
+                    c->a_next, c->rlist,  c->rcount, c->rcand};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -357,7 +357,8 @@ static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long 
     KNOR_CUDA(c, prec_assign(c->tmX, c->tmC, c->pp, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, mark(1));
     KNOR_CUDA(c, mark(8));
-    KNOR_CUDA(c, prec_recheck(c->dv, c->X, c->C32, c->k, c->rlist, c->rcount, c->a_next, c->ctr, 4 * c->num_sms, s));
+    KNOR_CUDA(c, prec_recheck(c->dv, c->X, c->C32, c->k, c->rlist, c->rcand, c->rcount, c->a_next, c->ctr,
+                              4 * c->num_sms, s));
     KNOR_CUDA(c, mark(9));
     KNOR_CUDA(c, mark(10));
     KNOR_CUDA(c, prec_delta_sums(c->X, c->n, c->d, c->st, c->a_next, c->part_S, c->part_cnt, c->ctr, c->k,
@@ -690,6 +691,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, &c->cmax, 1));
         KC(dalloc(c, &c->a_next, (size_t)n));
         KC(dalloc(c, &c->rlist, (size_t)n));
+        KC(dalloc(c, &c->rcand, (size_t)n * PREC_CANDS));
         KC(dalloc(c, &c->rcount, 1));
         KCU(prec_points(c->X, n, d, c->Xb, c->xn, c->stream));
         KC(encode_bf16_map(c, c->tmX, c->Xb, (uint64_t)d, (uint64_t)n, 128));
@@ -700,7 +702,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         c->prec_grid = (int)std::min<int64_t>(c->num_sms, ntile);
         PrecParams &pp = c->pp;
         pp.n = n; pp.d = d; pp.k = k; pp.xn = c->xn; pp.cn = c->cn; pp.cmax = c->cmax;
-        pp.a_next = c->a_next; pp.rlist = c->rlist; pp.rcount = c->rcount;
+        pp.a_next = c->a_next; pp.rlist = c->rlist; pp.rcount = c->rcount; pp.rcand = c->rcand;
         prec_error_constants(d, &pp.eA, &pp.eB);
         pp.err = c->flags + F_ERR;
         c->kname[KNOR_KERNEL_DENSE] = "k_bf16_assign";

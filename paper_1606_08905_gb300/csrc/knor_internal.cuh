@@ -114,6 +114,10 @@ struct FinParams {
     unsigned long long cond_handle; // cudaGraphConditionalHandle, 0 if none
 };
 
+// Candidate slots per re-scored point in the precision form (count + 8,
+// padded to 12 ints = three int4).
+constexpr int PREC_CANDS = 12;
+
 // Parameters of the precision-form assignment (precision.cu).
 struct PrecParams {
     int64_t n;
@@ -123,6 +127,7 @@ struct PrecParams {
     const float *cmax;   // max ||c|| rounded up
     int32_t *a_next;     // n: new assignment of certified points
     int32_t *rlist;      // points to re-score exactly
+    int32_t *rcand;      // per listed point: count (-1: too many) and up to PREC_CANDS centroids
     unsigned *rcount;
     float eA, eB;        // E(x) = eA |x| Cmax + eB (|x|^2 + Cmax^2), rounded up
     int32_t *err;        // set when a bounded wait gives up
@@ -169,7 +174,8 @@ cudaError_t prec_assign_attr(size_t smem);
 cudaError_t prec_assign(const void *tmX, const void *tmC, const PrecParams &p, int grid, size_t smem, cudaStream_t s);
 void prec_error_constants(int d, float *eA, float *eB);
 cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
-                         const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid, cudaStream_t s);
+                         const int32_t *rcand, const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid,
+                         cudaStream_t s);
 cudaError_t prec_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next, double *S,
                             long long *cnt, Counters *ctr, int32_t k, int32_t *nslots, int32_t *fresh, int grid,
                             cudaStream_t s);

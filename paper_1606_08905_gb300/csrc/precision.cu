@@ -261,15 +261,26 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue
+        // Per point: the smallest d~^2 (m1, at i1), the second smallest (m2),
+        // and the centroids that could still be the FP32 nearest: every c
+        // seen with d~^2(c) <= (running m1) + 2E.  Since m1 only decreases,
+        // this holds every c with d~^2(c) <= (final m1) + 2E, which contains
+        // the FP32 argmin whenever the point is not certified.
         const int q = warp & 3;       // TMEM lane quarter this warp may access
         const int rloc = 32 * q + lane;
-        uint32_t cons = 0; // accumulators consumed
+        uint32_t cons = 0;            // accumulators consumed
+        const float C = *p.cmax;
         for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
             const int64_t row = t * TM + rloc;
             const bool valid = row < p.n;
             const float xn = valid ? p.xn[row] : 0.0f;
+            const float X = __fsqrt_ru(fmaxf(xn, 0.0f));
+            const float twoE = __fmul_ru(2.0f, __fmaf_ru(p.eA, __fmul_ru(X, C),
+                                                         __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C)))));
             float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
             int i1 = 0;
+            int nc = 0;
+            int cl0 = 0, cl1 = 0, cl2 = 0, cl3 = 0, cl4 = 0, cl5 = 0, cl6 = 0, cl7 = 0;
             bool ok = true;
             for (int j = 0; j < nchunk; ++j) {
                 // lane 0 waits, the warp follows its outcome (the TMEM loads
@@ -290,8 +301,22 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                         const int c = cbase + cc + u;
                         if (c < p.k) {
                             const float dd = __fmaf_rn(-2.0f, __uint_as_float(r[u]), __fadd_rn(xn, cn_s[c]));
-                            if (dd < m1) { m2 = m1; m1 = dd; i1 = c; }
-                            else if (dd < m2) { m2 = dd; }
+                            bool add;
+                            if (dd < m1) { m2 = m1; m1 = dd; i1 = c; add = true; }
+                            else {
+                                if (dd < m2) m2 = dd;
+                                add = dd <= __fadd_ru(m1, twoE);
+                            }
+                            if (add) {
+                                switch (nc) {
+                                case 0: cl0 = c; break; case 1: cl1 = c; break;
+                                case 2: cl2 = c; break; case 3: cl3 = c; break;
+                                case 4: cl4 = c; break; case 5: cl5 = c; break;
+                                case 6: cl6 = c; break; case 7: cl7 = c; break;
+                                default: break;
+                                }
+                                ++nc;
+                            }
                         }
                     }
                 }
@@ -301,17 +326,24 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                 ++cons;
             }
             if (!ok) break;
-            if (valid) {
-                // certified when the gap exceeds twice the error bound E(x)
-                const float X = __fsqrt_ru(fmaxf(xn, 0.0f));
-                const float C = *p.cmax;
-                const float E = __fmaf_ru(p.eA, __fmul_ru(X, C), __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C))));
-                if (__fsub_rd(m2, m1) > __fmul_ru(2.0f, E)) {
-                    p.a_next[row] = i1;
-                } else {
-                    const unsigned slot = atomicAdd(p.rcount, 1u);
-                    p.rlist[slot] = (int32_t)row;
-                }
+            // certified when the gap exceeds twice the error bound E(x)
+            const bool cert = valid && __fsub_rd(m2, m1) > twoE;
+            if (cert) p.a_next[row] = i1;
+            const bool push = valid && !cert;
+            // warp-aggregated append to the recheck list
+            const unsigned pm = __ballot_sync(FULL_MASK, push);
+            unsigned base = 0;
+            if (pm) {
+                if (lane == __ffs(pm) - 1) base = atomicAdd(p.rcount, (unsigned)__popc(pm));
+                base = __shfl_sync(FULL_MASK, base, __ffs(pm) - 1);
+            }
+            if (push) {
+                const unsigned slot = base + __popc(pm & ((1u << lane) - 1u));
+                p.rlist[slot] = (int32_t)row;
+                int4 *cd = reinterpret_cast<int4 *>(p.rcand + (size_t)slot * PREC_CANDS);
+                cd[0] = make_int4(nc <= 8 ? nc : -1, cl0, cl1, cl2);
+                cd[1] = make_int4(cl3, cl4, cl5, cl6);
+                cd[2] = make_int4(cl7, 0, 0, 0);
             }
         }
     }
@@ -324,17 +356,39 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
     }
 }
 
-// Exact FP32 re-score of the points the tensor-core pass could not certify:
-// one warp per point, lanes over centroids, the library's FP32 distance,
-// lowest index on ties.
+// Exact FP32 re-score of the points the tensor-core pass could not certify,
+// with the library's FP32 distance and lowest index on ties: one thread per
+// point over its recorded candidates (ascending indices), or, when more than
+// PREC_CANDS were recorded, one warp over all centroids.
 template <int DV>
-__global__ void k_recheck(const float *X, const float *C32, int32_t k, const int32_t *rlist,
+__global__ void k_recheck(const float *X, const float *C32, int32_t k, const int32_t *rlist, const int32_t *rcand,
                           const unsigned *rcount, int32_t *a_next, Counters *ctr) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned cnt = *rcount;
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long evals = 0;
+    for (int64_t e = gtid; e < cnt; e += nthreads) {
+        const int32_t *cd = rcand + (size_t)e * PREC_CANDS;
+        const int nc = cd[0];
+        if (nc < 0) continue; // overflow: scored by the warp pass below
+        const int32_t i = rlist[e];
+        unsigned long long x2[DV / 2];
+        ldg_x2<DV>(x2, X + (int64_t)i * DV);
+        float bd = CUDART_INF_F;
+        int best = 0;
+        for (int t = 0; t < nc; ++t) {
+            const int c = cd[1 + t];
+            const float r = d2_reg<DV>(x2, C32 + (size_t)c * DV);
+            if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+        }
+        evals += nc;
+        a_next[i] = best;
+    }
+    // points with too many candidates: one warp per point, lanes over centroids
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = gtid >> 5, nw = nthreads >> 5;
     for (int64_t e = wid; e < cnt; e += nw) {
+        if (rcand[(size_t)e * PREC_CANDS] >= 0) continue;
         const int32_t i = rlist[e];
         unsigned long long x2[DV / 2];
         ldg_x2<DV>(x2, X + (int64_t)i * DV);
@@ -349,12 +403,11 @@ __global__ void k_recheck(const float *X, const float *C32, int32_t k, const int
             const int oi = __shfl_xor_sync(FULL_MASK, best, o);
             if (ob < bd || (ob == bd && oi < best)) { bd = ob; best = oi; }
         }
-        if (lane == 0) a_next[i] = best;
+        if (lane == 0) { a_next[i] = best; evals += k; }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        atomicAdd(&ctr->rechecked, (unsigned long long)cnt);
-        atomicAdd(&ctr->evals, (unsigned long long)cnt * (unsigned long long)k);
-    }
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL_MASK, evals, o);
+    if (lane == 0 && evals) atomicAdd(&ctr->evals, evals);
+    if (gtid == 0) atomicAdd(&ctr->rechecked, (unsigned long long)cnt);
 }
 
 // Commits the new assignments and moves the rows that changed cluster
@@ -496,10 +549,11 @@ cudaError_t prec_assign_maps(const CUtensorMap &tmX, const CUtensorMap &tmC, con
 }
 
 cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
-                         const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid, cudaStream_t s) {
+                         const int32_t *rcand, const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid,
+                         cudaStream_t s) {
     switch (dv) {
-    case 64: k_recheck<64><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcount, a_next, ctr); break;
-    case 128: k_recheck<128><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcount, a_next, ctr); break;
+    case 64: k_recheck<64><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcand, rcount, a_next, ctr); break;
+    case 128: k_recheck<128><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcand, rcount, a_next, ctr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

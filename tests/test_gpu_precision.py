@@ -80,3 +80,31 @@ def test_precision_form_rejects_unsupported_shapes():
     with pytest.raises(knor.KnorError) as e:
         knor.Context(X, 4, precision="bf16")
     assert e.value.status == knor.KNOR_ERR_ARG
+
+
+def test_precision_workload_full_size_teacher_forced():
+    """The 10M x 128, k = 1024 precision workload at full size: at iterations
+    1, 2 and 5 the tensor-core form assigns every point exactly as the plain
+    FP32 path started from the same centroids, and the FP64 oracle agrees on
+    a 20k-point sample (near-tie rule)."""
+    n, d, k = 10_000_000, 128, 1024
+    X = synth.make("aniso", n, d, k, 1003, device="cuda")
+    rng = np.random.default_rng(1)
+    sample = torch.as_tensor(np.sort(rng.choice(n, 20000, replace=False)), device="cuda")
+    Xs = X[sample].cpu().numpy()
+    with knor.Context(X, k, seed=42, precision="bf16") as c:
+        for t in range(1, 6):
+            C_before = c.centroids()
+            s = c.iterate()
+            if t not in (1, 2, 5):
+                continue
+            a = torch.empty(n, dtype=torch.int32, device="cuda")
+            c.assignments(a)
+            with knor.Context(X, k, init="explicit", prune=False) as q:
+                q.set_init_centroids(C_before)
+                q.iterate()
+                b = torch.empty(n, dtype=torch.int32, device="cuda")
+                q.assignments(b)
+            diff = int((a != b).sum())
+            assert diff == 0, f"iteration {t}: {diff} assignments differ from the FP32 path (rechecked {s['rechecked']})"
+            check_assignments(Xs, C_before, a[sample].cpu().numpy(), f"bf16 10M it {t}")
