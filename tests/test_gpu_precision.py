@@ -44,7 +44,9 @@ def _run_checked(X, k, iters, seed=42, init=None):
             check_assignments(X, C_before, a, f"bf16 it {t + 1}")
             C_ref, cnt = oracle.means(X, a, C_before)
             check_centroids(c.centroids(), C_ref, f"bf16 it {t + 1}")
-            assert s["dist_evals"] == X.shape[0] * k + s["rechecked"] * k
+            # the tensor-core scan scores every pair; a recheck scores its
+            # recorded candidates (at most 8), or all k on overflow
+            assert X.shape[0] * k <= s["dist_evals"] <= X.shape[0] * k + s["rechecked"] * k
             rechecked += s["rechecked"]
             if s["changed"] == 0:
                 break
