@@ -60,6 +60,36 @@ def test_precision_form_equals_fp32_assignments(n, d, k):
     _run_checked(X, k, 12)
 
 
+@pytest.mark.parametrize("n,d,k", [(600_000, 64, 64), (300_000, 128, 256)])
+def test_precision_form_many_tiles_per_cta(n, d, k):
+    """Enough points that every CTA of the persistent kernel reuses its tile
+    stages and accumulator buffers many times."""
+    X = synth.aniso_mixture(n, d, min(k, 64), 300 + k).numpy()
+    Xd = torch.as_tensor(X).cuda()
+    with knor.Context(Xd, k, seed=5, precision="bf16") as c:
+        for t in range(2):
+            C32 = c.centroids_f32()
+            c.iterate()
+            a = c.assignments()
+            a32 = oracle.assign_f32(X, C32)
+            assert np.array_equal(a, a32), f"it {t + 1}: {int((a != a32).sum())} differ"
+
+
+def test_plain_path_large_kd_matches_fp32_restatement():
+    """The plain FP32 path when k x d is too large for shared memory
+    (centroids read from global memory, cluster sums by FP64 atomics)."""
+    X = synth.aniso_mixture(20000, 128, 64, 17).numpy()
+    with knor.Context(torch.as_tensor(X).cuda(), 1024, seed=3, prune=False) as c:
+        for t in range(3):
+            C_before, C32 = c.centroids(), c.centroids_f32()
+            c.iterate()
+            a = c.assignments()
+            a32 = oracle.assign_f32(X, C32)
+            assert np.array_equal(a, a32), f"it {t + 1}: {int((a != a32).sum())} differ"
+            C_ref, _ = oracle.means(X, a, C_before)
+            check_centroids(c.centroids(), C_ref, f"plain large kd it {t + 1}")
+
+
 def test_planted_ties_are_rechecked():
     """Points exactly between two centroids have a zero top-2 gap: they must be
     re-scored in FP32 (and land on the lower index)."""
@@ -107,6 +137,7 @@ def test_precision_workload_full_size_teacher_forced():
                 q.iterate()
                 b = torch.empty(n, dtype=torch.int32, device="cuda")
                 q.assignments(b)
+            check_assignments(Xs, C_before, a[sample].cpu().numpy(), f"bf16 10M it {t}")
+            check_assignments(Xs, C_before, b[sample].cpu().numpy(), f"fp32 10M it {t}")
             diff = int((a != b).sum())
             assert diff == 0, f"iteration {t}: {diff} assignments differ from the FP32 path (rechecked {s['rechecked']})"
-            check_assignments(Xs, C_before, a[sample].cpu().numpy(), f"bf16 10M it {t}")
