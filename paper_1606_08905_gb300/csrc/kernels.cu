@@ -157,10 +157,17 @@ __global__ void __launch_bounds__(NT) k_dense(const IterParams p, const int32_t 
         const int64_t base = lo + (int64_t)b * NT;
         const int rows = (int)min((int64_t)NT, hi - base);
         const int stage = p.stages == 2 ? (b & 1) : 0;
-        if (p.stages == 2 && b + 1 < nbatch) {
-            load_tile(stage ^ 1, base + NT, (int)min((int64_t)NT, hi - base - NT));
-            cp_async_wait<1>();
+        if (p.stages == 2) {
+            if (b + 1 < nbatch) {
+                load_tile(stage ^ 1, base + NT, (int)min((int64_t)NT, hi - base - NT));
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
         } else {
+            // one stage: this batch's rows, after the previous batch's
+            // trailing barrier released the tile
+            if (b > 0) load_tile(0, base, rows);
             cp_async_wait<0>();
         }
         __syncthreads();

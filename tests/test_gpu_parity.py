@@ -142,6 +142,23 @@ def test_run_equals_iterate(prune):
         assert recs2 == more
 
 
+@pytest.mark.parametrize("d,k", [(128, 1024), (128, 17), (64, 600), (33, 40)])
+def test_many_batches_per_cta(d, k):
+    """Enough points that every CTA of the point kernels runs many row
+    batches (tile reuse), for widths and k x d that select the CTA kernels."""
+    X = synth.aniso_mixture(400_000, d, 32, 40 + d).numpy()
+    for prune in (False, True):
+        with knor.Context(_dev(X), k, seed=6, prune=prune) as c:
+            for t in range(3):
+                C_before, C32 = c.centroids(), c.centroids_f32()
+                c.iterate()
+                a = c.assignments()
+                a32 = oracle.assign_f32(X, C32)
+                assert np.array_equal(a, a32), f"prune={prune} it {t + 1}: {int((a != a32).sum())} differ"
+                C_ref, _ = oracle.means(X, a, C_before)
+                check_centroids(c.centroids(), C_ref, f"d{d} k{k} it {t + 1}")
+
+
 def test_deterministic_rerun():
     X = _dev(synth.spd_mixture(50000, 32, 20, 22))
     out = []
