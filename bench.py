@@ -324,7 +324,9 @@ def our_arm(args, wl, world, rank, local):
                 "peak": peaks["bf16_tflops_sustained"], "peak_source": peak_src + " (bf16 sustained)",
                 "unit": "TFLOP/s", "frac": tf / peaks["bf16_tflops_sustained"],
                 "traffic": None, "share_of_kernel_time": ms_k / total_prof_ms,
-                "rechecked_fraction": rechecked / float(n * max(1, len(prof_recs)))}
+                "rechecked_fraction": rechecked / float(n * max(1, len(prof_recs))),
+                "fp32_evals_per_rechecked_point":
+                    (sum(r["dist_evals"] for r in prof_recs) - n * k * len(prof_recs)) / float(max(1, rechecked))}
     else:
         dense_bytes = sum(n * (4 * d + 16) for r in prof_recs if (r["iteration"] == 1 or not wl["prune"]))
         mti_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in prof_recs

@@ -147,11 +147,13 @@ void *knor_stream(const knor_ctx *ctx);
  * (reset_after = 1 clears them after reading). */
 typedef enum {
     KNOR_KERNEL_DENSE = 0,  /* full scan + fresh sums (plain Lloyd, MTI iteration 1);
-                               the tensor-core scan in the precision form */
+                               the certifying tensor-core scan of all points in the
+                               precision form */
     KNOR_KERNEL_MTI = 1,    /* Clause-1 test + pruned scan + delta sums */
     KNOR_KERNEL_REDUCE = 2, /* ordered FP64 merge of per-CTA sums, new centroids */
     KNOR_KERNEL_TABLE = 3,  /* drift, k x k half-distance table, s(c) */
-    KNOR_KERNEL_RECHECK = 4, /* precision form: exact FP32 re-score of uncertified points */
+    KNOR_KERNEL_RECHECK = 4, /* precision form: the uncertified points -- gather, tensor-core
+                                candidate pass, exact FP32 re-score of the candidates */
     KNOR_KERNEL_SUMS = 5,   /* precision form: delta cluster sums of the changed points */
     KNOR_KERNEL_COUNT = 6
 } knor_kernel;

@@ -118,7 +118,10 @@ struct knor_ctx {
 
     // precision form (BF16 tensor-core distances + exact FP32 recheck)
     bool prec = false;
-    void *Xb = nullptr, *Cb = nullptr;
+    void *Xb = nullptr, *Cb = nullptr, *Xc = nullptr;
+    float *rm1 = nullptr, *rxn = nullptr;
+    alignas(64) unsigned char tmXc[128] = {};
+    PrecParams pp2{};
     float *xn = nullptr, *cn = nullptr, *cmax = nullptr;
     int32_t *a_next = nullptr, *rlist = nullptr, *rcand = nullptr;
     unsigned *rcount = nullptr;
@@ -177,7 +180,7 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->cmax,
-                    c->a_next, c->rlist,  c->rcount, c->rcand};
+                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -356,7 +359,11 @@ static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long 
     KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->Cb, c->cn, c->cmax, s));
     KNOR_CUDA(c, prec_assign(c->tmX, c->tmC, c->pp, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, mark(1));
+    // the points left uncertified: candidate pass over their gathered rows,
+    // then the exact FP32 re-score
     KNOR_CUDA(c, mark(8));
+    KNOR_CUDA(c, prec_gather(c->dv, c->Xb, c->xn, c->rlist, c->rcount, c->Xc, c->rxn, 8 * c->num_sms, s));
+    KNOR_CUDA(c, prec_assign(c->tmXc, c->tmC, c->pp2, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, prec_recheck(c->dv, c->X, c->C32, c->k, c->rlist, c->rcand, c->rcount, c->a_next, c->ctr,
                               4 * c->num_sms, s));
     KNOR_CUDA(c, mark(9));
@@ -692,21 +699,35 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, &c->a_next, (size_t)n));
         KC(dalloc(c, &c->rlist, (size_t)n));
         KC(dalloc(c, &c->rcand, (size_t)n * PREC_CANDS));
+        KC(dalloc(c, (uint16_t **)&c->Xc, nd));
+        KC(dalloc(c, &c->rm1, (size_t)n));
+        KC(dalloc(c, &c->rxn, (size_t)n));
         KC(dalloc(c, &c->rcount, 1));
         KCU(prec_points(c->X, n, d, c->Xb, c->xn, c->stream));
         KC(encode_bf16_map(c, c->tmX, c->Xb, (uint64_t)d, (uint64_t)n, 128));
         KC(encode_bf16_map(c, c->tmC, c->Cb, (uint64_t)d, (uint64_t)k, 256));
+        KC(encode_bf16_map(c, c->tmXc, c->Xc, (uint64_t)d, (uint64_t)n, 128));
         c->prec_smem = prec_smem_bytes(d, k);
+        int smem_optin = 0;
+        KCU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+        if (c->prec_smem > (size_t)smem_optin) {
+            c->err = "knor_create: the precision form's shared-memory tiles for this k do not fit one CTA";
+            return bail(KNOR_ERR_ARG);
+        }
         KCU(prec_assign_attr(c->prec_smem));
         const int64_t ntile = (n + 127) / 128;
         c->prec_grid = (int)std::min<int64_t>(c->num_sms, ntile);
         PrecParams &pp = c->pp;
         pp.n = n; pp.d = d; pp.k = k; pp.xn = c->xn; pp.cn = c->cn; pp.cmax = c->cmax;
         pp.a_next = c->a_next; pp.rlist = c->rlist; pp.rcount = c->rcount; pp.rcand = c->rcand;
+        pp.rm1 = c->rm1; pp.rxn = c->rxn; pp.mode = 0;
         prec_error_constants(d, &pp.eA, &pp.eB);
         pp.err = c->flags + F_ERR;
+        c->pp2 = pp;
+        c->pp2.mode = 1;
         c->kname[KNOR_KERNEL_DENSE] = "k_bf16_assign";
-        c->kname[KNOR_KERNEL_RECHECK] = "k_recheck<" + std::to_string(c->dv) + ">";
+        c->kname[KNOR_KERNEL_RECHECK] =
+            "k_prec_gather + k_bf16_assign (candidates) + k_recheck<" + std::to_string(c->dv) + ">";
         c->kname[KNOR_KERNEL_SUMS] = "k_delta_sums";
     }
     // C^0

@@ -116,7 +116,7 @@ struct FinParams {
 
 // Candidate slots per re-scored point in the precision form (count + 8,
 // padded to 12 ints = three int4).
-constexpr int PREC_CANDS = 12;
+constexpr int PREC_CANDS = 16;
 
 // Parameters of the precision-form assignment (precision.cu).
 struct PrecParams {
@@ -127,7 +127,11 @@ struct PrecParams {
     const float *cmax;   // max ||c|| rounded up
     int32_t *a_next;     // n: new assignment of certified points
     int32_t *rlist;      // points to re-score exactly
-    int32_t *rcand;      // per listed point: count (-1: too many) and up to PREC_CANDS centroids
+    int32_t *rcand;      // per listed point: two lists (one per half of the columns), each a
+                         // count (-1: too many) and up to 7 centroids
+    float *rm1;          // per listed point: its smallest d~^2
+    const float *rxn;    // mode 1: ||x||^2 of the gathered points
+    int32_t mode;        // 0: all points, certify or list; 1: listed points, record candidates
     unsigned *rcount;
     float eA, eB;        // E(x) = eA |x| Cmax + eB (|x|^2 + Cmax^2), rounded up
     int32_t *err;        // set when a bounded wait gives up
@@ -176,6 +180,8 @@ void prec_error_constants(int d, float *eA, float *eB);
 cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
                          const int32_t *rcand, const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid,
                          cudaStream_t s);
+cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
+                        void *Xc, float *rxn, int grid, cudaStream_t s);
 cudaError_t prec_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next, double *S,
                             long long *cnt, Counters *ctr, int32_t k, int32_t *nslots, int32_t *fresh, int grid,
                             cudaStream_t s);

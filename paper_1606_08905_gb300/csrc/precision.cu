@@ -9,10 +9,12 @@
 // over all centroids.  A point whose gap min2 - min1 exceeds 2 E(x) -- E(x)
 // bounds the BF16 error of d~^2 plus the error of the library's FP32 distance
 // (prec_error_constants below) -- provably has the same nearest centroid under
-// the FP32 distance of the plain path; every other point is re-scored exactly
-// in FP32 over all centroids.  The assignments are therefore identical to the
-// plain FP32 path's.  The cluster sums are then updated by the deltas of the
-// points that changed cluster.
+// the FP32 distance of the plain path.  The other points are gathered and run
+// through the same kernel a second time, which records every centroid within
+// min1 + 2 E(x) (a handful); those candidates are re-scored exactly in FP32
+// (all k when more than eight were recorded).  The assignments are therefore
+// identical to the plain FP32 path's.  The cluster sums are then updated by
+// the deltas of the points that changed cluster.
 //
 // The paper has no GEMM path (its serial baseline table notes that GEMM codes
 // were slower on its CPUs); this form is an addition for the tensor cores.
@@ -112,8 +114,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 consecutive FP32 columns of this thread's TMEM lane (asynchronous: the
+// registers are valid after tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
                  "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -123,7 +126,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
                    "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
                    "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// One d~^2 - ||x||^2 value into a (smallest, its index, second smallest) chain.
+__device__ __forceinline__ void top2_step(float &m1, float &m2, int &i1, float t, int c) {
+    m2 = fminf(m2, fmaxf(m1, t));
+    if (t < m1) i1 = c;
+    m1 = fminf(m1, t);
+}
+// Merges chain b into chain a.  On equal minima the merged second smallest
+// equals the smallest: the gap is 0 and the point is never certified, so the
+// index kept does not matter.
+__device__ __forceinline__ void top2_merge(float &m1, float &m2, int &i1, float b1, float b2, int bi) {
+    m2 = fminf(fminf(m2, b2), fmaxf(m1, b1));
+    if (b1 < m1) { m1 = b1; i1 = bi; }
 }
 
 // ---------------------------------------------------------------- layout
@@ -133,13 +150,17 @@ constexpr int TN = 256;              // centroids per chunk (MMA N)
 constexpr int TKB = 64;              // BF16 elements per 128-byte row of a TMA box
 constexpr int A_BOX = TM * 128;      // bytes of one A box (16 KB)
 constexpr int B_BOX = TN * 128;      // bytes of one B box (32 KB)
-constexpr int PREC_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int EPI_WARPS = 8;         // two epilogue warps per TMEM lane quarter
+constexpr int PREC_THREADS = 64 + 32 * EPI_WARPS; // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int HALF = TN / 2;         // columns of each chunk read by one epilogue warp
 constexpr int TMEM_COLS = 2 * TN;    // two accumulator buffers
+constexpr int NBARS = 21;            // mbarriers, see the kernel
 
 size_t prec_smem_bytes(int d, int k) {
     const int nkc = d / TKB;
-    return 1024 /* alignment */ + 2 * (size_t)nkc * A_BOX + 2 * (size_t)nkc * B_BOX + (size_t)k * 4 + 16 +
-           16 * 8 + 16;
+    const size_t kpad = (size_t)(k + TN - 1) / TN * TN;
+    return 1024 /* alignment */ + 2 * (size_t)nkc * A_BOX + 2 * (size_t)nkc * B_BOX + kpad * 4 +
+           3 * TM * 4 /* pair hand-off */ + NBARS * 8 + 16;
 }
 
 // ------------------------------------------------------------- the kernel
@@ -148,8 +169,9 @@ size_t prec_smem_bytes(int d, int k) {
 // per tile, ceil(k / 256) centroid chunks.  Warp 0 (one lane) issues TMA
 // loads of point tiles (two stages) and centroid chunks (two stages); warp 1
 // allocates 512 TMEM columns and one lane issues the MMAs into two
-// accumulator buffers; warps 2-5 read a finished buffer (one TMEM lane per
-// point) while the next chunk is being multiplied.
+// accumulator buffers; warps 2-9 read a finished buffer (one TMEM lane per
+// point; the two warps of a lane quarter take one half of the columns each)
+// while the next chunk is being multiplied.
 __global__ void __launch_bounds__(PREC_THREADS, 1)
     k_bf16_assign(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC,
                   const PrecParams p) {
@@ -159,16 +181,19 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
     const int nkc = p.d / TKB;
     unsigned char *sA = sm;                                  // [2][nkc][A_BOX]
     unsigned char *sB = sA + 2 * (size_t)nkc * A_BOX;        // [2][nkc][B_BOX]
-    float *cn_s = reinterpret_cast<float *>(sB + 2 * (size_t)nkc * B_BOX);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(cn_s + p.k + ((4 - (p.k & 3)) & 3)); // 16-byte aligned
+    const int nchunk = (p.k + TN - 1) / TN;
+    float *cn_s = reinterpret_cast<float *>(sB + 2 * (size_t)nkc * B_BOX); // [nchunk * TN], +inf past k
+    float *hand = cn_s + (size_t)nchunk * TN;                                // [3][TM] pair hand-off
+    uint64_t *bars = reinterpret_cast<uint64_t *>(hand + 3 * TM);
     uint64_t *fullA = bars, *emptyA = bars + 2, *fullB = bars + 4, *emptyB = bars + 6;
     uint64_t *tfull = bars + 8, *tempty = bars + 10, *done = bars + 12;
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 13);
+    uint64_t *hfull = bars + 13, *hfree = bars + 17; // per lane quarter
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + NBARS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntile = (p.n + TM - 1) / TM;
-    const int nchunk = (p.k + TN - 1) / TN;
+    const int64_t nrows = p.mode ? (int64_t)*p.rcount : p.n; // mode 1: the gathered points
+    const int64_t ntile = (nrows + TM - 1) / TM;
 
-    for (int c = threadIdx.x; c < p.k; c += PREC_THREADS) cn_s[c] = p.cn[c];
+    for (int c = threadIdx.x; c < nchunk * TN; c += PREC_THREADS) cn_s[c] = c < p.k ? p.cn[c] : CUDART_INF_F;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&fullA[i], 1);
@@ -176,9 +201,13 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
             mbar_init(&fullB[i], 1);
             mbar_init(&emptyB[i], 1);
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 4); // one arrive per epilogue warp
+            mbar_init(&tempty[i], EPI_WARPS); // one arrive per epilogue warp
         }
         mbar_init(done, 1);
+        for (int i = 0; i < 4; ++i) {
+            mbar_init(&hfull[i], 32); // every lane of the quarter's second warp
+            mbar_init(&hfree[i], 32); // every lane of the quarter's first warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -261,26 +290,40 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue
-        // Per point: the smallest d~^2 (m1, at i1), the second smallest (m2),
-        // and the centroids that could still be the FP32 nearest: every c
-        // seen with d~^2(c) <= (running m1) + 2E.  Since m1 only decreases,
-        // this holds every c with d~^2(c) <= (final m1) + 2E, which contains
-        // the FP32 argmin whenever the point is not certified.
-        const int q = warp & 3;       // TMEM lane quarter this warp may access
+        // Values compared: t(c) = ||c||^2 - 2 x~.c~ = d~^2 - ||x||^2 (||x||^2
+        // is common to the row and cancels from every comparison).
+        // Mode 0 (all points): the smallest t (m1, at i1) and the second
+        // smallest (m2); a point is certified when m2 - m1 > 2E, else it is
+        // listed with its m1.  Mode 1 (the listed points, gathered): every
+        // centroid with t <= m1 + 2E is recorded.  Each t + ||x||^2 is within
+        // E_tc of the exact d^2 and each FP32 distance within E_f (E = E_tc +
+        // E_f), so the FP32 nearest centroid c* has t(c*) + ||x||^2 <= d32(c*)
+        // + E <= d32(i1) + E <= m1 + ||x||^2 + 2E: it is always among the
+        // candidates, whichever pass computed the two t values.
+        const int q = warp & 3;          // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;   // which half of each chunk's columns
         const int rloc = 32 * q + lane;
-        uint32_t cons = 0;            // accumulators consumed
+        float *hm1 = hand, *hm2 = hand + TM;
+        int *hi1 = reinterpret_cast<int *>(hand + 2 * TM);
+        uint32_t cons = 0;  // accumulators consumed
+        uint32_t tiles = 0; // tiles handed between the quarter's two warps
         const float C = *p.cmax;
         for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
             const int64_t row = t * TM + rloc;
-            const bool valid = row < p.n;
-            const float xn = valid ? p.xn[row] : 0.0f;
+            const bool valid = row < nrows;
+            const float xn = valid ? (p.mode ? p.rxn[row] : p.xn[row]) : 0.0f;
             const float X = __fsqrt_ru(fmaxf(xn, 0.0f));
             const float twoE = __fmul_ru(2.0f, __fmaf_ru(p.eA, __fmul_ru(X, C),
                                                          __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C)))));
-            float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
-            int i1 = 0;
-            int nc = 0;
-            int cl0 = 0, cl1 = 0, cl2 = 0, cl3 = 0, cl4 = 0, cl5 = 0, cl6 = 0, cl7 = 0;
+            const float thr = (p.mode && valid) ? __fadd_ru(p.rm1[row], twoE) : -CUDART_INF_F;
+            // four independent chains (columns u mod 4) keep the dependent
+            // min/max sequences short
+            float a1[4], a2[4];
+            int ai[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { a1[j] = CUDART_INF_F; a2[j] = CUDART_INF_F; ai[j] = 0; }
+            int nc = 0; // mode 1: candidates met in this warp's columns
+            int32_t *cd = p.rcand + (size_t)(valid ? row : 0) * PREC_CANDS + h * (PREC_CANDS / 2);
             bool ok = true;
             for (int j = 0; j < nchunk; ++j) {
                 // lane 0 waits, the warp follows its outcome (the TMEM loads
@@ -291,31 +334,42 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                 if (!okw) { ok = false; break; }
                 tc_fence_after();
                 const int buf = cons & 1;
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TN);
-                const int cbase = j * TN;
-                for (int cc = 0; cc < TN; cc += 32) {
-                    uint32_t r[32];
+                const uint32_t taddr =
+                    tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TN + h * HALF);
+#pragma unroll 1
+                for (int cc = 0; cc < HALF; cc += 64) {
+                    uint32_t r[64];
                     tmem_ld32(taddr + (uint32_t)cc, r);
+                    tmem_ld32(taddr + (uint32_t)cc + 32, r + 32);
+                    tmem_wait_ld();
+                    const int cb = j * TN + h * HALF + cc;
+                    const float4 *cn4 = reinterpret_cast<const float4 *>(cn_s + cb);
+                    if (p.mode == 0) {
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        const int c = cbase + cc + u;
-                        if (c < p.k) {
-                            const float dd = __fmaf_rn(-2.0f, __uint_as_float(r[u]), __fadd_rn(xn, cn_s[c]));
-                            bool add;
-                            if (dd < m1) { m2 = m1; m1 = dd; i1 = c; add = true; }
-                            else {
-                                if (dd < m2) m2 = dd;
-                                add = dd <= __fadd_ru(m1, twoE);
-                            }
-                            if (add) {
-                                switch (nc) {
-                                case 0: cl0 = c; break; case 1: cl1 = c; break;
-                                case 2: cl2 = c; break; case 3: cl3 = c; break;
-                                case 4: cl4 = c; break; case 5: cl5 = c; break;
-                                case 6: cl6 = c; break; case 7: cl7 = c; break;
-                                default: break;
+                        for (int v = 0; v < 16; ++v) {
+                            const float4 cv = cn4[v];
+                            top2_step(a1[0], a2[0], ai[0], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 0]), cv.x), cb + 4 * v + 0);
+                            top2_step(a1[1], a2[1], ai[1], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 1]), cv.y), cb + 4 * v + 1);
+                            top2_step(a1[2], a2[2], ai[2], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 2]), cv.z), cb + 4 * v + 2);
+                            top2_step(a1[3], a2[3], ai[3], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 3]), cv.w), cb + 4 * v + 3);
+                        }
+                    } else {
+                        bool any = false;
+#pragma unroll
+                        for (int v = 0; v < 16; ++v) {
+                            const float4 cv = cn4[v];
+                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 0]), cv.x) <= thr;
+                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 1]), cv.y) <= thr;
+                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 2]), cv.z) <= thr;
+                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 3]), cv.w) <= thr;
+                        }
+                        if (any) { // rare: record the group's candidates
+#pragma unroll
+                            for (int u = 0; u < 64; ++u) {
+                                if (__fmaf_rn(-2.0f, __uint_as_float(r[u]), cn_s[cb + u]) <= thr) {
+                                    if (nc < PREC_CANDS / 2 - 1) cd[1 + nc] = cb + u;
+                                    ++nc;
                                 }
-                                ++nc;
                             }
                         }
                     }
@@ -326,12 +380,44 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                 ++cons;
             }
             if (!ok) break;
+            if (p.mode == 1) {
+                if (valid) cd[0] = nc < PREC_CANDS / 2 ? nc : -1;
+                continue;
+            }
+            float m1 = a1[0], m2 = a2[0];
+            int i1 = ai[0];
+#pragma unroll
+            for (int j = 1; j < 4; ++j) top2_merge(m1, m2, i1, a1[j], a2[j], ai[j]);
+            // the quarter's second warp hands its half to the first
+            if (h == 1) {
+                if (tiles > 0) {
+                    int okw = 1;
+                    if (lane == 0) okw = mbar_wait(&hfree[q], (tiles - 1) & 1, p.err) ? 1 : 0;
+                    okw = __shfl_sync(FULL_MASK, okw, 0);
+                    if (!okw) break;
+                }
+                hm1[rloc] = m1;
+                hm2[rloc] = m2;
+                hi1[rloc] = i1;
+                mbar_arrive(&hfull[q]);
+                ++tiles;
+                continue;
+            }
+            {
+                int okw = 1;
+                if (lane == 0) okw = mbar_wait(&hfull[q], tiles & 1, p.err) ? 1 : 0;
+                okw = __shfl_sync(FULL_MASK, okw, 0);
+                if (!okw) break;
+                __syncwarp();
+            }
+            top2_merge(m1, m2, i1, hm1[rloc], hm2[rloc], hi1[rloc]);
+            mbar_arrive(&hfree[q]);
+            ++tiles;
             // certified when the gap exceeds twice the error bound E(x)
             const bool cert = valid && __fsub_rd(m2, m1) > twoE;
             if (cert) p.a_next[row] = i1;
             const bool push = valid && !cert;
-            // warp-aggregated append to the recheck list
-            const unsigned pm = __ballot_sync(FULL_MASK, push);
+            const unsigned pm = __ballot_sync(FULL_MASK, push); // warp-aggregated append
             unsigned base = 0;
             if (pm) {
                 if (lane == __ffs(pm) - 1) base = atomicAdd(p.rcount, (unsigned)__popc(pm));
@@ -340,10 +426,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
             if (push) {
                 const unsigned slot = base + __popc(pm & ((1u << lane) - 1u));
                 p.rlist[slot] = (int32_t)row;
-                int4 *cd = reinterpret_cast<int4 *>(p.rcand + (size_t)slot * PREC_CANDS);
-                cd[0] = make_int4(nc <= 8 ? nc : -1, cl0, cl1, cl2);
-                cd[1] = make_int4(cl3, cl4, cl5, cl6);
-                cd[2] = make_int4(cl7, 0, 0, 0);
+                p.rm1[slot] = m1;
             }
         }
     }
@@ -358,37 +441,38 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
 
 // Exact FP32 re-score of the points the tensor-core pass could not certify,
 // with the library's FP32 distance and lowest index on ties: one thread per
-// point over its recorded candidates (ascending indices), or, when more than
-// PREC_CANDS were recorded, one warp over all centroids.
+// point over its recorded candidates (two lists, one per half of the
+// columns), or, when a list overflowed, one warp over all centroids.
 template <int DV>
 __global__ void k_recheck(const float *X, const float *C32, int32_t k, const int32_t *rlist, const int32_t *rcand,
                           const unsigned *rcount, int32_t *a_next, Counters *ctr) {
+    constexpr int HC = PREC_CANDS / 2;
     const unsigned cnt = *rcount;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     unsigned long long evals = 0;
     for (int64_t e = gtid; e < cnt; e += nthreads) {
         const int32_t *cd = rcand + (size_t)e * PREC_CANDS;
-        const int nc = cd[0];
-        if (nc < 0) continue; // overflow: scored by the warp pass below
+        const int n0 = cd[0], n1 = cd[HC];
+        if (n0 < 0 || n1 < 0) continue; // overflow: scored by the warp pass below
         const int32_t i = rlist[e];
         unsigned long long x2[DV / 2];
         ldg_x2<DV>(x2, X + (int64_t)i * DV);
         float bd = CUDART_INF_F;
-        int best = 0;
-        for (int t = 0; t < nc; ++t) {
-            const int c = cd[1 + t];
+        int best = 0x7fffffff;
+        for (int t = 0; t < n0 + n1; ++t) {
+            const int c = t < n0 ? cd[1 + t] : cd[HC + 1 + (t - n0)];
             const float r = d2_reg<DV>(x2, C32 + (size_t)c * DV);
             if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
         }
-        evals += nc;
+        evals += n0 + n1;
         a_next[i] = best;
     }
     // points with too many candidates: one warp per point, lanes over centroids
     const int lane = threadIdx.x & 31;
     const int64_t wid = gtid >> 5, nw = nthreads >> 5;
     for (int64_t e = wid; e < cnt; e += nw) {
-        if (rcand[(size_t)e * PREC_CANDS] >= 0) continue;
+        if (rcand[(size_t)e * PREC_CANDS] >= 0 && rcand[(size_t)e * PREC_CANDS + HC] >= 0) continue;
         const int32_t i = rlist[e];
         unsigned long long x2[DV / 2];
         ldg_x2<DV>(x2, X + (int64_t)i * DV);
@@ -408,6 +492,25 @@ __global__ void k_recheck(const float *X, const float *C32, int32_t k, const int
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL_MASK, evals, o);
     if (lane == 0 && evals) atomicAdd(&ctr->evals, evals);
     if (gtid == 0) atomicAdd(&ctr->rechecked, (unsigned long long)cnt);
+}
+
+// Gathers the BF16 rows (and ||x||^2) of the listed points into a compact
+// matrix for the candidate pass: one warp per point, 16 bytes per lane.
+template <int DV>
+__global__ void k_prec_gather(const __nv_bfloat16 *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
+                              __nv_bfloat16 *Xc, float *rxn) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = *rcount;
+    constexpr int V = DV * 2 / 16; // 16-byte vectors per row
+    for (int64_t e = wid; e < cnt; e += nw) {
+        const int32_t i = rlist[e];
+        if (lane < V)
+            reinterpret_cast<int4 *>(Xc + (size_t)e * DV)[lane] =
+                reinterpret_cast<const int4 *>(Xb + (size_t)i * DV)[lane];
+        if (lane == 0) rxn[e] = xn[i];
+    }
 }
 
 // Commits the new assignments and moves the rows that changed cluster
@@ -554,6 +657,18 @@ cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, co
     switch (dv) {
     case 64: k_recheck<64><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcand, rcount, a_next, ctr); break;
     case 128: k_recheck<128><<<grid, 256, 0, s>>>(X, C32, k, rlist, rcand, rcount, a_next, ctr); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
+                        void *Xc, float *rxn, int grid, cudaStream_t s) {
+    const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(Xb);
+    __nv_bfloat16 *b = static_cast<__nv_bfloat16 *>(Xc);
+    switch (dv) {
+    case 64: k_prec_gather<64><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;
+    case 128: k_prec_gather<128><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
