@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=0, help="override the workload's n (profiling runs)")
+    ap.add_argument("--precision", default="", choices=["", "bf16", "fp16"],
+                    help="override the tensor-core operand format of a precision workload")
     return ap.parse_args()
 
 
@@ -225,8 +227,8 @@ def synth_n(name):
 
 def config_of(wl, name, world):
     return {"workload": name if wl["n"] == synth_n(name) else f"{name} (n overridden)", "n": wl["n"],
-            "distance": ("BF16 tensor cores + exact FP32 recheck" if wl.get("precision", "fp32") != "fp32"
-                         else "FP32"), "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
+            "distance": (wl["precision"].upper() + " tensor cores + exact FP32 recheck"
+                         if wl.get("precision", "fp32") != "fp32" else "FP32"), "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
             "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42",
             "data_seed": wl["data_seed"], "points_dtype": "f32",
             "l2": f"inputs larger than L2 ({wl['n'] * wl['d'] * 4 / 1e9:.2f} GB of points)",
@@ -439,6 +441,8 @@ def main():
     wl = dict(synth.WORKLOADS[args.workload])
     if args.n:
         wl["n"] = args.n
+    if args.precision and wl.get("precision", "fp32") != "fp32":
+        wl["precision"] = args.precision
     if args.impl == "reference":
         reference_arm(args, wl, world, rank)
         return

@@ -122,7 +122,10 @@ struct knor_ctx {
     float *rm1 = nullptr, *rxn = nullptr;
     alignas(64) unsigned char tmXc[128] = {};
     PrecParams pp2{};
-    float *xn = nullptr, *cn = nullptr, *cmax = nullptr;
+    float *xn = nullptr, *cn = nullptr, *absmax = nullptr;
+    PrecIter *pit = nullptr;
+    int32_t fmt = PREC_FMT_BF16;
+    float sx = 1.0f; // point scale (a power of two)
     int32_t *a_next = nullptr, *rlist = nullptr, *rcand = nullptr;
     unsigned *rcount = nullptr;
     alignas(64) unsigned char tmX[128] = {}, tmC[128] = {}; // CUtensorMap
@@ -179,7 +182,7 @@ static void free_all(knor_ctx *c) {
     if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
-                    c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->cmax,
+                    c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
                     c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -189,8 +192,10 @@ static void free_all(knor_ctx *c) {
 
 // A 2-D TMA descriptor over a row-major rows x inner BF16 matrix, boxes of
 // 64 columns (128 bytes) x box_rows rows, 128-byte swizzle, zero fill outside.
-static knor_status encode_bf16_map(knor_ctx *c, void *out, void *base, uint64_t inner, uint64_t rows,
-                                   uint32_t box_rows) {
+// TMA map of a row-major matrix of 16-bit operands (rows x inner), 64-element
+// (128-byte) boxes of box_rows rows, 128-byte swizzle.
+static knor_status encode_op_map(knor_ctx *c, void *out, void *base, uint64_t inner, uint64_t rows,
+                                 uint32_t box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q{};
@@ -204,7 +209,9 @@ static knor_status encode_bf16_map(knor_ctx *c, void *out, void *base, uint64_t 
     cuuint64_t strides[1] = {inner * 2};
     cuuint32_t box[2] = {64, box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(static_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+    const CUtensorMapDataType dt =
+        c->fmt == PREC_FMT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = fn(static_cast<CUtensorMap *>(out), dt, 2, base, dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(c, KNOR_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -356,7 +363,7 @@ static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long 
     KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
     KNOR_CUDA(c, cudaMemsetAsync(c->rcount, 0, sizeof(unsigned), s));
     KNOR_CUDA(c, mark(0));
-    KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->Cb, c->cn, c->cmax, s));
+    KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->fmt, c->sx, c->Cb, c->cn, c->pit, s));
     KNOR_CUDA(c, prec_assign(c->tmX, c->tmC, c->pp, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, mark(1));
     // the points left uncertified: candidate pass over their gathered rows,
@@ -579,12 +586,14 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     if (init != KNOR_INIT_FORGY && init != KNOR_INIT_EXPLICIT) { g_create_err = "knor_create: bad init"; return KNOR_ERR_ARG; }
     knor_opts o{};
     if (opts) o = *opts;
-    if (o.precision != KNOR_PREC_FP32 && o.precision != KNOR_PREC_BF16) {
-        g_create_err = "knor_create: precision must be KNOR_PREC_FP32 or KNOR_PREC_BF16 (the FP8 variant is not built)";
+    if (o.precision != KNOR_PREC_FP32 && o.precision != KNOR_PREC_BF16 && o.precision != KNOR_PREC_FP16) {
+        g_create_err = "knor_create: precision must be KNOR_PREC_FP32, KNOR_PREC_BF16 or KNOR_PREC_FP16 "
+                       "(the FP8 variant is not built)";
         return KNOR_ERR_ARG;
     }
-    if (o.precision == KNOR_PREC_BF16 && ((d != 64 && d != 128) || k > 8192)) {
-        g_create_err = "knor_create: the BF16 tensor-core form needs d = 64 or 128 and k <= 8192";
+    const bool tc_form = o.precision == KNOR_PREC_BF16 || o.precision == KNOR_PREC_FP16;
+    if (tc_form && ((d != 64 && d != 128) || k > 8192)) {
+        g_create_err = "knor_create: the tensor-core forms need d = 64 or 128 and k <= 8192";
         return KNOR_ERR_ARG;
     }
     if (o.full_recompute_every < 0) { g_create_err = "knor_create: full_recompute_every < 0"; return KNOR_ERR_ARG; }
@@ -651,7 +660,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     // Both scans use the same accumulation mode: per-CTA partial slots, or,
     // when k x d sums do not fit in shared memory, one slot updated by FP64
     // atomics.
-    const int acc_global = (c->ip_dense.acc_global || c->ip_mti.acc_global || o.precision == KNOR_PREC_BF16) ? 1 : 0;
+    const int acc_global = (c->ip_dense.acc_global || c->ip_mti.acc_global || tc_form) ? 1 : 0;
     if (acc_global && (c->ip_dense.warp_kernels || c->ip_mti.warp_kernels)) {
         // the warp kernels always write per-CTA slots: use the CTA kernels for both
         c->ip_dense = IterParams{};
@@ -686,7 +695,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     f.run_iter = c->flags + F_RUN_ITER; f.total_iter = c->flags + F_TOTAL_ITER;
     f.max_iters_dev = c->flags + F_MAX_ITERS;
 
-    if (o.precision == KNOR_PREC_BF16) {
+    if (tc_form) {
         // The precision form scans every point each iteration (no MTI bounds):
         // its sums move by deltas through partial slot 0.
         c->prec = true;
@@ -695,7 +704,8 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, (uint16_t **)&c->Cb, kd));
         KC(dalloc(c, &c->xn, (size_t)n));
         KC(dalloc(c, &c->cn, (size_t)k));
-        KC(dalloc(c, &c->cmax, 1));
+        KC(dalloc(c, &c->pit, 1));
+        KC(dalloc(c, &c->absmax, 1));
         KC(dalloc(c, &c->a_next, (size_t)n));
         KC(dalloc(c, &c->rlist, (size_t)n));
         KC(dalloc(c, &c->rcand, (size_t)n * PREC_CANDS));
@@ -703,10 +713,21 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, &c->rm1, (size_t)n));
         KC(dalloc(c, &c->rxn, (size_t)n));
         KC(dalloc(c, &c->rcount, 1));
-        KCU(prec_points(c->X, n, d, c->Xb, c->xn, c->stream));
-        KC(encode_bf16_map(c, c->tmX, c->Xb, (uint64_t)d, (uint64_t)n, 128));
-        KC(encode_bf16_map(c, c->tmC, c->Cb, (uint64_t)d, (uint64_t)k, 256));
-        KC(encode_bf16_map(c, c->tmXc, c->Xc, (uint64_t)d, (uint64_t)n, 128));
+        c->fmt = o.precision == KNOR_PREC_FP16 ? PREC_FMT_FP16 : PREC_FMT_BF16;
+        int ex = 0;
+        if (c->fmt == PREC_FMT_FP16) {
+            // point scale 2^ex from the largest |x_j| (read back once)
+            float am = 0.0f;
+            KCU(prec_absmax(c->X, (int64_t)nd, c->absmax, c->stream));
+            KCU(cudaMemcpyAsync(&am, c->absmax, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            KCU(cudaStreamSynchronize(c->stream));
+            ex = prec_point_scale_exp(c->fmt, am);
+        }
+        c->sx = std::ldexp(1.0f, ex);
+        KCU(prec_points(c->X, n, d, c->fmt, c->sx, c->Xb, c->xn, c->stream));
+        KC(encode_op_map(c, c->tmX, c->Xb, (uint64_t)d, (uint64_t)n, 128));
+        KC(encode_op_map(c, c->tmC, c->Cb, (uint64_t)d, (uint64_t)k, 256));
+        KC(encode_op_map(c, c->tmXc, c->Xc, (uint64_t)d, (uint64_t)n, 128));
         c->prec_smem = prec_smem_bytes(d, k);
         int smem_optin = 0;
         KCU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
@@ -718,16 +739,16 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         const int64_t ntile = (n + 127) / 128;
         c->prec_grid = (int)std::min<int64_t>(c->num_sms, ntile);
         PrecParams &pp = c->pp;
-        pp.n = n; pp.d = d; pp.k = k; pp.xn = c->xn; pp.cn = c->cn; pp.cmax = c->cmax;
+        pp.n = n; pp.d = d; pp.k = k; pp.xn = c->xn; pp.cn = c->cn; pp.it = c->pit;
         pp.a_next = c->a_next; pp.rlist = c->rlist; pp.rcount = c->rcount; pp.rcand = c->rcand;
         pp.rm1 = c->rm1; pp.rxn = c->rxn; pp.mode = 0;
-        prec_error_constants(d, &pp.eA, &pp.eB);
+        prec_error_constants(c->fmt, d, c->sx, pp);
         pp.err = c->flags + F_ERR;
         c->pp2 = pp;
         c->pp2.mode = 1;
-        c->kname[KNOR_KERNEL_DENSE] = "k_bf16_assign";
+        c->kname[KNOR_KERNEL_DENSE] = "k_tc_assign";
         c->kname[KNOR_KERNEL_RECHECK] =
-            "k_prec_gather + k_bf16_assign (candidates) + k_recheck<" + std::to_string(c->dv) + ">";
+            "k_prec_gather + k_tc_assign (candidates) + k_recheck<" + std::to_string(c->dv) + ">";
         c->kname[KNOR_KERNEL_SUMS] = "k_delta_sums";
     }
     // C^0

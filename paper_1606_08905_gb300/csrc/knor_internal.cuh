@@ -118,13 +118,25 @@ struct FinParams {
 // padded to 12 ints = three int4).
 constexpr int PREC_CANDS = 16;
 
+// Per-iteration quantities of the precision form, written on the device
+// before the tensor-core scan: norms and the centroid scale.
+struct PrecIter {
+    float cnorm_max; // max ||c|| rounded up (atomicMax on the bits)
+    float cabs_max;  // max |c_j| (atomicMax on the bits)
+    float neg2inv;   // -2 / (s_x s_c): a power of two
+    float eta_c;     // sqrt(d) * (absolute rounding error of a scaled coordinate) / s_c, rounded up
+};
+
+// Operand format of the precision form's tensor-core scan.
+enum PrecFormat : int32_t { PREC_FMT_BF16 = 0, PREC_FMT_FP16 = 1 };
+
 // Parameters of the precision-form assignment (precision.cu).
 struct PrecParams {
     int64_t n;
     int32_t d, k;
     const float *xn;     // n: ||x||^2 (FP64 sum rounded to FP32)
     const float *cn;     // k: ||c||^2
-    const float *cmax;   // max ||c|| rounded up
+    const PrecIter *it;  // this iteration's centroid quantities
     int32_t *a_next;     // n: new assignment of certified points
     int32_t *rlist;      // points to re-score exactly
     int32_t *rcand;      // per listed point: two lists (one per half of the columns), each a
@@ -133,7 +145,11 @@ struct PrecParams {
     const float *rxn;    // mode 1: ||x||^2 of the gathered points
     int32_t mode;        // 0: all points, certify or list; 1: listed points, record candidates
     unsigned *rcount;
-    float eA, eB;        // E(x) = eA |x| Cmax + eB (|x|^2 + Cmax^2), rounded up
+    uint32_t idesc;      // tcgen05 instruction descriptor (operand format)
+    // error bound E(x) (prec_error_constants): unit roundoff of the operand
+    // format, sqrt(d) * absolute error of a scaled point coordinate / s_x,
+    // tensor-core accumulation factor, FP32 epilogue and distance factors
+    float uq, eta_x, gtc, eA32, eB;
     int32_t *err;        // set when a bounded wait gives up
 };
 
@@ -171,12 +187,16 @@ void set_global_error(const char *msg); // message for knor_last_error(NULL)
 
 // precision form (precision.cu)
 size_t prec_smem_bytes(int d, int k);
-cudaError_t prec_points(const float *X, int64_t n, int32_t d, void *Xb, float *xn, cudaStream_t s);
-cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, void *Cb, float *cn, float *cmax, cudaStream_t s);
+cudaError_t prec_absmax(const float *X, int64_t count, float *out, cudaStream_t s);
+cudaError_t prec_points(const float *X, int64_t n, int32_t d, int32_t fmt, float sx, void *Xb, float *xn,
+                        cudaStream_t s);
+cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, int32_t fmt, float sx, void *Cb, float *cn,
+                      PrecIter *it, cudaStream_t s);
+int prec_point_scale_exp(int32_t fmt, float absmax); // s_x = 2^this
 cudaError_t prec_assign_attr(size_t smem);
 // tmX / tmC point to CUtensorMap objects (cuda.h) over the BF16 points / centroids
 cudaError_t prec_assign(const void *tmX, const void *tmC, const PrecParams &p, int grid, size_t smem, cudaStream_t s);
-void prec_error_constants(int d, float *eA, float *eB);
+void prec_error_constants(int32_t fmt, int d, float sx, PrecParams &p);
 cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
                          const int32_t *rcand, const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid,
                          cudaStream_t s);

@@ -1,25 +1,27 @@
-// precision.cu -- the precision form of the assignment step (BF16 tensor
-// cores with an exact FP32 recheck).
+// precision.cu -- the precision forms of the assignment step (BF16 or FP16
+// tensor cores with an exact FP32 recheck).
 //
 // The distance block d~^2(x, c) = ||x||^2 - 2 x~.c~ + ||c||^2 is formed with
-// x~, c~ the BF16 roundings of the FP32 point and centroid: the dot products
-// run on the 5th-generation tensor cores (tcgen05.mma, kind::f16, BF16 x BF16
-// -> FP32 in tensor memory), fed by TMA tiles in 128-byte-swizzled shared
-// memory.  The epilogue keeps each point's smallest and second smallest d~^2
-// over all centroids.  A point whose gap min2 - min1 exceeds 2 E(x) -- E(x)
-// bounds the BF16 error of d~^2 plus the error of the library's FP32 distance
+// x~, c~ the 16-bit roundings of the FP32 point and centroid (FP16 operands
+// are first scaled by powers of two into range): the dot products run on the
+// 5th-generation tensor cores (tcgen05.mma, kind::f16, FP32 accumulation in
+// tensor memory), fed by TMA tiles in 128-byte-swizzled shared memory.  The
+// epilogue keeps each point's smallest and second smallest d~^2 over all
+// centroids.  A point whose gap min2 - min1 exceeds 2 E(x) -- E(x) bounds the
+// error of d~^2 plus the error of the library's FP32 distance
 // (prec_error_constants below) -- provably has the same nearest centroid under
 // the FP32 distance of the plain path.  The other points are gathered and run
 // through the same kernel a second time, which records every centroid within
 // min1 + 2 E(x) (a handful); those candidates are re-scored exactly in FP32
-// (all k when more than eight were recorded).  The assignments are therefore
-// identical to the plain FP32 path's.  The cluster sums are then updated by
-// the deltas of the points that changed cluster.
+// (all k when more than seven per half were recorded).  The assignments are
+// therefore identical to the plain FP32 path's.  The cluster sums are then
+// updated by the deltas of the points that changed cluster.
 //
 // The paper has no GEMM path (its serial baseline table notes that GEMM codes
 // were slower on its CPUs); this form is an addition for the tensor cores.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cmath>
 
@@ -93,13 +95,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
-// A BF16 (7-9 = 1), B BF16 (10-12 = 1), both K-major (15, 16 = 0),
-// N >> 3 (17-22), M >> 4 (24-28).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// A and B of one format (bits 7-9 and 10-12: 0 = FP16, 1 = BF16; the two
+// must match), both K-major (15, 16 = 0), N >> 3 (17-22), M >> 4 (24-28).
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t ab_format) {
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
@@ -143,6 +146,19 @@ __device__ __forceinline__ void top2_merge(float &m1, float &m2, int &i1, float 
     if (b1 < m1) { m1 = b1; i1 = bi; }
 }
 
+// 2E(x) for a point with ||x||^2 = xn (see prec_error_constants), every
+// operation rounded up.  C bounds ||c||, zeta bounds ||c~ - c|| (c~ the scaled
+// and rounded centroid, unscaled), Cz = C + zeta.
+__device__ __forceinline__ float prec_two_e(float xn, float C, float zeta, float Cz, const PrecParams &p) {
+    const float X = __fsqrt_ru(__fmul_ru(fmaxf(xn, 0.0f), 1.0000005f)); // covers the rounding of xn
+    const float xi = __fmaf_ru(p.uq, X, p.eta_x);                       // bound on ||x~ - x||
+    const float Xx = __fadd_ru(X, xi);
+    // |x.c - acc| <= ||x|| zeta + xi (C + zeta) + g_tc (X + xi)(C + zeta)
+    const float etc = __fmaf_ru(X, zeta, __fmaf_ru(xi, Cz, __fmul_ru(p.gtc, __fmul_ru(Xx, Cz))));
+    const float e32 = __fmaf_ru(p.eA32, __fmul_ru(Xx, Cz), __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C))));
+    return __fmul_ru(2.0f, __fmaf_ru(2.02f, etc, e32));
+}
+
 // ---------------------------------------------------------------- layout
 
 constexpr int TM = 128;              // points per tile (MMA M)
@@ -173,7 +189,7 @@ size_t prec_smem_bytes(int d, int k) {
 // point; the two warps of a lane quarter take one half of the columns each)
 // while the next chunk is being multiplied.
 __global__ void __launch_bounds__(PREC_THREADS, 1)
-    k_bf16_assign(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC,
+    k_tc_assign(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC,
                   const PrecParams p) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(TM, TN);
+            const uint32_t idesc = p.idesc;
             uint32_t ca = 0, cb = 0, cbuf = 0; // consumed A fills, B fills, accumulators issued
             for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
                 const int sa = ca & 1;
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                         const uint32_t a0 = smem_u32(sA + ((size_t)sa * nkc + kc) * A_BOX);
                         const uint32_t b0 = smem_u32(sB + ((size_t)sb * nkc + kc) * B_BOX);
                         for (int kk = 0; kk < TKB / 16; ++kk)
-                            mma_bf16(dcol, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                            mma_f16kind(dcol, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
                                      (kc | kk) != 0 ? 1u : 0u);
                     }
                     mma_commit(&emptyB[sb]); // B slot free once these MMAs are done
@@ -307,15 +323,19 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
         int *hi1 = reinterpret_cast<int *>(hand + 2 * TM);
         uint32_t cons = 0;  // accumulators consumed
         uint32_t tiles = 0; // tiles handed between the quarter's two warps
-        const float C = *p.cmax;
+        const float C = p.it->cnorm_max;
+        const float neg2inv = p.it->neg2inv;
+        const float zeta = __fmaf_ru(p.uq, C, p.it->eta_c); // bound on ||c~ - c||
+        const float Cz = __fadd_ru(C, zeta);
         for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
             const int64_t row = t * TM + rloc;
             const bool valid = row < nrows;
             const float xn = valid ? (p.mode ? p.rxn[row] : p.xn[row]) : 0.0f;
-            const float X = __fsqrt_ru(fmaxf(xn, 0.0f));
-            const float twoE = __fmul_ru(2.0f, __fmaf_ru(p.eA, __fmul_ru(X, C),
-                                                         __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C)))));
+            const float twoE = prec_two_e(xn, C, zeta, Cz, p);
+            // twoE = +inf (an unrepresentable scale) sends every point to the
+            // full FP32 scan
             const float thr = (p.mode && valid) ? __fadd_ru(p.rm1[row], twoE) : -CUDART_INF_F;
+            const bool all_cands = p.mode && !(twoE < CUDART_INF_F);
             // four independent chains (columns u mod 4) keep the dependent
             // min/max sequences short
             float a1[4], a2[4];
@@ -348,29 +368,36 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
 #pragma unroll
                         for (int v = 0; v < 16; ++v) {
                             const float4 cv = cn4[v];
-                            top2_step(a1[0], a2[0], ai[0], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 0]), cv.x), cb + 4 * v + 0);
-                            top2_step(a1[1], a2[1], ai[1], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 1]), cv.y), cb + 4 * v + 1);
-                            top2_step(a1[2], a2[2], ai[2], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 2]), cv.z), cb + 4 * v + 2);
-                            top2_step(a1[3], a2[3], ai[3], __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 3]), cv.w), cb + 4 * v + 3);
+                            top2_step(a1[0], a2[0], ai[0], __fmaf_rn(__uint_as_float(r[4 * v + 0]), neg2inv, cv.x), cb + 4 * v + 0);
+                            top2_step(a1[1], a2[1], ai[1], __fmaf_rn(__uint_as_float(r[4 * v + 1]), neg2inv, cv.y), cb + 4 * v + 1);
+                            top2_step(a1[2], a2[2], ai[2], __fmaf_rn(__uint_as_float(r[4 * v + 2]), neg2inv, cv.z), cb + 4 * v + 2);
+                            top2_step(a1[3], a2[3], ai[3], __fmaf_rn(__uint_as_float(r[4 * v + 3]), neg2inv, cv.w), cb + 4 * v + 3);
                         }
                     } else {
-                        bool any = false;
+                        // bit u of (mlo, mhi): column cb + u is a candidate
+                        uint32_t mlo = 0, mhi = 0;
 #pragma unroll
                         for (int v = 0; v < 16; ++v) {
                             const float4 cv = cn4[v];
-                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 0]), cv.x) <= thr;
-                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 1]), cv.y) <= thr;
-                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 2]), cv.z) <= thr;
-                            any |= __fmaf_rn(-2.0f, __uint_as_float(r[4 * v + 3]), cv.w) <= thr;
-                        }
-                        if (any) { // rare: record the group's candidates
+                            const float tv[4] = {__fmaf_rn(__uint_as_float(r[4 * v + 0]), neg2inv, cv.x),
+                                                 __fmaf_rn(__uint_as_float(r[4 * v + 1]), neg2inv, cv.y),
+                                                 __fmaf_rn(__uint_as_float(r[4 * v + 2]), neg2inv, cv.z),
+                                                 __fmaf_rn(__uint_as_float(r[4 * v + 3]), neg2inv, cv.w)};
 #pragma unroll
-                            for (int u = 0; u < 64; ++u) {
-                                if (__fmaf_rn(-2.0f, __uint_as_float(r[u]), cn_s[cb + u]) <= thr) {
-                                    if (nc < PREC_CANDS / 2 - 1) cd[1 + nc] = cb + u;
-                                    ++nc;
+                            for (int w = 0; w < 4; ++w) {
+                                const int u = 4 * v + w;
+                                if (tv[w] <= thr) {
+                                    if (u < 32) mlo |= 1u << u;
+                                    else mhi |= 1u << (u - 32);
                                 }
                             }
+                        }
+                        while (mlo | mhi) { // a few per point: record them in column order
+                            int u;
+                            if (mlo) { u = __ffs(mlo) - 1; mlo &= mlo - 1; }
+                            else { u = 32 + __ffs(mhi) - 1; mhi &= mhi - 1; }
+                            if (nc < PREC_CANDS / 2 - 1) cd[1 + nc] = cb + u;
+                            ++nc;
                         }
                     }
                 }
@@ -381,7 +408,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
             }
             if (!ok) break;
             if (p.mode == 1) {
-                if (valid) cd[0] = nc < PREC_CANDS / 2 ? nc : -1;
+                if (valid) cd[0] = (nc < PREC_CANDS / 2 && !all_cands) ? nc : -1;
                 continue;
             }
             float m1 = a1[0], m2 = a2[0];
@@ -442,10 +469,12 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
 // Exact FP32 re-score of the points the tensor-core pass could not certify,
 // with the library's FP32 distance and lowest index on ties: one thread per
 // point over its recorded candidates (two lists, one per half of the
-// columns), or, when a list overflowed, one warp over all centroids.
+// columns; four candidates at a time, the point row streamed through L1), or,
+// when a list overflowed, one warp over all centroids.
 template <int DV>
-__global__ void k_recheck(const float *X, const float *C32, int32_t k, const int32_t *rlist, const int32_t *rcand,
-                          const unsigned *rcount, int32_t *a_next, Counters *ctr) {
+__global__ void __launch_bounds__(256) k_recheck(const float *X, const float *C32, int32_t k, const int32_t *rlist,
+                                                 const int32_t *rcand, const unsigned *rcount, int32_t *a_next,
+                                                 Counters *ctr) {
     constexpr int HC = PREC_CANDS / 2;
     const unsigned cnt = *rcount;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -455,17 +484,39 @@ __global__ void k_recheck(const float *X, const float *C32, int32_t k, const int
         const int32_t *cd = rcand + (size_t)e * PREC_CANDS;
         const int n0 = cd[0], n1 = cd[HC];
         if (n0 < 0 || n1 < 0) continue; // overflow: scored by the warp pass below
+        const int nc = n0 + n1;
         const int32_t i = rlist[e];
-        unsigned long long x2[DV / 2];
-        ldg_x2<DV>(x2, X + (int64_t)i * DV);
+        const float *xr = X + (int64_t)i * DV;
         float bd = CUDART_INF_F;
         int best = 0x7fffffff;
-        for (int t = 0; t < n0 + n1; ++t) {
-            const int c = t < n0 ? cd[1 + t] : cd[HC + 1 + (t - n0)];
-            const float r = d2_reg<DV>(x2, C32 + (size_t)c * DV);
-            if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+        for (int qb = 0; qb < nc; qb += 4) {
+            const float *cr[4];
+            int cc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int t = qb + q < nc ? qb + q : qb; // padding repeats a candidate
+                cc[q] = t < n0 ? cd[1 + t] : cd[HC + 1 + (t - n0)];
+                cr[q] = C32 + (size_t)cc[q] * DV;
+            }
+            unsigned long long acc[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+#pragma unroll 8
+            for (int j = 0; j < DV; j += 4) {
+                const float4 xv = __ldg(reinterpret_cast<const float4 *>(xr + j));
+                const unsigned long long xa = pack2(xv.x, xv.y), xb = pack2(xv.z, xv.w);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(cr[q] + j));
+                    acc[q] = sqacc2(sub2(xa, pack2(v.x, v.y)), acc[q]);
+                    acc[q] = sqacc2(sub2(xb, pack2(v.z, v.w)), acc[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float r = fold2(acc[q]);
+                if (r < bd || (r == bd && cc[q] < best)) { bd = r; best = cc[q]; }
+            }
         }
-        evals += n0 + n1;
+        evals += nc;
         a_next[i] = best;
     }
     // points with too many candidates: one warp per point, lanes over centroids
@@ -473,13 +524,20 @@ __global__ void k_recheck(const float *X, const float *C32, int32_t k, const int
     const int64_t wid = gtid >> 5, nw = nthreads >> 5;
     for (int64_t e = wid; e < cnt; e += nw) {
         if (rcand[(size_t)e * PREC_CANDS] >= 0 && rcand[(size_t)e * PREC_CANDS + HC] >= 0) continue;
-        const int32_t i = rlist[e];
-        unsigned long long x2[DV / 2];
-        ldg_x2<DV>(x2, X + (int64_t)i * DV);
+        const float *xr = X + (int64_t)rlist[e] * DV; // the same row for every lane
         float bd = CUDART_INF_F;
         int best = 0x7fffffff;
         for (int c = lane; c < k; c += 32) {
-            const float r = d2_reg<DV>(x2, C32 + (size_t)c * DV);
+            const float *cr = C32 + (size_t)c * DV;
+            unsigned long long acc = 0ULL;
+#pragma unroll 8
+            for (int j = 0; j < DV; j += 4) {
+                const float4 xv = __ldg(reinterpret_cast<const float4 *>(xr + j));
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(cr + j));
+                acc = sqacc2(sub2(pack2(xv.x, xv.y), pack2(v.x, v.y)), acc);
+                acc = sqacc2(sub2(pack2(xv.z, xv.w), pack2(v.z, v.w)), acc);
+            }
+            const float r = fold2(acc);
             if (r < bd) { bd = r; best = c; }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -487,18 +545,18 @@ __global__ void k_recheck(const float *X, const float *C32, int32_t k, const int
             const int oi = __shfl_xor_sync(FULL_MASK, best, o);
             if (ob < bd || (ob == bd && oi < best)) { bd = ob; best = oi; }
         }
-        if (lane == 0) { a_next[i] = best; evals += k; }
+        if (lane == 0) { a_next[rlist[e]] = best; evals += k; }
     }
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL_MASK, evals, o);
     if (lane == 0 && evals) atomicAdd(&ctr->evals, evals);
     if (gtid == 0) atomicAdd(&ctr->rechecked, (unsigned long long)cnt);
 }
 
-// Gathers the BF16 rows (and ||x||^2) of the listed points into a compact
+// Gathers the 16-bit operand rows (and ||x||^2) of the listed points into a compact
 // matrix for the candidate pass: one warp per point, 16 bytes per lane.
 template <int DV>
-__global__ void k_prec_gather(const __nv_bfloat16 *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
-                              __nv_bfloat16 *Xc, float *rxn) {
+__global__ void k_prec_gather(const uint16_t *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
+                              uint16_t *Xc, float *rxn) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -561,30 +619,89 @@ __global__ void k_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, 
     if (lane == 0 && changed) atomicAdd(&ctr->changed, changed);
 }
 
-// Per iteration: BF16 centroids, ||c||^2 (FP64 sum of the FP32 values,
-// rounded to nearest FP32) and max ||c|| (rounded up), one CTA per centroid.
-__global__ void k_prec_prep(const float *C32, int32_t d, __nv_bfloat16 *Cb, float *cn, float *cmax) {
+template <int FMT>
+__device__ __forceinline__ uint16_t to_op(float v) {
+    if (FMT == PREC_FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return __half_as_ushort(__float2half_rn(v));
+}
+
+// Exponent e of the scale 2^e of an FP16 operand: the largest with
+// absmax * 2^e <= 2^15 (half of the FP16 range), clamped to [-60, 60].
+// BF16 has the FP32 exponent range and is not scaled.
+__host__ __device__ inline int scale_exp(int32_t fmt, float absmax) {
+    if (fmt == PREC_FMT_BF16) return 0;
+    if (!(absmax > 0.0f)) return 60;
+    int ex;
+    const float m = frexpf(absmax, &ex); // absmax = m 2^ex, m in [0.5, 1)
+    const int cl = (m == 0.5f) ? ex - 1 : ex; // ceil(log2(absmax))
+    const int e = 15 - cl;
+    return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+
+// Per iteration, step 1: ||c||^2 (FP64 sum of the FP32 values, rounded to
+// nearest), max ||c|| (rounded up) and max |c_j|; one CTA per centroid.
+__global__ void k_prec_cnorm(const float *C32, int32_t d, float *cn, PrecIter *it) {
     const int c = blockIdx.x;
     __shared__ double red[128];
+    __shared__ float amax[128];
     double acc = 0.0;
+    float am = 0.0f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const float v = C32[(size_t)c * d + j];
-        Cb[(size_t)c * d + j] = __float2bfloat16_rn(v);
         acc += (double)v * (double)v;
+        am = fmaxf(am, fabsf(v));
     }
     red[threadIdx.x] = acc;
+    amax[threadIdx.x] = am;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+        float m = 0.0f;
+        for (int i = 0; i < (int)blockDim.x; ++i) { t += red[i]; m = fmaxf(m, amax[i]); }
         cn[c] = __double2float_rn(t);
         const float nrm = __double2float_ru(__dsqrt_ru(__dmul_ru(t, 1.0 + 1e-15)));
-        atomicMax(reinterpret_cast<int *>(cmax), __float_as_int(nrm)); // non-negative floats order as ints
+        // non-negative floats order as ints
+        atomicMax(reinterpret_cast<int *>(&it->cnorm_max), __float_as_int(nrm));
+        atomicMax(reinterpret_cast<int *>(&it->cabs_max), __float_as_int(m));
     }
 }
 
-// Once per context: BF16 points and ||x||^2 (FP64 sum, rounded to nearest).
-__global__ void k_prec_points(const float *X, int64_t n, int32_t d, __nv_bfloat16 *Xb, float *xn) {
+// Per iteration, step 2: the scaled, rounded centroids c~ = fmt(c s_c), and
+// (block 0) the scale-dependent constants.
+template <int FMT>
+__global__ void k_prec_conv(const float *C32, int64_t kd, int32_t d, float sx, uint16_t *Cb, PrecIter *it) {
+    const float M = it->cabs_max;
+    const int ec = scale_exp(FMT, M);
+    const float sc = ldexpf(1.0f, ec);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < kd; i += (int64_t)gridDim.x * blockDim.x)
+        Cb[i] = to_op<FMT>(C32[i] * sc); // a power-of-two scale: exact
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int ex;
+        frexpf(sx, &ex); // sx = 2^(ex - 1)
+        it->neg2inv = ldexpf(-2.0f, -(ex - 1) - ec);
+        // absolute error of one rounded coordinate in the scaled domain:
+        // half the smallest FP16 subnormal (2^-25), or for BF16 anything
+        // above half its smallest subnormal (2^-134); taken with a margin
+        const double eta = FMT == PREC_FMT_BF16 ? 0x1p-100 : 0x1p-24;
+        float ec_bound = __double2float_ru(sqrt((double)d) * 1.000001 * eta * ldexp(1.0, -ec));
+        if (FMT != PREC_FMT_BF16 && !(M * sc <= 32768.0f)) ec_bound = CUDART_INF_F; // unrepresentable
+        it->eta_c = ec_bound;
+    }
+}
+
+// Largest |x_j| over the points (once per context, for the point scale).
+__global__ void k_prec_absmax(const float *X, int64_t count, float *out) {
+    float m = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(X[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
+}
+
+// Once per context: scaled, rounded points x~ = fmt(x s_x) and ||x||^2
+// (FP64 sum, rounded to nearest).
+template <int FMT>
+__global__ void k_prec_points(const float *X, int64_t n, int32_t d, float sx, uint16_t *Xb, float *xn) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -592,7 +709,7 @@ __global__ void k_prec_points(const float *X, int64_t n, int32_t d, __nv_bfloat1
         double acc = 0.0;
         for (int j = lane; j < d; j += 32) {
             const float v = X[i * d + j];
-            Xb[i * d + j] = __float2bfloat16_rn(v);
+            Xb[i * d + j] = to_op<FMT>(v * sx);
             acc += (double)v * (double)v;
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
@@ -602,40 +719,67 @@ __global__ void k_prec_points(const float *X, int64_t n, int32_t d, __nv_bfloat1
 
 // ------------------------------------------------------------- launchers
 
-// Constants of the certification bound E(x) = eA |x| Cmax + eB (|x|^2 + Cmax^2)
-// on |d~^2 - d^2| plus the error of the FP32 distance, with u_b = 2^-8 (BF16
-// rounding of x and c), the tensor-core FP32 accumulation of the d products
-// allowed 2^-23 per addition (truncation) and a factor 2, u = 2^-24:
-//   |x.c - x~.c~|  <= (2 u_b + u_b^2 + g_tc (1 + u_b)^2) |x| |c|   (Cauchy-Schwarz)
-//   epilogue: ||x||^2 and ||c||^2 rounded once each, one add, one fma
-//   FP32 distance of the plain path: relative (d + 2) u / (1 - (d + 2) u) of
-//   d^2 <= 2 (|x|^2 + |c|^2)
-// so eA = 2 (2 u_b + u_b^2 + g_tc (1 + u_b)^2) + 2 u and
-//    eB = 3 u + 2 g_d, each with 1 % of slack and rounded up.
-void prec_error_constants(int d, float *eA, float *eB) {
-    const double ub = std::ldexp(1.0, -8), u = std::ldexp(1.0, -24);
+// Constants of the certification bound.  With x~, c~ the operands the tensor
+// cores see (unscaled), u_q the unit roundoff of the format (BF16 2^-8, FP16
+// 2^-11) and eta the absolute error of a rounded scaled coordinate (FP16
+// subnormals):
+//   ||x~ - x|| <= xi = u_q ||x|| + sqrt(d) eta / s_x,  ||c~ - c|| <= zeta
+//   |x.c - x~.c~| <= ||x|| zeta + xi (||c|| + zeta)
+//   tensor-core FP32 accumulation of d products: at most g_tc ||x~|| ||c~||
+//     with g_tc = 2d 2^-23 / (1 - 2d 2^-23) (truncating adds, a factor 2)
+//   epilogue t = fma(acc, -2/(s_x s_c), ||c||^2): ||c||^2 rounded once and
+//     the fma once, <= u (||c||^2 + |t|) <= 2u ||x~|| ||c~|| + 2u ||c||^2
+//   FP32 distance of the plain path: relative (d + 2) u / (1 - (d + 2) u)
+//     of d^2 <= 2 (||x||^2 + ||c||^2)
+// with u = 2^-24.  E = 2 (1.01) (dot error + accumulation) + eA32 ||x~|| ||c~||
+// + eB (||x||^2 + ||c||^2), eA32 = 1.01 (2u), eB = 1.01 (3u + 2 g_d), each
+// rounded up (prec_two_e evaluates it per point).
+void prec_error_constants(int32_t fmt, int d, float sx, PrecParams &p) {
+    const double u = std::ldexp(1.0, -24);
     const double gtc = 2.0 * d * std::ldexp(1.0, -23) / (1.0 - 2.0 * d * std::ldexp(1.0, -23));
     const double g = (d + 2) * u / (1.0 - (d + 2) * u);
-    const double a1 = 2 * ub + ub * ub + gtc * (1 + ub) * (1 + ub);
-    const double A = 1.01 * (2 * a1 + 2 * u), B = 1.01 * (3 * u + 2 * g);
-    *eA = std::nextafter((float)A, INFINITY);
-    *eB = std::nextafter((float)B, INFINITY);
+    const double eta = fmt == PREC_FMT_BF16 ? std::ldexp(1.0, -100) : std::ldexp(1.0, -24);
+    p.uq = fmt == PREC_FMT_BF16 ? std::ldexp(1.0f, -8) : std::ldexp(1.0f, -11);
+    p.gtc = std::nextafter((float)gtc, INFINITY);
+    p.eta_x = std::nextafter((float)(std::sqrt((double)d) * 1.000001 * eta / sx), INFINITY);
+    p.eA32 = std::nextafter((float)(1.01 * 2 * u), INFINITY);
+    p.eB = std::nextafter((float)(1.01 * (3 * u + 2 * g)), INFINITY);
+    p.idesc = idesc_f16kind(TM, TN, fmt == PREC_FMT_BF16 ? 1u : 0u);
 }
 
-cudaError_t prec_points(const float *X, int64_t n, int32_t d, void *Xb, float *xn, cudaStream_t s) {
-    k_prec_points<<<1024, 256, 0, s>>>(X, n, d, static_cast<__nv_bfloat16 *>(Xb), xn);
+int prec_point_scale_exp(int32_t fmt, float absmax) { return scale_exp(fmt, absmax); }
+
+cudaError_t prec_absmax(const float *X, int64_t count, float *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    k_prec_absmax<<<1024, 256, 0, s>>>(X, count, out);
     return cudaGetLastError();
 }
 
-cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, void *Cb, float *cn, float *cmax, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(float), s);
+cudaError_t prec_points(const float *X, int64_t n, int32_t d, int32_t fmt, float sx, void *Xb, float *xn,
+                        cudaStream_t s) {
+    uint16_t *o = static_cast<uint16_t *>(Xb);
+    if (fmt == PREC_FMT_BF16) k_prec_points<PREC_FMT_BF16><<<1024, 256, 0, s>>>(X, n, d, sx, o, xn);
+    else k_prec_points<PREC_FMT_FP16><<<1024, 256, 0, s>>>(X, n, d, sx, o, xn);
+    return cudaGetLastError();
+}
+
+cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, int32_t fmt, float sx, void *Cb, float *cn,
+                      PrecIter *it, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(it, 0, sizeof(PrecIter), s);
     if (e != cudaSuccess) return e;
-    k_prec_prep<<<k, 128, 0, s>>>(C32, d, static_cast<__nv_bfloat16 *>(Cb), cn, cmax);
+    k_prec_cnorm<<<k, 128, 0, s>>>(C32, d, cn, it);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t kd = (int64_t)k * d;
+    const int grid = (int)std::min<int64_t>((kd + 255) / 256, 1024);
+    uint16_t *o = static_cast<uint16_t *>(Cb);
+    if (fmt == PREC_FMT_BF16) k_prec_conv<PREC_FMT_BF16><<<grid, 256, 0, s>>>(C32, kd, d, sx, o, it);
+    else k_prec_conv<PREC_FMT_FP16><<<grid, 256, 0, s>>>(C32, kd, d, sx, o, it);
     return cudaGetLastError();
 }
 
 cudaError_t prec_assign_attr(size_t smem) {
-    return cudaFuncSetAttribute(k_bf16_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_tc_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t prec_assign_maps(const CUtensorMap &tmX, const CUtensorMap &tmC, const PrecParams &p, int grid, size_t smem, cudaStream_t s);
@@ -647,7 +791,7 @@ cudaError_t prec_assign(const void *tmX, const void *tmC, const PrecParams &p, i
 
 cudaError_t prec_assign_maps(const CUtensorMap &tmX, const CUtensorMap &tmC, const PrecParams &p, int grid,
                              size_t smem, cudaStream_t s) {
-    k_bf16_assign<<<grid, PREC_THREADS, smem, s>>>(tmX, tmC, p);
+    k_tc_assign<<<grid, PREC_THREADS, smem, s>>>(tmX, tmC, p);
     return cudaGetLastError();
 }
 
@@ -664,8 +808,8 @@ cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, co
 
 cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
                         void *Xc, float *rxn, int grid, cudaStream_t s) {
-    const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(Xb);
-    __nv_bfloat16 *b = static_cast<__nv_bfloat16 *>(Xc);
+    const uint16_t *a = static_cast<const uint16_t *>(Xb);
+    uint16_t *b = static_cast<uint16_t *>(Xc);
     switch (dv) {
     case 64: k_prec_gather<64><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;
     case 128: k_prec_gather<128><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;

@@ -19,7 +19,7 @@ _lib = None
 
 KNOR_OK, KNOR_ERR_ARG, KNOR_ERR_OOM, KNOR_ERR_CUDA, KNOR_ERR_TIMEOUT, KNOR_ERR_STATE = 0, -1, -2, -3, -4, -5
 KNOR_INIT_FORGY, KNOR_INIT_EXPLICIT = 0, 1
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
 
 
 class KnorError(RuntimeError):

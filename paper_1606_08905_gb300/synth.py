@@ -179,7 +179,7 @@ WORKLOADS = {
     "mti_66m_d32_k20": dict(kind="spd", n=66_000_000, d=32, k=20, data_seed=1002,
                             max_iters=50, prune=True),
     "precision_10m_d128_k1024": dict(kind="aniso", n=10_000_000, d=128, k=1024,
-                                     data_seed=1003, max_iters=30, prune=False, precision="bf16"),
+                                     data_seed=1003, max_iters=30, prune=False, precision="fp16"),
     "scale_1b_d16_k100_uniform": dict(kind="uniform", n=1_000_000_000, d=16, k=100,
                                       data_seed=1005, max_iters=20, prune=True),
     "scale_1b_d16_k100_mixture": dict(kind="spd_scaled", n=1_000_000_000, d=16, k=100,

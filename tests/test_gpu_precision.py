@@ -1,5 +1,5 @@
-"""GPU parity of the precision form (BF16 tensor-core distances with an exact
-FP32 recheck of the points whose top-2 gap is inside the error bound).
+"""GPU parity of the precision forms (BF16 or FP16 tensor-core distances with
+an exact FP32 recheck of the points whose top-2 gap is inside the error bound).
 
 The form is certified to return exactly the FP32 assignment of the plain path:
 at every iteration its assignments must equal, bit for bit, the oracle's FP32
@@ -27,10 +27,13 @@ def _lib():
     knor.load()
 
 
-def _run_checked(X, k, iters, seed=42, init=None):
+FORMS = ["bf16", "fp16"]
+
+
+def _run_checked(X, k, iters, seed=42, init=None, form="bf16"):
     Xd = torch.as_tensor(X).cuda()
     rechecked = 0
-    with knor.Context(Xd, k, seed=seed, precision="bf16", init="explicit" if init is not None else "forgy") as c:
+    with knor.Context(Xd, k, seed=seed, precision=form, init="explicit" if init is not None else "forgy") as c:
         if init is not None:
             c.set_init_centroids(init)
         for t in range(iters):
@@ -41,11 +44,11 @@ def _run_checked(X, k, iters, seed=42, init=None):
             a32 = oracle.assign_f32(X, C32)
             bad = np.flatnonzero(a != a32)
             assert bad.size == 0, f"it {t + 1}: {bad.size} assignments differ from the FP32 argmin, e.g. {bad[:5]}"
-            check_assignments(X, C_before, a, f"bf16 it {t + 1}")
+            check_assignments(X, C_before, a, f"{form} it {t + 1}")
             C_ref, cnt = oracle.means(X, a, C_before)
-            check_centroids(c.centroids(), C_ref, f"bf16 it {t + 1}")
+            check_centroids(c.centroids(), C_ref, f"{form} it {t + 1}")
             # the tensor-core scan scores every pair; a recheck scores its
-            # recorded candidates (at most 8), or all k on overflow
+            # recorded candidates (at most 14), or all k on overflow
             assert X.shape[0] * k <= s["dist_evals"] <= X.shape[0] * k + s["rechecked"] * k
             rechecked += s["rechecked"]
             if s["changed"] == 0:
@@ -53,20 +56,40 @@ def _run_checked(X, k, iters, seed=42, init=None):
     return rechecked
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n,d,k", [(5000, 128, 64), (20011, 128, 300), (9000, 64, 256), (30000, 128, 1024),
                                    (100, 64, 3), (130, 128, 129)])
-def test_precision_form_equals_fp32_assignments(n, d, k):
+def test_precision_form_equals_fp32_assignments(n, d, k, form):
     X = synth.aniso_mixture(n, d, min(k, 64), 200 + k).numpy()
-    _run_checked(X, k, 12)
+    _run_checked(X, k, 12, form=form)
 
 
+@pytest.mark.parametrize("scale", [1e-12, 1e-3, 1e12])
+def test_fp16_form_scales_any_magnitude(scale):
+    """FP16 operands are scaled by powers of two into range: data many orders
+    of magnitude away from 1 still gives the FP32 assignments, and few points
+    need the recheck."""
+    X = (synth.aniso_mixture(8000, 64, 32, 77).numpy().astype(np.float64) * scale).astype(np.float32)
+    rechecked = _run_checked(X, 32, 4, form="fp16")
+    assert rechecked < 0.5 * 4 * X.shape[0]
+
+
+def test_fp16_form_rechecks_fewer_points_than_bf16():
+    """The FP16 bound is eight times tighter (11 significand bits against 8)."""
+    X = synth.aniso_mixture(30000, 128, 64, 1204).numpy()
+    rb = _run_checked(X, 1024, 3, form="bf16")
+    rh = _run_checked(X, 1024, 3, form="fp16")
+    assert rh < rb
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n,d,k", [(600_000, 64, 64), (300_000, 128, 256)])
-def test_precision_form_many_tiles_per_cta(n, d, k):
+def test_precision_form_many_tiles_per_cta(n, d, k, form):
     """Enough points that every CTA of the persistent kernel reuses its tile
     stages and accumulator buffers many times."""
     X = synth.aniso_mixture(n, d, min(k, 64), 300 + k).numpy()
     Xd = torch.as_tensor(X).cuda()
-    with knor.Context(Xd, k, seed=5, precision="bf16") as c:
+    with knor.Context(Xd, k, seed=5, precision=form) as c:
         for t in range(2):
             C32 = c.centroids_f32()
             c.iterate()
@@ -90,7 +113,8 @@ def test_plain_path_large_kd_matches_fp32_restatement():
             check_centroids(c.centroids(), C_ref, f"plain large kd it {t + 1}")
 
 
-def test_planted_ties_are_rechecked():
+@pytest.mark.parametrize("form", FORMS)
+def test_planted_ties_are_rechecked(form):
     """Points exactly between two centroids have a zero top-2 gap: they must be
     re-scored in FP32 (and land on the lower index)."""
     rng = np.random.default_rng(3)
@@ -100,21 +124,23 @@ def test_planted_ties_are_rechecked():
     X = np.concatenate([mids, C + 0.01 * rng.standard_normal((k, d)).astype(np.float32),
                         rng.uniform(-5, 5, (3000, d)).astype(np.float32)])
     Xd = torch.as_tensor(X).cuda()
-    with knor.Context(Xd, k, init="explicit", precision="bf16") as c:
+    with knor.Context(Xd, k, init="explicit", precision=form) as c:
         c.set_init_centroids(C.astype(np.float64))
         s = c.iterate()
         assert s["rechecked"] >= 8
         assert np.array_equal(c.assignments(), oracle.assign_f32(X, C))
 
 
-def test_precision_form_rejects_unsupported_shapes():
+@pytest.mark.parametrize("form", FORMS)
+def test_precision_form_rejects_unsupported_shapes(form):
     X = torch.zeros((100, 32), device="cuda")
     with pytest.raises(knor.KnorError) as e:
-        knor.Context(X, 4, precision="bf16")
+        knor.Context(X, 4, precision=form)
     assert e.value.status == knor.KNOR_ERR_ARG
 
 
-def test_precision_workload_full_size_teacher_forced():
+@pytest.mark.parametrize("form", FORMS)
+def test_precision_workload_full_size_teacher_forced(form):
     """The 10M x 128, k = 1024 precision workload at full size: at iterations
     1, 2 and 5 the tensor-core form assigns every point exactly as the plain
     FP32 path started from the same centroids, and the FP64 oracle agrees on
@@ -124,7 +150,7 @@ def test_precision_workload_full_size_teacher_forced():
     rng = np.random.default_rng(1)
     sample = torch.as_tensor(np.sort(rng.choice(n, 20000, replace=False)), device="cuda")
     Xs = X[sample].cpu().numpy()
-    with knor.Context(X, k, seed=42, precision="bf16") as c:
+    with knor.Context(X, k, seed=42, precision=form) as c:
         for t in range(1, 6):
             C_before = c.centroids()
             s = c.iterate()
@@ -137,7 +163,7 @@ def test_precision_workload_full_size_teacher_forced():
                 q.iterate()
                 b = torch.empty(n, dtype=torch.int32, device="cuda")
                 q.assignments(b)
-            check_assignments(Xs, C_before, a[sample].cpu().numpy(), f"bf16 10M it {t}")
+            check_assignments(Xs, C_before, a[sample].cpu().numpy(), f"{form} 10M it {t}")
             check_assignments(Xs, C_before, b[sample].cpu().numpy(), f"fp32 10M it {t}")
             diff = int((a != b).sum())
             assert diff == 0, f"iteration {t}: {diff} assignments differ from the FP32 path (rechecked {s['rechecked']})"
