@@ -88,7 +88,10 @@ typedef struct {
     int64_t rechecked;       /* precision forms: rows re-scored exactly in FP32 */
     int32_t empty;           /* clusters with no member after the iteration */
     int32_t iteration;       /* 1-based iteration number */
-    int64_t violations;      /* debug_invariants only: bounds found below the true distance */
+    int64_t violations;      /* debug_invariants: MTI bounds found below the true distance,
+                                or (precision forms) points whose assignment differs from a
+                                full FP32 scan; precision forms always: points left without a
+                                new assignment.  Always 0 unless the library is faulty. */
 } knor_iter_stats;
 
 /* Creates a context holding a copy of the n x d FP32 points (host or device)

@@ -554,7 +554,7 @@ __global__ void k_table(const FinParams f, int32_t *mode_dense, int32_t need_tab
         r.rechecked = (long long)f.ctr->rechecked;
         r.empty = (int32_t)f.ctr->empty;
         r.iteration = total;
-        r.violations = 0;
+        r.violations = (long long)f.ctr->violations; // debug checks add theirs later
         f.stats[it] = r;
         *f.run_iter = it + 1;
         *f.total_iter = total;

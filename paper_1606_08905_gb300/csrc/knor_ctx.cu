@@ -362,6 +362,9 @@ static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long 
     KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
     KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
     KNOR_CUDA(c, cudaMemsetAsync(c->rcount, 0, sizeof(unsigned), s));
+    // every point gets a new assignment from the scan or the recheck; -1
+    // marks one that did not (k_delta_sums counts it as a violation)
+    KNOR_CUDA(c, cudaMemsetAsync(c->a_next, 0xFF, sizeof(int32_t) * (size_t)c->n, s));
     KNOR_CUDA(c, mark(0));
     KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->fmt, c->sx, c->Cb, c->cn, c->pit, s));
     KNOR_CUDA(c, prec_assign(c->tmX, c->tmC, c->pp, c->prec_grid, c->prec_smem, s));
@@ -373,6 +376,8 @@ static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long 
     KNOR_CUDA(c, prec_assign(c->tmXc, c->tmC, c->pp2, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, prec_recheck(c->dv, c->X, c->C32, c->k, c->rlist, c->rcand, c->rcount, c->a_next, c->ctr,
                               4 * c->num_sms, s));
+    if (c->opts.debug_invariants)
+        KNOR_CUDA(c, prec_verify(c->X, c->n, c->d, c->C32, c->k, c->a_next, &c->ctr->violations, s));
     KNOR_CUDA(c, mark(9));
     KNOR_CUDA(c, mark(10));
     KNOR_CUDA(c, prec_delta_sums(c->X, c->n, c->d, c->st, c->a_next, c->part_S, c->part_cnt, c->ctr, c->k,

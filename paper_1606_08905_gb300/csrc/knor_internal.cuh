@@ -202,6 +202,8 @@ cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, co
                          cudaStream_t s);
 cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
                         void *Xc, float *rxn, int grid, cudaStream_t s);
+cudaError_t prec_verify(const float *X, int64_t n, int32_t d, const float *C32, int32_t k, const int32_t *a_next,
+                        unsigned long long *viol, cudaStream_t s);
 cudaError_t prec_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next, double *S,
                             long long *cnt, Counters *ctr, int32_t k, int32_t *nslots, int32_t *fresh, int grid,
                             cudaStream_t s);

@@ -131,6 +131,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
                  : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// After tmem_wait_ld: passes the 32 loaded registers through an (empty)
+// volatile asm that follows the wait, so no instruction that reads them can
+// be scheduled before the wait (the load's outputs are not yet valid there).
+__device__ __forceinline__ void tmem_regs_ready(uint32_t *r) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+}
 
 // One d~^2 - ||x||^2 value into a (smallest, its index, second smallest) chain.
 __device__ __forceinline__ void top2_step(float &m1, float &m2, int &i1, float t, int c) {
@@ -334,7 +345,9 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
             const float twoE = prec_two_e(xn, C, zeta, Cz, p);
             // twoE = +inf (an unrepresentable scale) sends every point to the
             // full FP32 scan
-            const float thr = (p.mode && valid) ? __fadd_ru(p.rm1[row], twoE) : -CUDART_INF_F;
+            // rows past the end of the gathered list hold stale operands (any
+            // value, inf included): a NaN threshold matches nothing there
+            const float thr = (p.mode && valid) ? __fadd_ru(p.rm1[row], twoE) : CUDART_NAN_F;
             const bool all_cands = p.mode && !(twoE < CUDART_INF_F);
             // four independent chains (columns u mod 4) keep the dependent
             // min/max sequences short
@@ -343,7 +356,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 4; ++j) { a1[j] = CUDART_INF_F; a2[j] = CUDART_INF_F; ai[j] = 0; }
             int nc = 0; // mode 1: candidates met in this warp's columns
-            int32_t *cd = p.rcand + (size_t)(valid ? row : 0) * PREC_CANDS + h * (PREC_CANDS / 2);
+            int32_t *cd = p.rcand + (size_t)(valid ? row : 0) * PREC_CANDS + h * (PREC_CANDS / 2); // valid rows only
             bool ok = true;
             for (int j = 0; j < nchunk; ++j) {
                 // lane 0 waits, the warp follows its outcome (the TMEM loads
@@ -362,6 +375,8 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                     tmem_ld32(taddr + (uint32_t)cc, r);
                     tmem_ld32(taddr + (uint32_t)cc + 32, r + 32);
                     tmem_wait_ld();
+                    tmem_regs_ready(r);
+                    tmem_regs_ready(r + 32);
                     const int cb = j * TN + h * HALF + cc;
                     const float4 *cn4 = reinterpret_cast<const float4 *>(cn_s + cb);
                     if (p.mode == 0) {
@@ -392,6 +407,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                                 }
                             }
                         }
+                        if (!valid) mlo = mhi = 0;
                         while (mlo | mhi) { // a few per point: record them in column order
                             int u;
                             if (mlo) { u = __ffs(mlo) - 1; mlo &= mlo - 1; }
@@ -483,7 +499,8 @@ __global__ void __launch_bounds__(256) k_recheck(const float *X, const float *C3
     for (int64_t e = gtid; e < cnt; e += nthreads) {
         const int32_t *cd = rcand + (size_t)e * PREC_CANDS;
         const int n0 = cd[0], n1 = cd[HC];
-        if (n0 < 0 || n1 < 0) continue; // overflow: scored by the warp pass below
+        // overflow (or, defensively, an empty list): scored by the warp pass below
+        if (n0 < 0 || n1 < 0 || n0 + n1 == 0) continue;
         const int nc = n0 + n1;
         const int32_t i = rlist[e];
         const float *xr = X + (int64_t)i * DV;
@@ -523,7 +540,8 @@ __global__ void __launch_bounds__(256) k_recheck(const float *X, const float *C3
     const int lane = threadIdx.x & 31;
     const int64_t wid = gtid >> 5, nw = nthreads >> 5;
     for (int64_t e = wid; e < cnt; e += nw) {
-        if (rcand[(size_t)e * PREC_CANDS] >= 0 && rcand[(size_t)e * PREC_CANDS + HC] >= 0) continue;
+        const int n0 = rcand[(size_t)e * PREC_CANDS], n1 = rcand[(size_t)e * PREC_CANDS + HC];
+        if (n0 >= 0 && n1 >= 0 && n0 + n1 > 0) continue;
         const float *xr = X + (int64_t)rlist[e] * DV; // the same row for every lane
         float bd = CUDART_INF_F;
         int best = 0x7fffffff;
@@ -550,6 +568,22 @@ __global__ void __launch_bounds__(256) k_recheck(const float *X, const float *C3
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL_MASK, evals, o);
     if (lane == 0 && evals) atomicAdd(&ctr->evals, evals);
     if (gtid == 0) atomicAdd(&ctr->rechecked, (unsigned long long)cnt);
+}
+
+// Debug invariant of the precision form: every new assignment equals the
+// FP32 argmin over all centroids (library distance, lowest index on ties);
+// each point that differs adds 1 to *viol.  O(n k d): debug runs only.
+__global__ void k_prec_verify(const float *X, int64_t n, int32_t d, const float *C32, int32_t k,
+                              const int32_t *a_next, unsigned long long *viol) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float bd = CUDART_INF_F;
+        int best = 0;
+        for (int c = 0; c < k; ++c) {
+            const float r = d2_gen(X + i * d, C32 + (size_t)c * d, d);
+            if (r < bd) { bd = r; best = c; }
+        }
+        if (best != a_next[i]) atomicAdd(viol, 1ULL);
+    }
 }
 
 // Gathers the 16-bit operand rows (and ||x||^2) of the listed points into a compact
@@ -594,6 +628,12 @@ __global__ void k_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, 
             anew = a_next[i];
             PtState s = st[i];
             aold = s.a;
+            if (anew < 0 || anew >= k) {
+                // no assignment was produced for this point (a library bug):
+                // count it, keep the old one, touch no sums
+                atomicAdd(&ctr->violations, 1ULL);
+                anew = aold;
+            }
             ch = aold != anew;
             if (ch) { s.a = anew; st[i] = s; }
         }
@@ -815,6 +855,12 @@ cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *
     case 128: k_prec_gather<128><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t prec_verify(const float *X, int64_t n, int32_t d, const float *C32, int32_t k, const int32_t *a_next,
+                        unsigned long long *viol, cudaStream_t s) {
+    k_prec_verify<<<1024, 128, 0, s>>>(X, n, d, C32, k, a_next, viol);
     return cudaGetLastError();
 }
 

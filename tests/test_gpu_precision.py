@@ -33,7 +33,8 @@ FORMS = ["bf16", "fp16"]
 def _run_checked(X, k, iters, seed=42, init=None, form="bf16"):
     Xd = torch.as_tensor(X).cuda()
     rechecked = 0
-    with knor.Context(Xd, k, seed=seed, precision=form, init="explicit" if init is not None else "forgy") as c:
+    with knor.Context(Xd, k, seed=seed, precision=form, init="explicit" if init is not None else "forgy",
+                      debug_invariants=True) as c:
         if init is not None:
             c.set_init_centroids(init)
         for t in range(iters):
@@ -50,6 +51,7 @@ def _run_checked(X, k, iters, seed=42, init=None, form="bf16"):
             # the tensor-core scan scores every pair; a recheck scores its
             # recorded candidates (at most 14), or all k on overflow
             assert X.shape[0] * k <= s["dist_evals"] <= X.shape[0] * k + s["rechecked"] * k
+            assert s["violations"] == 0
             rechecked += s["rechecked"]
             if s["changed"] == 0:
                 break
@@ -124,11 +126,41 @@ def test_planted_ties_are_rechecked(form):
     X = np.concatenate([mids, C + 0.01 * rng.standard_normal((k, d)).astype(np.float32),
                         rng.uniform(-5, 5, (3000, d)).astype(np.float32)])
     Xd = torch.as_tensor(X).cuda()
-    with knor.Context(Xd, k, init="explicit", precision=form) as c:
+    with knor.Context(Xd, k, init="explicit", precision=form, debug_invariants=True) as c:
         c.set_init_centroids(C.astype(np.float64))
         s = c.iterate()
         assert s["rechecked"] >= 8
-        assert np.array_equal(c.assignments(), oracle.assign_f32(X, C))
+        assert s["violations"] == 0, s
+        a, ref = c.assignments(), oracle.assign_f32(X, C)
+        bad = np.flatnonzero(a != ref)
+        assert bad.size == 0, (f"{bad.size} differ: points {bad[:8]}, library {a[bad[:8]]}, "
+                               f"FP32 argmin {ref[bad[:8]]}, stats {s}")
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_stale_operand_rows_never_enter_candidate_lists(form):
+    """Rows past the end of the gathered list are stale device memory.  Fill
+    freed memory with 16-bit infinities first (so the context's buffers very
+    likely start out holding them): those rows must record no candidates,
+    in particular not into the first listed point's list."""
+    inf16 = 0x7C00 if form == "fp16" else 0x7F80
+    junk = torch.full((256 << 20,), inf16, dtype=torch.int16, device="cuda")
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(11)
+    d, k = 64, 48
+    C = rng.uniform(-5, 5, (k, d)).astype(np.float32)
+    X = rng.uniform(-5, 5, (20000, d)).astype(np.float32)
+    with knor.Context(torch.as_tensor(X).cuda(), k, init="explicit", precision=form, debug_invariants=True) as c:
+        c.set_init_centroids(C.astype(np.float64))
+        for _ in range(3):
+            C32 = c.centroids_f32()
+            s = c.iterate()
+            assert s["violations"] == 0, s
+            a = c.assignments()
+            ref = oracle.assign_f32(X, C32)
+            assert np.array_equal(a, ref), f"{int((a != ref).sum())} differ"
 
 
 @pytest.mark.parametrize("form", FORMS)
