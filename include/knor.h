@@ -226,6 +226,75 @@ void knor_destroy(knor_ctx *ctx);
 /* Library version, "major.minor.patch". */
 const char *knor_version(void);
 
+/* ------------------------------------------------------------------------
+ * Batched form: m independent problems advanced together.
+ *
+ * Each step runs one Lloyd iteration (with MTI pruning unless opts->no_prune)
+ * of every instance that has not converged, as one persistent scan launch
+ * over work units (instance, point range) taken longest-first from a device
+ * queue -- the GPU counterpart of the paper's task queue with work stealing
+ * ("Parallel Lloyd's Algorithm"; NUMA-aware task scheduling) -- followed by
+ * batched merge and table launches.  An instance gets the same assignments
+ * it would get alone from the same centroids; its sums are updated by FP64
+ * atomics, so centroids agree with the single-instance path to FP64
+ * rounding (not bit for bit).  An instance whose iteration changed no point
+ * is converged and skipped from then on.
+ * ---------------------------------------------------------------------- */
+typedef struct knor_batch knor_batch;
+
+typedef struct {
+    int64_t n;             /* points */
+    int32_t d, k;
+    int32_t iterations;    /* iterations run since the last reset */
+    int32_t converged;     /* 1 once an iteration changed no assignment */
+    int64_t changed_last;  /* points that changed cluster in its last iteration */
+} knor_batch_instance;
+
+/* points[i]: row-major n[i] x d[i] FP32 (host or device, copied; the caller
+ * keeps ownership).  Limits per instance: 1 <= k[i] <= min(n[i], 256), d[i]
+ * in {8, 16, 32, 64}; coordinates finite with |x| <= 1e15.  C^0 of instance
+ * i is Forgy with seed + i (as knor_create with that seed).  opts: NULL or
+ * FP32 distances with full_recompute_every = 0 (no_prune selects plain
+ * Lloyd).  Creation tunes the work-unit size per (d, k) bucket and the CTAs
+ * per SM by timing dry scans (set KNOR_AUTOTUNE=0 to skip; results are cached
+ * per device and bucket for the process and, if KNOR_AUTOTUNE_CACHE names a
+ * file, across processes).  Errors: KNOR_ERR_ARG (message from
+ * knor_last_error(NULL)), KNOR_ERR_OOM, KNOR_ERR_CUDA. */
+knor_status knor_batch_create(int32_t m, const float *const *points, const int64_t *n, const int32_t *d,
+                              const int32_t *k, uint64_t seed, const knor_opts *opts, knor_batch **out);
+/* C^0 of one instance, k x d FP64 (host or device); resets the whole batch
+ * to iteration 0. */
+knor_status knor_batch_set_init_centroids(knor_batch *b, int32_t instance, const double *c_kxd);
+/* Back to C^0 for every instance. */
+knor_status knor_batch_reset(knor_batch *b);
+/* One iteration of every active instance; *out (may be NULL) sums the
+ * counters over the instances that ran. */
+knor_status knor_batch_iterate(knor_batch *b, knor_iter_stats *out);
+/* Up to max_iters iterations as one graph launch, stopping on the device once
+ * every instance has converged; per_iter (NULL or max_iters records) as for
+ * knor_iterate. */
+knor_status knor_batch_run(knor_batch *b, int32_t max_iters, int32_t *iters_done, knor_iter_stats *per_iter);
+/* Per-instance results into caller buffers (host or device): n int32
+ * assignments, k x d FP64 centroids, k x d FP32 scan copy, k int64 Forgy
+ * indices, and the instance record. */
+knor_status knor_batch_get_assignments(const knor_batch *b, int32_t instance, int32_t *out_n);
+knor_status knor_batch_get_centroids(const knor_batch *b, int32_t instance, double *out_kxd);
+knor_status knor_batch_get_centroids_f32(const knor_batch *b, int32_t instance, float *out_kxd);
+knor_status knor_batch_get_init_indices(const knor_batch *b, int32_t instance, int64_t *out_k);
+knor_status knor_batch_get_instance(const knor_batch *b, int32_t instance, knor_batch_instance *out);
+/* Profiling as for a context; the batch fills the KNOR_KERNEL_MTI (scan),
+ * KNOR_KERNEL_REDUCE (merge) and KNOR_KERNEL_TABLE (bookkeeping + table)
+ * slots. */
+knor_status knor_batch_set_profiling(knor_batch *b, int32_t on);
+knor_status knor_batch_get_profile(knor_batch *b, knor_profile *out, int32_t reset_after);
+const char *knor_batch_kernel_name(const knor_batch *b, int32_t kernel);
+/* The tuned launch shape, as text (valid for the batch's lifetime). */
+const char *knor_batch_describe(const knor_batch *b);
+/* The batch's CUDA stream (cudaStream_t). */
+void *knor_batch_stream(const knor_batch *b);
+const char *knor_batch_last_error(const knor_batch *b);
+void knor_batch_destroy(knor_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

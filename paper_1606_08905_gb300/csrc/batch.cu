@@ -1,0 +1,1176 @@
+// batch.cu -- the batched form: m independent k-means problems advanced
+// together, one iteration of every active problem per step.
+//
+// All instances live in one set of concatenated device arrays (points,
+// per-point state, centroids, sums, tables), addressed through a per-instance
+// descriptor.  The points are cut into work units (instance, point range);
+// the units are ordered longest-processing-time first (cost = points x k x d)
+// and one persistent kernel drains them through an atomic counter -- the GPU
+// counterpart of the paper's task queue with work stealing ("Parallel Lloyd's
+// Algorithm", NUMA-aware task scheduling): a CTA that finishes early simply
+// takes the next unit, and the costly units are handed out first so the tail
+// is short.  Within a unit every point runs the same MTI test and pruned scan
+// as the single-problem scan (Clauses 1-3 with the rounding slack), so an
+// instance gets exactly the assignments it would get alone from the same
+// centroids; cluster sums move by the deltas of the points that changed
+// cluster (FP64).  K5 (merge + finalize) and K1 (drift, half distances, s)
+// are batched launches over all centroids of all active instances; a small
+// bookkeeping kernel masks the instances that converged.  An iteration is one
+// CUDA graph; a run is a graph with a device-side WHILE loop.
+//
+// The unit size per (d, k) bucket and the number of persistent CTAs per SM
+// are chosen by a grid search over dry scans (no state written) at creation,
+// cached per device and bucket for the process (and in a file when
+// KNOR_AUTOTUNE_CACHE names one).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "knor_internal.cuh"
+#include "knor.h"
+
+namespace knor {
+
+constexpr int BT = 256;            // threads of the scan CTA
+constexpr int B_KMAX = 256;        // largest k of an instance
+constexpr int B_PART_CAP = 4096;   // k x d up to which a unit sums in shared memory
+
+struct BInst {
+    int64_t n;      // points
+    int64_t xoff;   // first coordinate in X
+    int64_t poff;   // first point in the per-point arrays
+    int64_t coff;   // first element of the k x d centroid arrays
+    int64_t hoff;   // first entry of the k x k half-distance table
+    int32_t d, k;
+    int32_t koff;   // first entry of the per-centroid arrays
+    int32_t pad;
+    float g_up, onepk, tau, tiny; // FP32 distance bound and MTI slack for this d
+};
+
+struct BUnit {
+    int32_t inst, pad;
+    int64_t lo, hi; // points [lo, hi) of the instance
+};
+
+struct BCounters {
+    unsigned long long changed, skipped, evals, empty;
+};
+
+struct BParams {
+    const BInst *inst;
+    int32_t m;
+    int32_t nunits;
+    const BUnit *units;
+    unsigned *qctr;
+    const float *X;
+    PtState *st;
+    float *C32, *C32n;
+    double *C64, *S, *D;
+    long long *cnt, *Dcnt;
+    float *halfD, *s, *F;
+    int32_t *active;          // per instance: still iterating
+    int32_t *iters;           // per instance: iterations since reset
+    long long *changed_last;  // per instance: changed count of its last iteration
+    BCounters *bctr;          // per instance, this iteration
+    const int32_t *cinst;     // per global centroid: its instance
+    IterStats *stats;
+    int32_t *run_iter, *total_iter;
+    const int32_t *max_iters_dev;
+    unsigned long long cond_handle;
+    int32_t mti, dry;
+    int32_t kd_max, k_max;    // shared-memory layout of the scan
+};
+
+// ------------------------------------------------------------------- scan
+
+template <int DV>
+__device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int64_t lo, int64_t hi,
+                                          const float *cent, const float *s_s, const float *F_s, double *part,
+                                          long long *pcnt, long long &changed, long long &skipped,
+                                          long long &evals) {
+    const int k = I.k;
+    const float *X = p.X + I.xoff;
+    PtState *st = p.st + I.poff;
+    const float *halfD = p.halfD + I.hoff;
+    double *D = p.D + I.coff;
+    long long *Dc = p.Dcnt + I.koff;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += BT) {
+        const PtState ps = st[i];
+        const int a = ps.a;
+        if (p.mti && a >= 0) {
+            // Clause 1 with u^t = ub + F^t(a)
+            const float uu = __fadd_ru(ps.ub, F_s[a]);
+            if (__fmaf_ru(uu, I.onepk, I.tau) < s_s[a]) {
+                ++skipped;
+                continue;
+            }
+        }
+        unsigned long long x[DV / 2];
+        ldg_x2<DV>(x, X + i * DV);
+        int best;
+        float bd;
+        if (a < 0 || !p.mti) {
+            bd = CUDART_INF_F;
+            best = 0;
+            for (int c = 0; c < k; ++c) {
+                const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
+                if (r < bd) { bd = r; best = c; }
+            }
+            evals += k;
+        } else {
+            // Clause 3 tightens u to d(v, c_a); Clause 2 skips every c with
+            // u < 1/2 d(c_a, c)
+            bd = d2_reg<DV>(x, cent + (size_t)a * DV);
+            best = a;
+            ++evals;
+            const float test = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
+            const float *hrow = halfD + (size_t)a * k;
+            for (int c = 0; c < k; ++c) {
+                if (c == a) continue;
+                if (test < __ldg(hrow + c)) continue;
+                const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
+                ++evals;
+                if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+            }
+        }
+        if (p.dry) continue;
+        PtState ns;
+        ns.a = best;
+        ns.ub = __fsub_ru(bound_up(bd, I.g_up, I.tiny), F_s[best]);
+        st[i] = ns;
+        if (best == a) continue;
+        ++changed;
+        double *dst_new = part ? part + (size_t)best * DV : D + (size_t)best * DV;
+        double *dst_old = a >= 0 ? (part ? part + (size_t)a * DV : D + (size_t)a * DV) : nullptr;
+#pragma unroll
+        for (int j = 0; j < DV / 2; ++j) {
+            float x0, x1;
+            unpack2(x[j], x0, x1);
+            atomicAdd(dst_new + 2 * j, (double)x0);
+            atomicAdd(dst_new + 2 * j + 1, (double)x1);
+            if (dst_old) {
+                atomicAdd(dst_old + 2 * j, -(double)x0);
+                atomicAdd(dst_old + 2 * j + 1, -(double)x1);
+            }
+        }
+        atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + best : Dc + best), 1ULL);
+        if (a >= 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + a : Dc + a), (unsigned long long)-1LL);
+    }
+}
+
+__device__ __forceinline__ long long block_sum(long long v, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int w = 0; w < BT / 32; ++w) t += red[w];
+    return t;
+}
+
+// Persistent: every CTA takes units from the LPT-ordered list until it is
+// drained.  Per unit: stage the instance's centroids, s and F in shared
+// memory, scan the unit's points (thread per point), merge the unit's delta
+// sums into the instance's (FP64 atomics), add the unit's counters.
+__global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_unit;
+    __shared__ long long red[BT / 32];
+    float *cent = reinterpret_cast<float *>(sm);
+    float *s_s = cent + p.kd_max;
+    float *F_s = s_s + p.k_max;
+    double *part = reinterpret_cast<double *>(F_s + p.k_max + ((p.kd_max + 2 * p.k_max) & 1));
+    long long *pcnt = reinterpret_cast<long long *>(part + min(p.kd_max, B_PART_CAP));
+    const int tid = threadIdx.x;
+    while (true) {
+        if (tid == 0) s_unit = (int)atomicAdd(p.qctr, 1u);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= p.nunits) break;
+        const BUnit U = p.units[u];
+        if (!p.active[U.inst]) continue;
+        const BInst I = p.inst[U.inst];
+        const int kd = I.k * I.d;
+        const bool use_part = !p.dry && kd <= B_PART_CAP;
+        for (int e = tid; e < kd; e += BT) cent[e] = p.C32[I.coff + e];
+        for (int c = tid; c < I.k; c += BT) {
+            s_s[c] = p.s[I.koff + c];
+            F_s[c] = p.F[I.koff + c];
+        }
+        if (use_part) {
+            for (int e = tid; e < kd; e += BT) part[e] = 0.0;
+            for (int c = tid; c < I.k; c += BT) pcnt[c] = 0;
+        }
+        __syncthreads();
+        long long ch = 0, sk = 0, ev = 0;
+        double *pp = use_part ? part : nullptr;
+        long long *pc = use_part ? pcnt : nullptr;
+        switch (I.d) {
+        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
+        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
+        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
+        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
+        }
+        __syncthreads();
+        if (use_part) {
+            double *D = p.D + I.coff;
+            long long *Dc = p.Dcnt + I.koff;
+            for (int e = tid; e < kd; e += BT)
+                if (part[e] != 0.0) atomicAdd(D + e, part[e]);
+            for (int c = tid; c < I.k; c += BT)
+                if (pcnt[c] != 0) atomicAdd(reinterpret_cast<unsigned long long *>(Dc + c), (unsigned long long)pcnt[c]);
+        }
+        ch = block_sum(ch, red);
+        sk = block_sum(sk, red);
+        ev = block_sum(ev, red);
+        if (tid == 0 && !p.dry) {
+            BCounters *b = p.bctr + U.inst;
+            if (ch) atomicAdd(&b->changed, (unsigned long long)ch);
+            if (sk) atomicAdd(&b->skipped, (unsigned long long)sk);
+            if (ev) atomicAdd(&b->evals, (unsigned long long)ev);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------ merge, bookkeeping, table
+
+// K5 per centroid of every active instance: S += the iteration's deltas,
+// c = S / count in FP64 (an empty cluster keeps its centroid, its sum reset
+// to exactly 0), the FP32 scan copy of the result.
+__global__ void k_breduce(const BParams p) {
+    const int g = blockIdx.x;
+    const int i = p.cinst[g];
+    if (!p.active[i]) return;
+    const BInst I = p.inst[i];
+    const int c = g - I.koff;
+    const int j = threadIdx.x;
+    const long long cn = p.cnt[g] + p.Dcnt[g];
+    if (j < I.d) {
+        const int64_t e = I.coff + (int64_t)c * I.d + j;
+        double Sn = p.S[e] + p.D[e];
+        double cv = p.C64[e];
+        if (cn > 0) cv = Sn / (double)cn;
+        else Sn = 0.0;
+        p.S[e] = Sn;
+        p.C64[e] = cv;
+        p.C32n[e] = __double2float_rn(cv);
+        p.D[e] = 0.0;
+    }
+    __syncthreads();
+    if (j == 0) {
+        p.cnt[g] = cn;
+        p.Dcnt[g] = 0;
+        if (cn == 0) atomicAdd(&p.bctr[i].empty, 1ULL);
+    }
+}
+
+// After the merge: per instance, count the iteration, mask it once no point
+// changed; the run's record (sums over the instances active in it) and the
+// device-side loop condition.  One CTA.
+__global__ void k_bstep(const BParams p, int32_t snapshot) {
+    __shared__ unsigned long long red[4][32];
+    __shared__ int any_s;
+    unsigned long long ch = 0, sk = 0, ev = 0, em = 0;
+    int any = 0;
+    if (threadIdx.x == 0) any_s = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.m; i += blockDim.x) {
+        const BCounters b = p.bctr[i];
+        if (p.active[i]) {
+            p.iters[i] += 1;
+            p.changed_last[i] = (long long)b.changed;
+            ch += b.changed;
+            sk += b.skipped;
+            ev += b.evals;
+            em += b.empty;
+            if (b.changed == 0) p.active[i] = 0;
+        }
+        any |= p.active[i];
+        p.bctr[i] = BCounters{0, 0, 0, 0};
+    }
+    if (any) atomicOr(&any_s, 1);
+    for (int o = 16; o > 0; o >>= 1) {
+        ch += __shfl_xor_sync(FULL_MASK, ch, o);
+        sk += __shfl_xor_sync(FULL_MASK, sk, o);
+        ev += __shfl_xor_sync(FULL_MASK, ev, o);
+        em += __shfl_xor_sync(FULL_MASK, em, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][w] = ch; red[1][w] = sk; red[2][w] = ev; red[3][w] = em; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ch = sk = ev = em = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+        ch += red[0][ww]; sk += red[1][ww]; ev += red[2][ww]; em += red[3][ww];
+    }
+    if (!snapshot) return;
+    const int it = *p.run_iter;
+    const int total = *p.total_iter + 1;
+    IterStats r;
+    r.changed = (long long)ch;
+    r.clause1_skipped = (long long)sk;
+    r.dist_evals = (long long)ev;
+    r.rechecked = 0;
+    r.empty = (int32_t)em;
+    r.iteration = total;
+    r.violations = 0;
+    p.stats[it] = r;
+    *p.run_iter = it + 1;
+    *p.total_iter = total;
+    if (p.cond_handle) {
+        const unsigned go = (any_s && it + 1 < *p.max_iters_dev) ? 1u : 0u;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)p.cond_handle, go);
+    }
+}
+
+// K1 per centroid a of every active instance, from the FP32 scan copies in
+// FP64 with directed rounding (the single-problem table's arithmetic): drift
+// f(a) rounded up and added to F(a); 1/2 d(c_a, c) rounded down; s(a) their
+// minimum over c != a; then the new scan copy replaces the old one.
+__global__ void k_btable(const BParams p, int32_t need_table) {
+    const int g = blockIdx.x;
+    const int i = p.cinst[g];
+    if (!p.active[i]) return;
+    const BInst I = p.inst[i];
+    const int a = g - I.koff, k = I.k, d = I.d, tid = threadIdx.x;
+    const float *Cn = p.C32n + I.coff;
+    float *Co = p.C32 + I.coff;
+    __shared__ double red[128];
+    __shared__ float redf[128];
+    if (need_table) {
+        double acc = 0.0;
+        for (int j = tid; j < d; j += blockDim.x) {
+            const double x = Cn[(size_t)a * d + j], y = Co[(size_t)a * d + j];
+            const double lo = __dsub_rd(x, y), hi = __dsub_ru(x, y);
+            const double mm = fmax(fabs(lo), fabs(hi));
+            acc = __dadd_ru(acc, __dmul_ru(mm, mm));
+        }
+        red[tid] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)blockDim.x; ++q) t = __dadd_ru(t, red[q]);
+            const float fa = __double2float_ru(__dsqrt_ru(t));
+            p.F[g] = __fadd_ru(p.F[g], fa);
+        }
+        float mymin = CUDART_INF_F;
+        float *hrow = p.halfD + I.hoff + (size_t)a * k;
+        for (int c = tid; c < k; c += blockDim.x) {
+            if (c == a) { hrow[c] = 0.0f; continue; }
+            double sdd = 0.0;
+            for (int j = 0; j < d; ++j) {
+                const double x = Cn[(size_t)a * d + j], y = Cn[(size_t)c * d + j];
+                const double lo = __dsub_rd(x, y), hi = __dsub_ru(x, y);
+                const double mm = lo > 0.0 ? lo : (hi < 0.0 ? -hi : 0.0);
+                sdd = __dadd_rd(sdd, __dmul_rd(mm, mm));
+            }
+            const float h = __double2float_rd(__dmul_rd(0.5, __dsqrt_rd(sdd)));
+            hrow[c] = h;
+            mymin = fminf(mymin, h);
+        }
+        redf[tid] = mymin;
+        __syncthreads();
+        if (tid == 0) {
+            float mn = CUDART_INF_F;
+            for (int q = 0; q < (int)blockDim.x; ++q) mn = fminf(mn, redf[q]);
+            p.s[g] = mn;
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < d; j += blockDim.x) Co[(size_t)a * d + j] = Cn[(size_t)a * d + j];
+}
+
+__global__ void k_binit_state(PtState *st, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        st[i] = PtState{CUDART_INF_F, -1};
+}
+
+__global__ void k_bround(const double *C64, float *C32, float *C32n, int64_t total) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const float v = __double2float_rn(C64[e]);
+        C32[e] = v;
+        C32n[e] = v;
+    }
+}
+
+__global__ void k_bgather(const float *X, int32_t d, const int64_t *idx, int32_t k, double *C0) {
+    const int64_t total = (int64_t)k * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        C0[e] = (double)X[idx[e / d] * d + e % d];
+}
+
+__global__ void k_bextract(const PtState *st, int64_t n, int32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = st[i].a;
+}
+
+static int gridfor(int64_t count, int threads) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, 4096));
+}
+
+} // namespace knor
+
+using namespace knor;
+
+// ------------------------------------------------------------------ host
+
+enum BFlag { BF_RUN_ITER = 0, BF_TOTAL_ITER, BF_MAX_ITERS, BF_COUNT };
+
+struct knor_batch {
+    int dev = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int32_t m = 0;
+    knor_opts opts{};
+    uint64_t seed = 0;
+    std::vector<BInst> h_inst;
+    std::vector<std::vector<int64_t>> init_idx;
+    std::vector<int32_t> unit_pts;  // tuned unit size per instance
+    int64_t total_n = 0, total_x = 0, total_c = 0, total_h = 0;
+    int32_t total_k = 0, kd_max = 0, k_max = 0;
+    float *X = nullptr, *C32 = nullptr, *C32n = nullptr, *halfD = nullptr, *s = nullptr, *F = nullptr;
+    PtState *st = nullptr;
+    double *C0 = nullptr, *C64 = nullptr, *S = nullptr, *D = nullptr;
+    long long *cnt = nullptr, *Dcnt = nullptr, *changed_last = nullptr;
+    BInst *inst = nullptr;
+    BUnit *units = nullptr;
+    int32_t nunits = 0;
+    unsigned *qctr = nullptr;
+    int32_t *active = nullptr, *iters = nullptr, *cinst = nullptr, *flags = nullptr;
+    BCounters *bctr = nullptr;
+    IterStats *stats = nullptr;
+    int64_t *d_idx = nullptr;
+    size_t smem = 0;
+    int grid = 0, bps = 1;
+    cudaGraphExec_t iter_exec = nullptr, run_exec = nullptr;
+    bool profiling = false;
+    cudaEvent_t ev[6] = {};
+    int64_t prof_n[KNOR_KERNEL_COUNT] = {};
+    double prof_ms[KNOR_KERNEL_COUNT] = {};
+    std::string tuning;
+};
+
+namespace {
+
+constexpr int kBStatsCap = 65536;
+
+knor_status bfail(knor_batch *b, knor_status st, const std::string &msg) {
+    b->err = msg;
+    return st;
+}
+
+#define BCUDA(b, call)                                                                                \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            cudaGetLastError();                                                                       \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? KNOR_ERR_OOM : KNOR_ERR_CUDA,           \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+        }                                                                                             \
+    } while (0)
+
+template <class T>
+knor_status balloc(knor_batch *b, T **p, size_t count) {
+    BCUDA(b, cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T)));
+    return KNOR_OK;
+}
+
+void bfree_all(knor_batch *b) {
+    void *bufs[] = {b->X,    b->C32,   b->C32n, b->halfD, b->s,      b->F,     b->st,     b->C0,
+                    b->C64,  b->S,     b->D,    b->cnt,   b->Dcnt,   b->changed_last, b->inst, b->units,
+                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->iter_exec) cudaGraphExecDestroy(b->iter_exec);
+    if (b->run_exec) cudaGraphExecDestroy(b->run_exec);
+    if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+BParams params_of(const knor_batch *b, int dry, unsigned long long cond, const BUnit *units, int32_t nunits) {
+    BParams p{};
+    p.inst = b->inst;
+    p.m = b->m;
+    p.nunits = nunits;
+    p.units = units;
+    p.qctr = b->qctr;
+    p.X = b->X;
+    p.st = b->st;
+    p.C32 = b->C32;
+    p.C32n = b->C32n;
+    p.C64 = b->C64;
+    p.S = b->S;
+    p.D = b->D;
+    p.cnt = b->cnt;
+    p.Dcnt = b->Dcnt;
+    p.halfD = b->halfD;
+    p.s = b->s;
+    p.F = b->F;
+    p.active = b->active;
+    p.iters = b->iters;
+    p.changed_last = b->changed_last;
+    p.bctr = b->bctr;
+    p.cinst = b->cinst;
+    p.stats = b->stats;
+    p.run_iter = b->flags + BF_RUN_ITER;
+    p.total_iter = b->flags + BF_TOTAL_ITER;
+    p.max_iters_dev = b->flags + BF_MAX_ITERS;
+    p.cond_handle = cond;
+    p.mti = b->opts.no_prune ? 0 : 1;
+    p.dry = dry;
+    p.kd_max = b->kd_max;
+    p.k_max = b->k_max;
+    return p;
+}
+
+// Work units: each instance cut into pieces of its bucket's unit size, all
+// pieces ordered by cost (points x k x d) descending, ties by instance and
+// position (a fixed order).
+std::vector<BUnit> make_units(const knor_batch *b, const std::vector<int32_t> &unit_pts,
+                              const std::vector<int> *only = nullptr) {
+    std::vector<BUnit> u;
+    std::vector<double> cost;
+    for (int32_t i = 0; i < b->m; ++i) {
+        if (only && std::find(only->begin(), only->end(), i) == only->end()) continue;
+        const BInst &I = b->h_inst[i];
+        const int64_t step = std::max<int64_t>(1, unit_pts[i]);
+        for (int64_t lo = 0; lo < I.n; lo += step) {
+            BUnit x{};
+            x.inst = i;
+            x.lo = lo;
+            x.hi = std::min<int64_t>(I.n, lo + step);
+            u.push_back(x);
+        }
+    }
+    std::vector<size_t> ord(u.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    auto cost_of = [&](const BUnit &x) {
+        const BInst &I = b->h_inst[x.inst];
+        return (double)(x.hi - x.lo) * I.k * I.d;
+    };
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t p, size_t q) { return cost_of(u[p]) > cost_of(u[q]); });
+    std::vector<BUnit> out;
+    out.reserve(u.size());
+    for (size_t q : ord) out.push_back(u[q]);
+    return out;
+}
+
+knor_status enqueue_iter(knor_batch *b, cudaStream_t s, unsigned long long cond, cudaEvent_t *ev) {
+    const BParams p = params_of(b, 0, cond, b->units, b->nunits);
+    auto mark = [&](int i) -> cudaError_t { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    BCUDA(b, cudaMemsetAsync(b->qctr, 0, sizeof(unsigned), s));
+    BCUDA(b, mark(0));
+    k_bscan<<<b->grid, BT, b->smem, s>>>(p);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, mark(1));
+    k_breduce<<<b->total_k, 64, 0, s>>>(p);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, mark(2));
+    k_bstep<<<1, 512, 0, s>>>(p, 1);
+    BCUDA(b, cudaGetLastError());
+    k_btable<<<b->total_k, 128, 0, s>>>(p, b->opts.no_prune ? 0 : 1);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, mark(3));
+    return KNOR_OK;
+}
+
+knor_status build_graphs(knor_batch *b) {
+    {
+        BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        knor_status st = enqueue_iter(b, b->stream, 0, nullptr);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st != KNOR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        BCUDA(b, e);
+        e = cudaGraphInstantiate(&b->iter_exec, g, 0);
+        cudaGraphDestroy(g);
+        BCUDA(b, e);
+    }
+    {
+        cudaGraph_t g = nullptr;
+        BCUDA(b, cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); BCUDA(b, e); }
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); BCUDA(b, e); }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); BCUDA(b, e); }
+        knor_status st = enqueue_iter(b, b->stream, (unsigned long long)h, nullptr);
+        cudaGraph_t got = nullptr;
+        e = cudaStreamEndCapture(b->stream, &got);
+        if (st != KNOR_OK) { cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) { cudaGraphDestroy(g); BCUDA(b, e); }
+        e = cudaGraphInstantiate(&b->run_exec, g, 0);
+        cudaGraphDestroy(g);
+        BCUDA(b, e);
+    }
+    return KNOR_OK;
+}
+
+// Back to C^0 (b->C0): centroids, sums, counts, drift, bounds, tables.
+knor_status breset(knor_batch *b) {
+    cudaStream_t s = b->stream;
+    const size_t tc = (size_t)b->total_c, tk = (size_t)b->total_k;
+    BCUDA(b, cudaMemcpyAsync(b->C64, b->C0, tc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_bround<<<gridfor((int64_t)tc, 256), 256, 0, s>>>(b->C0, b->C32, b->C32n, (int64_t)tc);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, cudaMemsetAsync(b->S, 0, tc * sizeof(double), s));
+    BCUDA(b, cudaMemsetAsync(b->D, 0, tc * sizeof(double), s));
+    BCUDA(b, cudaMemsetAsync(b->cnt, 0, tk * sizeof(long long), s));
+    BCUDA(b, cudaMemsetAsync(b->Dcnt, 0, tk * sizeof(long long), s));
+    BCUDA(b, cudaMemsetAsync(b->F, 0, tk * sizeof(float), s));
+    BCUDA(b, cudaMemsetAsync(b->bctr, 0, (size_t)b->m * sizeof(BCounters), s));
+    BCUDA(b, cudaMemsetAsync(b->iters, 0, (size_t)b->m * sizeof(int32_t), s));
+    BCUDA(b, cudaMemsetAsync(b->changed_last, 0, (size_t)b->m * sizeof(long long), s));
+    std::vector<int32_t> ones((size_t)b->m, 1);
+    BCUDA(b, cudaMemcpyAsync(b->active, ones.data(), ones.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_binit_state<<<gridfor(b->total_n, 256), 256, 0, s>>>(b->st, b->total_n);
+    BCUDA(b, cudaGetLastError());
+    int32_t fl[BF_COUNT] = {0, 0, 1};
+    BCUDA(b, cudaMemcpyAsync(b->flags, fl, sizeof(fl), cudaMemcpyHostToDevice, s));
+    // tables for C^0 (drift 0, no record)
+    const BParams p = params_of(b, 0, 0, b->units, b->nunits);
+    k_btable<<<b->total_k, 128, 0, s>>>(p, b->opts.no_prune ? 0 : 1);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, cudaStreamSynchronize(s));
+    return KNOR_OK;
+}
+
+// ---------------------------------------------------------------- autotune
+
+std::mutex g_tune_mu;
+std::map<std::string, int32_t> g_tune; // key -> unit size
+bool g_tune_loaded = false;
+
+std::string tune_key(const cudaDeviceProp &pr, int d, int kb, bool mti) {
+    char buf[320];
+    std::snprintf(buf, sizeof(buf), "%s|sm%d|%d.%d|d%d|kb%d|%s", pr.name, pr.multiProcessorCount, pr.major,
+                  pr.minor, d, kb, mti ? "mti" : "plain");
+    return buf;
+}
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("KNOR_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        char *sep = std::strrchr(line, '=');
+        if (!sep) continue;
+        *sep = 0;
+        g_tune[line] = std::atoi(sep + 1);
+    }
+    std::fclose(f);
+}
+
+void tune_store(const std::string &key, int32_t v) {
+    g_tune[key] = v;
+    const char *path = std::getenv("KNOR_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s=%d\n", key.c_str(), v);
+    std::fclose(f);
+}
+
+int k_bucket(int k) { return k <= 32 ? 0 : (k <= 96 ? 1 : 2); }
+
+// Times one dry scan (nothing written) over the given units.
+knor_status time_dry(knor_batch *b, const std::vector<BUnit> &u, int grid, float *ms) {
+    BUnit *du = nullptr;
+    BCUDA(b, cudaMalloc(&du, std::max<size_t>(u.size(), 1) * sizeof(BUnit)));
+    cudaError_t e = cudaMemcpyAsync(du, u.data(), u.size() * sizeof(BUnit), cudaMemcpyHostToDevice, b->stream);
+    const BParams p = params_of(b, 1, 0, du, (int32_t)u.size());
+    float best = 1e30f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaMemsetAsync(b->qctr, 0, sizeof(unsigned), b->stream);
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(b->ev[0], b->stream);
+        if (e != cudaSuccess) break;
+        k_bscan<<<grid, BT, b->smem, b->stream>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(b->ev[1], b->stream);
+        if (e != cudaSuccess) break;
+        e = cudaEventSynchronize(b->ev[1]);
+        if (e != cudaSuccess) break;
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, b->ev[0], b->ev[1]);
+        best = std::min(best, t);
+    }
+    cudaFree(du);
+    BCUDA(b, e);
+    *ms = best;
+    return KNOR_OK;
+}
+
+// Grid search: per (d, k) bucket the unit size in {1024, 4096, 16384,
+// 65536} points, timed on a sample of that bucket's instances (at most
+// 8M points) in their iteration-1 state; then the persistent CTAs per SM.
+knor_status autotune(knor_batch *b) {
+    cudaDeviceProp pr{};
+    BCUDA(b, cudaGetDeviceProperties(&pr, b->dev));
+    int maxbps = 1;
+    BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxbps, k_bscan, BT, b->smem));
+    maxbps = std::max(1, maxbps);
+    const bool enabled = !(std::getenv("KNOR_AUTOTUNE") && std::string(std::getenv("KNOR_AUTOTUNE")) == "0");
+    const int32_t cands[4] = {1024, 4096, 16384, 65536};
+    const bool mti = !b->opts.no_prune;
+    std::map<std::pair<int, int>, std::vector<int>> buckets;
+    for (int32_t i = 0; i < b->m; ++i)
+        buckets[{b->h_inst[i].d, k_bucket(b->h_inst[i].k)}].push_back(i);
+    b->unit_pts.assign((size_t)b->m, 8192);
+    std::string desc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+    }
+    b->grid = b->num_sms * maxbps;
+    for (auto &kv : buckets) {
+        const std::string key = tune_key(pr, kv.first.first, kv.first.second, mti);
+        int32_t chosen = 8192;
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) { chosen = it->second; cached = true; }
+        }
+        if (!cached && enabled) {
+            // sample: the bucket's instances, largest first, up to 8M points
+            std::vector<int> sample = kv.second;
+            std::sort(sample.begin(), sample.end(), [&](int p, int q) { return b->h_inst[p].n > b->h_inst[q].n; });
+            std::vector<int> take;
+            int64_t pts = 0;
+            for (int i : sample) {
+                if (pts >= (8 << 20)) break;
+                take.push_back(i);
+                pts += b->h_inst[i].n;
+            }
+            float best = 1e30f;
+            for (int32_t c : cands) {
+                std::vector<int32_t> up((size_t)b->m, c);
+                const std::vector<BUnit> u = make_units(b, up, &take);
+                float ms = 0.0f;
+                knor_status st = time_dry(b, u, b->grid, &ms);
+                if (st != KNOR_OK) return st;
+                if (ms < best) { best = ms; chosen = c; }
+            }
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_store(key, chosen);
+        }
+        for (int i : kv.second) b->unit_pts[(size_t)i] = chosen;
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "%sd%d/kb%d:%d", desc.empty() ? "" : " ", kv.first.first, kv.first.second,
+                      chosen);
+        desc += buf;
+    }
+    // persistent CTAs per SM, on the whole unit list
+    const std::vector<BUnit> all = make_units(b, b->unit_pts);
+    int best_bps = maxbps;
+    if (enabled && maxbps > 1) {
+        float best = 1e30f;
+        for (int q = 1; q <= maxbps; ++q) {
+            float ms = 0.0f;
+            knor_status st = time_dry(b, all, b->num_sms * q, &ms);
+            if (st != KNOR_OK) return st;
+            if (ms < best) { best = ms; best_bps = q; }
+        }
+    }
+    b->bps = best_bps;
+    b->grid = b->num_sms * best_bps;
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "; %d CTAs/SM x %d SMs; %zu units", best_bps, b->num_sms, all.size());
+    b->tuning = "unit points per (d, k bucket): " + desc + buf + (enabled ? "" : " (autotune off)");
+    return KNOR_OK;
+}
+
+knor_status read_bstats(knor_batch *b, int32_t count, knor_iter_stats *out) {
+    if (!out || count <= 0) return KNOR_OK;
+    std::vector<IterStats> h((size_t)count);
+    BCUDA(b, cudaMemcpy(h.data(), b->stats, sizeof(IterStats) * count, cudaMemcpyDeviceToHost));
+    for (int32_t t = 0; t < count; ++t) {
+        knor_iter_stats &o = out[t];
+        o.changed = h[t].changed;
+        o.clause1_skipped = h[t].clause1_skipped;
+        o.dist_evals = h[t].dist_evals;
+        o.rechecked = h[t].rechecked;
+        o.empty = h[t].empty;
+        o.iteration = h[t].iteration;
+        o.violations = h[t].violations;
+    }
+    return KNOR_OK;
+}
+
+knor_status profiled_iter(knor_batch *b) {
+    knor_status st = enqueue_iter(b, b->stream, 0, b->ev);
+    if (st != KNOR_OK) return st;
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    float t = 0.0f;
+    BCUDA(b, cudaEventElapsedTime(&t, b->ev[0], b->ev[1]));
+    b->prof_n[KNOR_KERNEL_MTI] += 1;
+    b->prof_ms[KNOR_KERNEL_MTI] += t;
+    BCUDA(b, cudaEventElapsedTime(&t, b->ev[1], b->ev[2]));
+    b->prof_n[KNOR_KERNEL_REDUCE] += 1;
+    b->prof_ms[KNOR_KERNEL_REDUCE] += t;
+    BCUDA(b, cudaEventElapsedTime(&t, b->ev[2], b->ev[3]));
+    b->prof_n[KNOR_KERNEL_TABLE] += 1;
+    b->prof_ms[KNOR_KERNEL_TABLE] += t;
+    return KNOR_OK;
+}
+
+knor_status check_instance(const knor_batch *b, int32_t i) {
+    if (i < 0 || i >= b->m) return KNOR_ERR_ARG;
+    return KNOR_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+knor_status knor_batch_create(int32_t m, const float *const *points, const int64_t *n, const int32_t *d,
+                              const int32_t *k, uint64_t seed, const knor_opts *opts, knor_batch **out) {
+    if (!out) return KNOR_ERR_ARG;
+    *out = nullptr;
+    set_global_error("");
+    if (m < 1 || !points || !n || !d || !k) {
+        set_global_error("knor_batch_create: need m >= 1 and non-NULL points, n, d, k");
+        return KNOR_ERR_ARG;
+    }
+    knor_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != KNOR_PREC_FP32 || o.full_recompute_every != 0) {
+        set_global_error("knor_batch_create: the batched form supports FP32 distances and delta sums only");
+        return KNOR_ERR_ARG;
+    }
+    for (int32_t i = 0; i < m; ++i) {
+        if (!points[i] || n[i] < 1 || k[i] < 1 || k[i] > n[i] || k[i] > B_KMAX ||
+            (d[i] != 8 && d[i] != 16 && d[i] != 32 && d[i] != 64)) {
+            set_global_error(("knor_batch_create: instance " + std::to_string(i) +
+                              ": need 1 <= k <= min(n, 256), d in {8, 16, 32, 64} and non-NULL points").c_str());
+            return KNOR_ERR_ARG;
+        }
+    }
+    knor_batch *b = new knor_batch();
+    b->m = m;
+    b->opts = o;
+    b->seed = seed;
+    auto bail = [&](knor_status st) {
+        set_global_error(b->err.c_str());
+        bfree_all(b);
+        delete b;
+        return st;
+    };
+#define BC(call) do { knor_status s_ = (call); if (s_ != KNOR_OK) return bail(s_); } while (0)
+#define BCU(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { b->err = std::string(#call) + ": " + cudaGetErrorString(e_); cudaGetLastError(); return bail(e_ == cudaErrorMemoryAllocation ? KNOR_ERR_OOM : KNOR_ERR_CUDA); } } while (0)
+    BCU(cudaGetDevice(&b->dev));
+    BCU(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->dev));
+    BCU(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    for (auto &e : b->ev) BCU(cudaEventCreate(&e));
+    // layout
+    b->h_inst.resize((size_t)m);
+    std::vector<int32_t> cinst;
+    const double u = std::ldexp(1.0, -24);
+    for (int32_t i = 0; i < m; ++i) {
+        BInst &I = b->h_inst[(size_t)i];
+        I.n = n[i];
+        I.d = d[i];
+        I.k = k[i];
+        I.xoff = b->total_x;
+        I.poff = b->total_n;
+        I.coff = b->total_c;
+        I.hoff = b->total_h;
+        I.koff = b->total_k;
+        const double g = (I.d + 2) * u / (1.0 - (I.d + 2) * u);
+        I.g_up = f32_up(1.0 / (1.0 - (I.d + 2) * u));
+        I.onepk = f32_up(1.0 + g);
+        I.tau = std::ldexp(1.0f, -40);
+        I.tiny = (float)std::ldexp((double)I.d, -149);
+        b->total_x += I.n * I.d;
+        b->total_n += I.n;
+        b->total_c += (int64_t)I.k * I.d;
+        b->total_h += (int64_t)I.k * I.k;
+        b->total_k += I.k;
+        b->kd_max = std::max(b->kd_max, I.k * I.d);
+        b->k_max = std::max(b->k_max, I.k);
+        for (int c = 0; c < I.k; ++c) cinst.push_back(i);
+    }
+    const size_t tc = (size_t)b->total_c, tk = (size_t)b->total_k;
+    BC(balloc(b, &b->X, (size_t)b->total_x));
+    BC(balloc(b, &b->st, (size_t)b->total_n));
+    BC(balloc(b, &b->C0, tc));
+    BC(balloc(b, &b->C64, tc));
+    BC(balloc(b, &b->S, tc));
+    BC(balloc(b, &b->D, tc));
+    BC(balloc(b, &b->C32, tc));
+    BC(balloc(b, &b->C32n, tc));
+    BC(balloc(b, &b->halfD, (size_t)b->total_h));
+    BC(balloc(b, &b->s, tk));
+    BC(balloc(b, &b->F, tk));
+    BC(balloc(b, &b->cnt, tk));
+    BC(balloc(b, &b->Dcnt, tk));
+    BC(balloc(b, &b->cinst, tk));
+    BC(balloc(b, &b->inst, (size_t)m));
+    BC(balloc(b, &b->active, (size_t)m));
+    BC(balloc(b, &b->iters, (size_t)m));
+    BC(balloc(b, &b->changed_last, (size_t)m));
+    BC(balloc(b, &b->bctr, (size_t)m));
+    BC(balloc(b, &b->qctr, 1));
+    BC(balloc(b, &b->flags, BF_COUNT));
+    BC(balloc(b, &b->stats, kBStatsCap));
+    BC(balloc(b, &b->d_idx, (size_t)b->k_max));
+    BCU(cudaMemcpyAsync(b->inst, b->h_inst.data(), sizeof(BInst) * (size_t)m, cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->cinst, cinst.data(), sizeof(int32_t) * tk, cudaMemcpyHostToDevice, b->stream));
+    // points (host or device), validated
+    unsigned long long *bad = nullptr;
+    BC(balloc(b, &bad, 1));
+    BCU(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), b->stream));
+    for (int32_t i = 0; i < m; ++i) {
+        const BInst &I = b->h_inst[(size_t)i];
+        const size_t bytes = sizeof(float) * (size_t)I.n * I.d;
+        BCU(cudaMemcpyAsync(b->X + I.xoff, points[i], bytes, cudaMemcpyDefault, b->stream));
+    }
+    BCU(launch_validate(b->X, b->total_x, bad, b->stream));
+    unsigned long long nbad = 0;
+    BCU(cudaMemcpyAsync(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    cudaFree(bad);
+    if (nbad) {
+        b->err = "knor_batch_create: " + std::to_string(nbad) + " coordinates are NaN, infinite or above 1e15";
+        return bail(KNOR_ERR_ARG);
+    }
+    // C^0: Forgy per instance, seed + instance
+    b->init_idx.resize((size_t)m);
+    for (int32_t i = 0; i < m; ++i) {
+        const BInst &I = b->h_inst[(size_t)i];
+        b->init_idx[(size_t)i] = forgy_indices(I.n, I.k, seed + (uint64_t)i);
+        BCU(cudaMemcpyAsync(b->d_idx, b->init_idx[(size_t)i].data(), sizeof(int64_t) * I.k, cudaMemcpyHostToDevice,
+                            b->stream));
+        k_bgather<<<gridfor((int64_t)I.k * I.d, 256), 256, 0, b->stream>>>(b->X + I.xoff, I.d, b->d_idx, I.k,
+                                                                             b->C0 + I.coff);
+        BCU(cudaGetLastError());
+        BCU(cudaStreamSynchronize(b->stream)); // d_idx is reused
+    }
+    // scan launch shape
+    b->smem = sizeof(float) * ((size_t)b->kd_max + 2 * b->k_max + 1) +
+              sizeof(double) * (size_t)std::min(b->kd_max, B_PART_CAP) + sizeof(long long) * b->k_max + 16;
+    BCU(cudaFuncSetAttribute(k_bscan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    BC(breset(b));
+    BC(autotune(b));
+    const std::vector<BUnit> units = make_units(b, b->unit_pts);
+    b->nunits = (int32_t)units.size();
+    BC(balloc(b, &b->units, units.size()));
+    BCU(cudaMemcpyAsync(b->units, units.data(), sizeof(BUnit) * units.size(), cudaMemcpyHostToDevice, b->stream));
+    BC(breset(b));
+    BC(build_graphs(b));
+    *out = b;
+    return KNOR_OK;
+#undef BC
+#undef BCU
+}
+
+void knor_batch_destroy(knor_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    bfree_all(b);
+    delete b;
+}
+
+const char *knor_batch_last_error(const knor_batch *b) { return b ? b->err.c_str() : ""; }
+void *knor_batch_stream(const knor_batch *b) { return b ? (void *)b->stream : nullptr; }
+const char *knor_batch_describe(const knor_batch *b) { return b ? b->tuning.c_str() : ""; }
+
+knor_status knor_batch_reset(knor_batch *b) {
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    return breset(b);
+}
+
+knor_status knor_batch_set_init_centroids(knor_batch *b, int32_t instance, const double *c_kxd) {
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    if (check_instance(b, instance) != KNOR_OK || !c_kxd)
+        return bfail(b, KNOR_ERR_ARG, "knor_batch_set_init_centroids: bad instance or NULL centroids");
+    const BInst &I = b->h_inst[(size_t)instance];
+    const size_t kd = (size_t)I.k * I.d;
+    std::vector<double> h(kd);
+    BCUDA(b, cudaMemcpy(h.data(), c_kxd, kd * sizeof(double), cudaMemcpyDefault));
+    for (double v : h)
+        if (!std::isfinite(v) || std::fabs(v) > 1e15)
+            return bfail(b, KNOR_ERR_ARG, "knor_batch_set_init_centroids: coordinate not finite or above 1e15");
+    BCUDA(b, cudaMemcpy(b->C0 + I.coff, h.data(), kd * sizeof(double), cudaMemcpyHostToDevice));
+    return breset(b);
+}
+
+knor_status knor_batch_iterate(knor_batch *b, knor_iter_stats *out) {
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    BCUDA(b, cudaMemsetAsync(b->flags + BF_RUN_ITER, 0, sizeof(int32_t), b->stream));
+    if (b->profiling) {
+        knor_status st = profiled_iter(b);
+        if (st != KNOR_OK) return st;
+    } else {
+        BCUDA(b, cudaGraphLaunch(b->iter_exec, b->stream));
+        BCUDA(b, cudaStreamSynchronize(b->stream));
+    }
+    return read_bstats(b, 1, out);
+}
+
+knor_status knor_batch_run(knor_batch *b, int32_t max_iters, int32_t *iters_done, knor_iter_stats *per_iter) {
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    if (iters_done) *iters_done = 0;
+    if (max_iters < 0 || max_iters > kBStatsCap) return bfail(b, KNOR_ERR_ARG, "knor_batch_run: max_iters out of range");
+    if (max_iters == 0) return KNOR_OK;
+    BCUDA(b, cudaMemsetAsync(b->flags + BF_RUN_ITER, 0, sizeof(int32_t), b->stream));
+    int32_t done = 0;
+    if (b->profiling) {
+        for (int t = 0; t < max_iters; ++t) {
+            knor_status st = profiled_iter(b);
+            if (st != KNOR_OK) return st;
+            done = t + 1;
+            int32_t any = 0;
+            std::vector<int32_t> act((size_t)b->m);
+            BCUDA(b, cudaMemcpy(act.data(), b->active, sizeof(int32_t) * act.size(), cudaMemcpyDeviceToHost));
+            for (int32_t v : act) any |= v;
+            if (!any) break;
+        }
+    } else {
+        BCUDA(b, cudaMemcpyAsync(b->flags + BF_MAX_ITERS, &max_iters, sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 b->stream));
+        BCUDA(b, cudaGraphLaunch(b->run_exec, b->stream));
+        BCUDA(b, cudaMemcpyAsync(&done, b->flags + BF_RUN_ITER, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+        BCUDA(b, cudaStreamSynchronize(b->stream));
+    }
+    if (iters_done) *iters_done = done;
+    return read_bstats(b, done, per_iter);
+}
+
+knor_status knor_batch_get_assignments(const knor_batch *bc, int32_t instance, int32_t *out_n) {
+    knor_batch *b = const_cast<knor_batch *>(bc);
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    if (check_instance(b, instance) != KNOR_OK || !out_n)
+        return bfail(b, KNOR_ERR_ARG, "knor_batch_get_assignments: bad instance or NULL output");
+    const BInst &I = b->h_inst[(size_t)instance];
+    int32_t *tmp = nullptr;
+    BCUDA(b, cudaMallocAsync(&tmp, sizeof(int32_t) * (size_t)I.n, b->stream));
+    k_bextract<<<gridfor(I.n, 256), 256, 0, b->stream>>>(b->st + I.poff, I.n, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_n, tmp, sizeof(int32_t) * (size_t)I.n, cudaMemcpyDefault, b->stream);
+    cudaFreeAsync(tmp, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    BCUDA(b, e);
+    return KNOR_OK;
+}
+
+knor_status knor_batch_get_centroids(const knor_batch *bc, int32_t instance, double *out_kxd) {
+    knor_batch *b = const_cast<knor_batch *>(bc);
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    if (check_instance(b, instance) != KNOR_OK || !out_kxd)
+        return bfail(b, KNOR_ERR_ARG, "knor_batch_get_centroids: bad instance or NULL output");
+    const BInst &I = b->h_inst[(size_t)instance];
+    BCUDA(b, cudaMemcpyAsync(out_kxd, b->C64 + I.coff, sizeof(double) * (size_t)I.k * I.d, cudaMemcpyDefault,
+                             b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    return KNOR_OK;
+}
+
+knor_status knor_batch_get_centroids_f32(const knor_batch *bc, int32_t instance, float *out_kxd) {
+    knor_batch *b = const_cast<knor_batch *>(bc);
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    if (check_instance(b, instance) != KNOR_OK || !out_kxd)
+        return bfail(b, KNOR_ERR_ARG, "knor_batch_get_centroids_f32: bad instance or NULL output");
+    const BInst &I = b->h_inst[(size_t)instance];
+    BCUDA(b, cudaMemcpyAsync(out_kxd, b->C32 + I.coff, sizeof(float) * (size_t)I.k * I.d, cudaMemcpyDefault,
+                             b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    return KNOR_OK;
+}
+
+knor_status knor_batch_get_init_indices(const knor_batch *b, int32_t instance, int64_t *out_k) {
+    if (!b || check_instance(b, instance) != KNOR_OK || !out_k) return KNOR_ERR_ARG;
+    const std::vector<int64_t> &v = b->init_idx[(size_t)instance];
+    std::memcpy(out_k, v.data(), sizeof(int64_t) * v.size());
+    return KNOR_OK;
+}
+
+knor_status knor_batch_get_instance(const knor_batch *bc, int32_t instance, knor_batch_instance *out) {
+    knor_batch *b = const_cast<knor_batch *>(bc);
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    if (check_instance(b, instance) != KNOR_OK || !out)
+        return bfail(b, KNOR_ERR_ARG, "knor_batch_get_instance: bad instance or NULL output");
+    int32_t it = 0, act = 0;
+    long long ch = 0;
+    BCUDA(b, cudaMemcpy(&it, b->iters + instance, sizeof(it), cudaMemcpyDeviceToHost));
+    BCUDA(b, cudaMemcpy(&act, b->active + instance, sizeof(act), cudaMemcpyDeviceToHost));
+    BCUDA(b, cudaMemcpy(&ch, b->changed_last + instance, sizeof(ch), cudaMemcpyDeviceToHost));
+    const BInst &I = b->h_inst[(size_t)instance];
+    out->n = I.n;
+    out->d = I.d;
+    out->k = I.k;
+    out->iterations = it;
+    out->converged = (it > 0 && ch == 0) ? 1 : 0;
+    out->changed_last = ch;
+    return KNOR_OK;
+}
+
+knor_status knor_batch_set_profiling(knor_batch *b, int32_t on) {
+    if (!b) return KNOR_ERR_ARG;
+    b->profiling = on != 0;
+    return KNOR_OK;
+}
+
+knor_status knor_batch_get_profile(knor_batch *b, knor_profile *out, int32_t reset_after) {
+    if (!b || !out) return KNOR_ERR_ARG;
+    for (int q = 0; q < KNOR_KERNEL_COUNT; ++q) {
+        out->launches[q] = b->prof_n[q];
+        out->ms[q] = b->prof_ms[q];
+        if (reset_after) { b->prof_n[q] = 0; b->prof_ms[q] = 0.0; }
+    }
+    return KNOR_OK;
+}
+
+const char *knor_batch_kernel_name(const knor_batch *b, int32_t kernel) {
+    if (!b) return "";
+    switch (kernel) {
+    case KNOR_KERNEL_MTI: return "k_bscan";
+    case KNOR_KERNEL_REDUCE: return "k_breduce";
+    case KNOR_KERNEL_TABLE: return "k_bstep + k_btable";
+    default: return "";
+    }
+}
+
+} // extern "C"

@@ -31,6 +31,10 @@ constexpr uint32_t kStateVersion = 1;
 // Device flags (int32 each).
 enum Flag { F_RUN_ITER = 0, F_TOTAL_ITER, F_MAX_ITERS, F_MODE_DENSE, F_NSLOTS, F_FRESH, F_ERR, F_COUNT };
 
+} // namespace
+
+namespace knor {
+
 // SplitMix64 (Steele, Lea and Flood 2014): golden-ratio increment, then the
 // published finaliser.
 uint64_t splitmix64(uint64_t &state) {
@@ -64,6 +68,10 @@ float f32_up(double v) { // smallest float >= v
     if ((double)f < v) f = std::nextafter(f, INFINITY);
     return f;
 }
+
+} // namespace knor
+
+namespace {
 
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at{};

@@ -1,6 +1,7 @@
 // knor_internal.cuh -- types and launch parameters shared by the kernels and
 // the host runtime of libknor.so.  Not part of the public ABI (include/knor.h).
 #pragma once
+#include <vector>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -184,6 +185,10 @@ cudaError_t launch_check_bounds(const float *X, int64_t n, int32_t d, const PtSt
                                 const int32_t *run_iter, cudaStream_t s);
 int supported_dv(int d); // template width used for d (0 = generic)
 void set_global_error(const char *msg); // message for knor_last_error(NULL)
+// Forgy initialisation: k distinct indices of [0, n) (Floyd's sampling on
+// SplitMix64(seed)), in the order drawn (knor_ctx.cu).
+std::vector<int64_t> forgy_indices(int64_t n, int32_t k, uint64_t seed);
+float f32_up(double v); // smallest float >= v
 
 // precision form (precision.cu)
 size_t prec_smem_bytes(int d, int k);

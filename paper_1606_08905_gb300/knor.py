@@ -49,6 +49,15 @@ class Profile(ctypes.Structure):
 
 KERNELS = ("dense", "mti", "reduce", "table", "recheck", "sums")
 
+
+class BatchInstance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("changed_last", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
 _SIGS = {
     "knor_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Opts),
@@ -75,6 +84,27 @@ _SIGS = {
     "knor_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "knor_destroy": (None, [ctypes.c_void_p]),
     "knor_version": (ctypes.c_char_p, []),
+    "knor_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_uint64, ctypes.POINTER(Opts),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "knor_batch_set_init_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "knor_batch_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "knor_batch_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(IterStats)]),
+    "knor_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(IterStats)]),
+    "knor_batch_get_assignments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "knor_batch_get_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "knor_batch_get_centroids_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "knor_batch_get_init_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "knor_batch_get_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(BatchInstance)]),
+    "knor_batch_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "knor_batch_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int32]),
+    "knor_batch_kernel_name": (ctypes.c_char_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "knor_batch_describe": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "knor_batch_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "knor_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "knor_batch_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -241,6 +271,131 @@ class Context:
     def set_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(load().knor_set_state(self._ctx, buf, len(blob)), self._ctx)
+
+
+def _bcheck(st: int, b):
+    if st != KNOR_OK:
+        msg = load().knor_batch_last_error(b) if b else load().knor_last_error(None)
+        raise KnorError(st, msg.decode() if msg else "")
+
+
+class Batch:
+    """m independent k-means problems advanced together (a knor_batch).
+
+    `points` is a list of n_i x d_i FP32 arrays or tensors (host or device),
+    `k` a list of cluster counts; instance i starts from Forgy with seed + i.
+    """
+
+    def __init__(self, points, k, seed: int = 0, prune: bool = True):
+        lib = load()
+        m = len(points)
+        if len(k) != m:
+            raise ValueError("one k per instance")
+        keep = []
+        ptrs = (ctypes.c_void_p * m)()
+        ns = (ctypes.c_int64 * m)()
+        ds = (ctypes.c_int32 * m)()
+        ks = (ctypes.c_int32 * m)()
+        self.shapes = []
+        for i, X in enumerate(points):
+            shape = tuple(X.shape)
+            if len(shape) != 2:
+                raise ValueError("points must be n x d")
+            ptr, kp = _ptr(X, np.float32)
+            keep.append(kp)
+            ptrs[i] = ptr
+            ns[i], ds[i], ks[i] = int(shape[0]), int(shape[1]), int(k[i])
+            self.shapes.append((int(shape[0]), int(shape[1]), int(k[i])))
+        opts = Opts(0 if prune else 1, 0, 0, 0)
+        out = ctypes.c_void_p()
+        st = lib.knor_batch_create(m, ptrs, ns, ds, ks, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opts),
+                                   ctypes.byref(out))
+        del keep
+        _bcheck(st, None)
+        self._b = out.value
+        self.m = m
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().knor_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_init_centroids(self, i: int, C):
+        ptr, keep = _ptr(C, np.float64)
+        _bcheck(load().knor_batch_set_init_centroids(self._b, int(i), ptr), self._b)
+
+    def reset(self):
+        _bcheck(load().knor_batch_reset(self._b), self._b)
+
+    def iterate(self) -> dict:
+        s = IterStats()
+        _bcheck(load().knor_batch_iterate(self._b, ctypes.byref(s)), self._b)
+        return s.as_dict()
+
+    def run(self, max_iters: int):
+        recs = (IterStats * max(1, max_iters))()
+        done = ctypes.c_int32(0)
+        _bcheck(load().knor_batch_run(self._b, int(max_iters), ctypes.byref(done), recs), self._b)
+        return int(done.value), [recs[i].as_dict() for i in range(done.value)]
+
+    def assignments(self, i: int, out=None):
+        if out is None:
+            out = np.empty(self.shapes[i][0], np.int32)
+        ptr, _ = _ptr(out, np.int32)
+        _bcheck(load().knor_batch_get_assignments(self._b, int(i), ptr), self._b)
+        return out
+
+    def centroids(self, i: int):
+        n, d, k = self.shapes[i]
+        out = np.empty((k, d), np.float64)
+        _bcheck(load().knor_batch_get_centroids(self._b, int(i), out.ctypes.data), self._b)
+        return out
+
+    def centroids_f32(self, i: int):
+        n, d, k = self.shapes[i]
+        out = np.empty((k, d), np.float32)
+        _bcheck(load().knor_batch_get_centroids_f32(self._b, int(i), out.ctypes.data), self._b)
+        return out
+
+    def init_indices(self, i: int):
+        out = np.empty(self.shapes[i][2], np.int64)
+        _bcheck(load().knor_batch_get_init_indices(self._b, int(i), out.ctypes.data), self._b)
+        return out
+
+    def instance(self, i: int) -> dict:
+        r = BatchInstance()
+        _bcheck(load().knor_batch_get_instance(self._b, int(i), ctypes.byref(r)), self._b)
+        return r.as_dict()
+
+    def set_profiling(self, on: bool):
+        _bcheck(load().knor_batch_set_profiling(self._b, 1 if on else 0), self._b)
+
+    def profile(self, reset: bool = False) -> dict:
+        pr = Profile()
+        _bcheck(load().knor_batch_get_profile(self._b, ctypes.byref(pr), 1 if reset else 0), self._b)
+        return {name: (int(pr.launches[i]), float(pr.ms[i])) for i, name in enumerate(KERNELS)}
+
+    def kernel_name(self, kernel: str) -> str:
+        return load().knor_batch_kernel_name(self._b, KERNELS.index(kernel)).decode()
+
+    def describe(self) -> str:
+        return load().knor_batch_describe(self._b).decode()
+
+    @property
+    def stream(self) -> int:
+        return int(load().knor_batch_stream(self._b) or 0)
 
 
 def lloyd_step_noalloc(points, centroids, assign_out, sums_out, counts_out, stream: int = 0):

@@ -52,3 +52,18 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.knor_iterate(None, None) == knor.KNOR_ERR_ARG
     assert lib.knor_reset(None) == knor.KNOR_ERR_ARG
     lib.knor_destroy(None)  # no-op
+
+
+def test_batch_create_rejects_bad_instances_without_touching_the_gpu(lib):
+    out = ctypes.c_void_p()
+    pts = np.zeros((4, 8), np.float32)
+    ptrs = (ctypes.c_void_p * 1)(pts.ctypes.data)
+    for n, d, k in [(4, 8, 5), (4, 12, 2), (4, 8, 0), (0, 8, 1), (400, 8, 257)]:
+        st = lib.knor_batch_create(1, ptrs, (ctypes.c_int64 * 1)(n), (ctypes.c_int32 * 1)(d),
+                                   (ctypes.c_int32 * 1)(k), 1, None, ctypes.byref(out))
+        assert st == knor.KNOR_ERR_ARG
+        assert out.value is None
+        assert lib.knor_last_error(None)
+    assert lib.knor_batch_create(0, ptrs, None, None, None, 1, None, ctypes.byref(out)) == knor.KNOR_ERR_ARG
+    assert lib.knor_batch_iterate(None, None) == knor.KNOR_ERR_ARG
+    lib.knor_batch_destroy(None)  # no-op
