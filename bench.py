@@ -220,12 +220,237 @@ def reference_arm(args, wl, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def batch_reference_arm(args, wl, world, rank):
+    """The FP64 oracle on the batched workload: whole runs of its instances,
+    smallest first, for a bounded time per step."""
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    from paper_1606_08905_gb300 import synth
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    specs = sorted(synth.batched_specs(wl["m"], wl["data_seed"]), key=lambda s: s.n)
+
+    def one_step():
+        pts, secs, used = 0, 0.0, 0
+        for sp in specs:
+            if secs >= per_step:
+                break
+            Xs = synth.batched_instance(sp).numpy()
+            p, dt, _ = cpu_oracle_run(Xs, sp.k, wl["max_iters"], wl["prune"], threads)
+            pts += p
+            secs += dt
+            used += 1
+        return pts, secs, used
+
+    for _ in range(args.warmup):
+        one_step()
+    pts, secs, used = 0, 0.0, 0
+    for _ in range(args.steps):
+        p, dt, used = one_step()
+        pts += p
+        secs += dt
+    value = pts / secs
+    sample = (f"the {used} smallest of the {wl['m']} instances, a full run of each ({'MTI' if wl['prune'] else 'plain'}, "
+              f"FP64), per step")
+    line = {
+        "impl": "reference", "metric": "point-iterations/sec", "value": value,
+        "unit": "point-iterations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl, args.workload, world),
+        "cpu_baseline": {"value": value, "unit": "point-iterations/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "point-iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def batch_arm(args, wl, world, rank, local):
+    """The batched form: every instance of the workload, one knor_batch_run
+    per step (from C^0, up to max_iters iterations)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1606_08905_gb300 import build as kbuild
+    from paper_1606_08905_gb300 import knor, synth
+    kbuild.build()
+    knor.load()
+    torch.cuda.set_device(local)
+    T = wl["max_iters"]
+    specs = synth.batched_specs(wl["m"], wl["data_seed"])
+    Xd = [synth.batched_instance(sp, device="cuda") for sp in specs]
+    ks = [sp.k for sp in specs]
+    torch.cuda.synchronize()
+    b = knor.Batch(Xd, ks, seed=42, prune=wl["prune"])
+    stream = torch.cuda.ExternalStream(b.stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        b.reset()
+        b.run(T)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, pit = [], 0
+    for _ in range(args.steps):
+        b.reset()
+        done, _ = b.run(T)
+        iters.append(done)
+        pit += b.work()[0]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms, float(pit)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, pts_all = float(mx[0]), float(t[1])
+    else:
+        ms_max, pts_all = ms, float(pit)
+    value = pts_all / (ms_max / 1000.0)
+    launches = sum(3 + 4 * it for it in iters)
+
+    # per-kernel event timing; the scan's roofline over the MTI iterations
+    # (iteration 1 is the full scan from C^0 and is timed apart)
+    peaks, peak_src = measured_peaks()
+    b.set_profiling(True)
+    b.reset()
+    b.profile(reset=True)
+    b.iterate()
+    first = b.profile(reset=True)
+    w1 = b.work()
+    done, recs = b.run(T - 1)
+    prof = b.profile(reset=True)
+    w2 = b.work()
+    b.set_profiling(False)
+    n_scan, ms_scan = prof["mti"]
+    mti_bytes = w2[1] - w1[1]
+    gbs = mti_bytes / (ms_scan / 1000.0) / 1e9 if ms_scan > 0 else 0.0
+    kernels = {
+        "scan_iteration1": {"kernel": "k_bscan", "launches": first["mti"][0], "ms_total": first["mti"][1],
+                            "point_iterations": w1[0], "algorithmic_bytes": w1[1]},
+        "scan_mti": {"kernel": "k_bscan", "launches": n_scan, "ms_total": ms_scan,
+                     "ms_per_launch": ms_scan / max(1, n_scan), "algorithmic_bytes_per_launch": mti_bytes / max(1, n_scan),
+                     "achieved_gbs": gbs},
+        "reduce": {"kernel": "k_breduce", "launches": prof["reduce"][0], "ms_total": prof["reduce"][1]},
+        "table": {"kernel": "k_bstep + k_btable", "launches": prof["table"][0], "ms_total": prof["table"][1]},
+    }
+    total_ms = sum(v[1] for v in prof.values()) + sum(v[1] for v in first.values())
+    roof = {"kernel": "k_bscan", "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+            "peak_source": peak_src, "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "traffic": ncu_traffic("k_bscan", args.workload),
+            "share_of_kernel_time": (ms_scan + first["mti"][1]) / total_ms if total_ms else None,
+            "scope": "MTI iterations (2..); iteration 1 is the full scan from C^0"}
+
+    # plain Lloyd on the same batch
+    plain = None
+    if not args.no_plain:
+        with knor.Batch(Xd, ks, seed=42, prune=False) as bp:
+            bp.reset()
+            bp.run(T)
+            ps = torch.cuda.ExternalStream(bp.stream)
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(ps)
+            bp.reset()
+            bp.run(T)
+            ppit = bp.work()[0]
+            q1.record(ps)
+            torch.cuda.synchronize()
+            same = all(np.array_equal(bp.assignments(i), b.assignments(i)) for i in range(0, wl["m"], 17))
+            pv = ppit / (q0.elapsed_time(q1) / 1000.0)
+            plain = {"value": pv, "unit": "point-iterations/s", "speedup": (value / world) / pv,
+                     "identical_assignments_every_17th_instance": bool(same)}
+
+    # e2e through the C ABI from pinned host memory: create, run, read back
+    e2e = None
+    if not args.no_e2e:
+        Xh = []
+        for x in Xd:
+            h = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+            h.copy_(x)
+            Xh.append(h)
+        outs = [torch.empty(sp.n, dtype=torch.int32, pin_memory=True) for sp in specs]
+        del b
+        torch.cuda.synchronize()
+        es = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        e_pit = 0
+        for _ in range(es):
+            with knor.Batch(Xh, ks, seed=42, prune=wl["prune"]) as b2:
+                b2.run(T)
+                for i in range(wl["m"]):
+                    b2.assignments(i, outs[i])
+                e_pit += b2.work()[0]
+        dt = time.perf_counter() - t0
+        ntot = sum(sp.n for sp in specs)
+        e2e = {"value": e_pit / dt, "unit": "point-iterations/s",
+               "h2d_bytes_per_step": sum(sp.n * sp.d * 4 for sp in specs), "d2h_bytes_per_step": ntot * 4,
+               "steps": es, "ms_per_step": 1000.0 * dt / es,
+               "includes": "knor_batch_create (H2D copies, validation, allocation, tuning from the cache, graph "
+                           "build), knor_batch_run, knor_batch_get_assignments for every instance, destroy"}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        threads = os.cpu_count() or 1
+        srt = sorted(specs, key=lambda sp: sp.n)
+        pts, secs, used = 0, 0.0, 0
+        for sp in srt:
+            if secs >= args.cpu_seconds:
+                break
+            Xs = synth.batched_instance(sp).numpy()
+            p, dt, _ = cpu_oracle_run(Xs, sp.k, T, wl["prune"], threads)
+            pts += p
+            secs += dt
+            used += 1
+        cpu = {"value": pts / secs, "unit": "point-iterations/s", "cores": threads, "kind": "oracle",
+               "sample": f"full runs of the {used} smallest of the {wl['m']} instances "
+                         f"({'MTI' if wl['prune'] else 'plain'}, FP64), {secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": "point-iterations/sec", "value": value, "unit": "point-iterations/s",
+                "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(wl, args.workload, world),
+                "iterations_per_step": iters, "roofline": roof, "kernels": kernels,
+                "cpu_baseline": cpu, "e2e": e2e, "vs_plain_fp32": plain,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def synth_n(name):
     from paper_1606_08905_gb300 import synth
     return synth.WORKLOADS[name]["n"]
 
 
+def batch_bytes(wl):
+    from paper_1606_08905_gb300 import synth
+    return sum(sp.n * sp.d * 4 for sp in synth.batched_specs(wl["m"], wl["data_seed"]))
+
+
 def config_of(wl, name, world):
+    if wl["kind"] == "batched":
+        return {"workload": name, "instances": wl["m"], "total_points": wl["n"],
+                "n_i": "log-uniform in [1e3, 1e6]", "d_i": "uniform over {8, 16, 32, 64}",
+                "k_i": "uniform on {4..256}", "max_iters": wl["max_iters"],
+                "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42 + instance",
+                "data_seed": wl["data_seed"], "points_dtype": "f32",
+                "l2": f"inputs larger than L2 ({batch_bytes(wl) / 1e9:.2f} GB of points)",
+                "parallelism": f"replicas x{world}"}
     return {"workload": name if wl["n"] == synth_n(name) else f"{name} (n overridden)", "n": wl["n"],
             "distance": (wl["precision"].upper() + " tensor cores + exact FP32 recheck"
                          if wl.get("precision", "fp32") != "fp32" else "FP32"), "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
@@ -444,7 +669,7 @@ def main():
     if args.precision and wl.get("precision", "fp32") != "fp32":
         wl["precision"] = args.precision
     if args.impl == "reference":
-        reference_arm(args, wl, world, rank)
+        (batch_reference_arm if wl["kind"] == "batched" else reference_arm)(args, wl, world, rank)
         return
     if world > 1:
         import torch
@@ -452,7 +677,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
     try:
-        our_arm(args, wl, world, rank, local)
+        (batch_arm if wl["kind"] == "batched" else our_arm)(args, wl, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist

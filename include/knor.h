@@ -282,6 +282,11 @@ knor_status knor_batch_get_centroids(const knor_batch *b, int32_t instance, doub
 knor_status knor_batch_get_centroids_f32(const knor_batch *b, int32_t instance, float *out_kxd);
 knor_status knor_batch_get_init_indices(const knor_batch *b, int32_t instance, int64_t *out_k);
 knor_status knor_batch_get_instance(const knor_batch *b, int32_t instance, knor_batch_instance *out);
+/* Work since the last reset: point-iterations (sum over the iterations of the
+ * points of every instance that ran in it) and the scan's algorithmic bytes
+ * (8 per point for the state read; 4d + 8 more per point not skipped by
+ * Clause 1: its row and the state write). */
+knor_status knor_batch_get_work(const knor_batch *b, int64_t *point_iterations, int64_t *scan_bytes);
 /* Profiling as for a context; the batch fills the KNOR_KERNEL_MTI (scan),
  * KNOR_KERNEL_REDUCE (merge) and KNOR_KERNEL_TABLE (bookkeeping + table)
  * slots. */

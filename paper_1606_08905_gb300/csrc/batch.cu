@@ -43,7 +43,8 @@ namespace knor {
 
 constexpr int BT = 256;            // threads of the scan CTA
 constexpr int B_KMAX = 256;        // largest k of an instance
-constexpr int B_PART_CAP = 4096;   // k x d up to which a unit sums in shared memory
+constexpr int B_PART_CAP = 2048;   // k x d up to which a unit sums in shared memory
+constexpr int B_QC = 1024;         // points per chunk of the pruned scan's queue
 
 struct BInst {
     int64_t n;      // points
@@ -64,6 +65,7 @@ struct BUnit {
 
 struct BCounters {
     unsigned long long changed, skipped, evals, empty;
+    unsigned long long bytes; // algorithmic bytes of the scan: 8 per point, + 4d + 8 per scanned point
 };
 
 struct BParams {
@@ -83,6 +85,7 @@ struct BParams {
     long long *changed_last;  // per instance: changed count of its last iteration
     BCounters *bctr;          // per instance, this iteration
     const int32_t *cinst;     // per global centroid: its instance
+    unsigned long long *work; // since reset: [0] point-iterations, [1] scan bytes
     IterStats *stats;
     int32_t *run_iter, *total_iter;
     const int32_t *max_iters_dev;
@@ -93,79 +96,200 @@ struct BParams {
 
 // ------------------------------------------------------------------- scan
 
+// The new state of one scanned point and its delta sums.
+template <int DV>
+__device__ __forceinline__ void commit_point(const BInst &I, PtState *st, int64_t i, int a, int best, float bd,
+                                             const unsigned long long (&x)[DV / 2], const float *F_s,
+                                             double *part, long long *pcnt, double *D, long long *Dc,
+                                             long long &changed) {
+    PtState ns;
+    ns.a = best;
+    ns.ub = __fsub_ru(bound_up(bd, I.g_up, I.tiny), F_s[best]);
+    st[i] = ns;
+    if (best == a) return;
+    ++changed;
+    double *dst_new = part ? part + (size_t)best * DV : D + (size_t)best * DV;
+    double *dst_old = a >= 0 ? (part ? part + (size_t)a * DV : D + (size_t)a * DV) : nullptr;
+#pragma unroll
+    for (int j = 0; j < DV / 2; ++j) {
+        float x0, x1;
+        unpack2(x[j], x0, x1);
+        atomicAdd(dst_new + 2 * j, (double)x0);
+        atomicAdd(dst_new + 2 * j + 1, (double)x1);
+        if (dst_old) {
+            atomicAdd(dst_old + 2 * j, -(double)x0);
+            atomicAdd(dst_old + 2 * j + 1, -(double)x1);
+        }
+    }
+    atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + best : Dc + best), 1ULL);
+    if (a >= 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + a : Dc + a), (unsigned long long)-1LL);
+}
+
+// Full scan of one point (iteration 1 and plain Lloyd): strict <, so the
+// lowest index wins ties.
+template <int DV>
+__device__ __forceinline__ void full_scan(const unsigned long long (&x)[DV / 2], const float *cent, int k,
+                                          int &best, float &bd) {
+    bd = CUDART_INF_F;
+    best = 0;
+    for (int c = 0; c < k; ++c) {
+        const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
+        if (r < bd) { bd = r; best = c; }
+    }
+}
+
+// One unit.  Plain Lloyd and points without a centroid yet: thread per
+// point, full scans (every lane runs the same loop).  MTI: the unit is taken
+// in chunks of B_QC points; Clause 1 (u^t = ub + F^t(a) against s(a)) drops
+// most points, the survivors are queued and counting-sorted by their cluster
+// so that a warp's lanes share a row of the half-distance table; each lane
+// tightens u to d(v, c_a) (Clause 3), builds its candidate mask 32 centroids
+// at a time (Clause 2: c survives unless u < 1/2 d(c_a, c)), and the warp
+// evaluates the union of its lanes' masks in index order -- a lane adopts c
+// only if c is in its own mask, exactly as in its own pruned scan.
 template <int DV>
 __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int64_t lo, int64_t hi,
                                           const float *cent, const float *s_s, const float *F_s, double *part,
-                                          long long *pcnt, long long &changed, long long &skipped,
-                                          long long &evals) {
+                                          long long *pcnt, int2 *queue, int2 *sorted, int *hist, int *qn,
+                                          long long &changed, long long &skipped, long long &evals) {
     const int k = I.k;
     const float *X = p.X + I.xoff;
     PtState *st = p.st + I.poff;
     const float *halfD = p.halfD + I.hoff;
     double *D = p.D + I.coff;
     long long *Dc = p.Dcnt + I.koff;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += BT) {
-        const PtState ps = st[i];
-        const int a = ps.a;
-        if (p.mti && a >= 0) {
-            // Clause 1 with u^t = ub + F^t(a)
-            const float uu = __fadd_ru(ps.ub, F_s[a]);
-            if (__fmaf_ru(uu, I.onepk, I.tau) < s_s[a]) {
-                ++skipped;
-                continue;
-            }
-        }
-        unsigned long long x[DV / 2];
-        ldg_x2<DV>(x, X + i * DV);
-        int best;
-        float bd;
-        if (a < 0 || !p.mti) {
-            bd = CUDART_INF_F;
-            best = 0;
-            for (int c = 0; c < k; ++c) {
-                const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
-                if (r < bd) { bd = r; best = c; }
-            }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (!p.mti) {
+        for (int64_t i = lo + tid; i < hi; i += BT) {
+            const int a = st[i].a;
+            unsigned long long x[DV / 2];
+            ldg_x2<DV>(x, X + i * DV);
+            int best;
+            float bd;
+            full_scan<DV>(x, cent, k, best, bd);
             evals += k;
-        } else {
-            // Clause 3 tightens u to d(v, c_a); Clause 2 skips every c with
-            // u < 1/2 d(c_a, c)
-            bd = d2_reg<DV>(x, cent + (size_t)a * DV);
-            best = a;
-            ++evals;
-            const float test = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
-            const float *hrow = halfD + (size_t)a * k;
-            for (int c = 0; c < k; ++c) {
-                if (c == a) continue;
-                if (test < __ldg(hrow + c)) continue;
-                const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
-                ++evals;
-                if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+            if (!p.dry) commit_point<DV>(I, st, i, a, best, bd, x, F_s, part, pcnt, D, Dc, changed);
+        }
+        return;
+    }
+    for (int64_t c0 = lo; c0 < hi; c0 += B_QC) {
+        const int64_t c1 = min(hi, c0 + (int64_t)B_QC);
+        // ---- Clause 1; survivors into the queue (warp-aggregated appends)
+        if (tid == 0) *qn = 0;
+        for (int c = tid; c <= k; c += BT) hist[c] = 0;
+        __syncthreads();
+        for (int64_t base = c0; base < c1; base += BT) {
+            const int64_t i = base + tid;
+            bool act = false;
+            int a = -1;
+            if (i < c1) {
+                const PtState ps = st[i];
+                a = ps.a;
+                act = true;
+                if (a >= 0) {
+                    const float uu = __fadd_ru(ps.ub, F_s[a]);
+                    act = !(__fmaf_ru(uu, I.onepk, I.tau) < s_s[a]);
+                }
+                if (!act) ++skipped;
+            }
+            const unsigned m = __ballot_sync(FULL_MASK, act);
+            int pos = 0;
+            if (m) {
+                if (lane == __ffs(m) - 1) pos = atomicAdd(qn, __popc(m));
+                pos = __shfl_sync(FULL_MASK, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
+            }
+            if (act) {
+                queue[pos] = make_int2((int)(i - c0), a);
+                atomicAdd(&hist[a + 1], 1); // key a + 1: a = -1 (no centroid yet) first
             }
         }
-        if (p.dry) continue;
-        PtState ns;
-        ns.a = best;
-        ns.ub = __fsub_ru(bound_up(bd, I.g_up, I.tiny), F_s[best]);
-        st[i] = ns;
-        if (best == a) continue;
-        ++changed;
-        double *dst_new = part ? part + (size_t)best * DV : D + (size_t)best * DV;
-        double *dst_old = a >= 0 ? (part ? part + (size_t)a * DV : D + (size_t)a * DV) : nullptr;
+        __syncthreads();
+        const int n_act = *qn;
+        if (n_act == 0) {
+            __syncthreads();
+            continue;
+        }
+        // ---- counting sort by cluster
+        if (warp == 0) {
+            int carry = 0;
+            for (int base = 0; base <= k; base += 32) {
+                const int c = base + lane;
+                const int v = c <= k ? hist[c] : 0;
+                int incl = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL_MASK, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (c <= k) hist[c] = carry + incl - v; // exclusive start
+                carry += __shfl_sync(FULL_MASK, incl, 31);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < n_act; e += BT) {
+            const int2 q = queue[e];
+            sorted[atomicAdd(&hist[q.y + 1], 1)] = q;
+        }
+        __syncthreads();
+        // ---- pruned scans, 32 queued points per warp at a time
+        for (int wb = warp * 32; wb < n_act; wb += BT) {
+            const int e = wb + lane;
+            const bool has = e < n_act;
+            const int2 q = has ? sorted[e] : make_int2(0, -2);
+            const int64_t i = c0 + q.x;
+            const int a = q.y;
+            unsigned long long x[DV / 2];
+            if (has) ldg_x2<DV>(x, X + i * DV);
+            else {
 #pragma unroll
-        for (int j = 0; j < DV / 2; ++j) {
-            float x0, x1;
-            unpack2(x[j], x0, x1);
-            atomicAdd(dst_new + 2 * j, (double)x0);
-            atomicAdd(dst_new + 2 * j + 1, (double)x1);
-            if (dst_old) {
-                atomicAdd(dst_old + 2 * j, -(double)x0);
-                atomicAdd(dst_old + 2 * j + 1, -(double)x1);
+                for (int j = 0; j < DV / 2; ++j) x[j] = 0ULL;
             }
+            int best = 0;
+            float bd = CUDART_INF_F;
+            const bool anyfull = __any_sync(FULL_MASK, has && a < 0);
+            if (anyfull) {
+                // points without a centroid yet (all full scans, run together)
+                if (has && a < 0) {
+                    full_scan<DV>(x, cent, k, best, bd);
+                    evals += k;
+                }
+            }
+            float test = 0.0f;
+            const float *hrow = halfD;
+            if (has && a >= 0) {
+                bd = d2_reg<DV>(x, cent + (size_t)a * DV);
+                best = a;
+                ++evals;
+                test = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
+                hrow = halfD + (size_t)a * k;
+            }
+            const bool pruned_scan = has && a >= 0;
+            if (__any_sync(FULL_MASK, pruned_scan)) {
+                for (int wbase = 0; wbase < k; wbase += 32) {
+                    unsigned word = 0;
+                    if (pruned_scan) {
+                        const int lim = min(32, k - wbase);
+                        for (int b = 0; b < lim; ++b) {
+                            const int c = wbase + b;
+                            if (c != a && !(test < __ldg(hrow + c))) word |= 1u << b;
+                        }
+                    }
+                    unsigned uni = __reduce_or_sync(FULL_MASK, word);
+                    while (uni) {
+                        const int b = __ffs(uni) - 1;
+                        uni &= uni - 1;
+                        const int c = wbase + b;
+                        const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
+                        if ((word >> b) & 1u) {
+                            ++evals;
+                            if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+                        }
+                    }
+                }
+            }
+            if (has && !p.dry) commit_point<DV>(I, st, i, a, best, bd, x, F_s, part, pcnt, D, Dc, changed);
         }
-        atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + best : Dc + best), 1ULL);
-        if (a >= 0)
-            atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + a : Dc + a), (unsigned long long)-1LL);
+        __syncthreads();
     }
 }
 
@@ -192,6 +316,10 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
     float *F_s = s_s + p.k_max;
     double *part = reinterpret_cast<double *>(F_s + p.k_max + ((p.kd_max + 2 * p.k_max) & 1));
     long long *pcnt = reinterpret_cast<long long *>(part + min(p.kd_max, B_PART_CAP));
+    int2 *queue = reinterpret_cast<int2 *>(pcnt + p.k_max);
+    int2 *sorted = queue + B_QC;
+    int *hist = reinterpret_cast<int *>(sorted + B_QC);
+    int *qn = hist + p.k_max + 1;
     const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) s_unit = (int)atomicAdd(p.qctr, 1u);
@@ -218,10 +346,10 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
         double *pp = use_part ? part : nullptr;
         long long *pc = use_part ? pcnt : nullptr;
         switch (I.d) {
-        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
-        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
-        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
-        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, sk, ev); break;
+        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
+        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
+        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
+        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
         }
         __syncthreads();
         if (use_part) {
@@ -237,9 +365,11 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
         ev = block_sum(ev, red);
         if (tid == 0 && !p.dry) {
             BCounters *b = p.bctr + U.inst;
+            const long long np = U.hi - U.lo;
             if (ch) atomicAdd(&b->changed, (unsigned long long)ch);
             if (sk) atomicAdd(&b->skipped, (unsigned long long)sk);
             if (ev) atomicAdd(&b->evals, (unsigned long long)ev);
+            atomicAdd(&b->bytes, (unsigned long long)(8 * np + (np - sk) * (4LL * I.d + 8)));
         }
         __syncthreads();
     }
@@ -283,7 +413,7 @@ __global__ void k_breduce(const BParams p) {
 __global__ void k_bstep(const BParams p, int32_t snapshot) {
     __shared__ unsigned long long red[4][32];
     __shared__ int any_s;
-    unsigned long long ch = 0, sk = 0, ev = 0, em = 0;
+    unsigned long long ch = 0, sk = 0, ev = 0, em = 0, pts = 0, by = 0;
     int any = 0;
     if (threadIdx.x == 0) any_s = 0;
     __syncthreads();
@@ -296,12 +426,18 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
             sk += b.skipped;
             ev += b.evals;
             em += b.empty;
+            pts += (unsigned long long)p.inst[i].n;
+            by += b.bytes;
             if (b.changed == 0) p.active[i] = 0;
         }
         any |= p.active[i];
-        p.bctr[i] = BCounters{0, 0, 0, 0};
+        p.bctr[i] = BCounters{0, 0, 0, 0, 0};
     }
     if (any) atomicOr(&any_s, 1);
+    if (snapshot) {
+        if (pts) atomicAdd(&p.work[0], pts);
+        if (by) atomicAdd(&p.work[1], by);
+    }
     for (int o = 16; o > 0; o >>= 1) {
         ch += __shfl_xor_sync(FULL_MASK, ch, o);
         sk += __shfl_xor_sync(FULL_MASK, sk, o);
@@ -336,10 +472,15 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
     }
 }
 
-// K1 per centroid a of every active instance, from the FP32 scan copies in
-// FP64 with directed rounding (the single-problem table's arithmetic): drift
-// f(a) rounded up and added to F(a); 1/2 d(c_a, c) rounded down; s(a) their
-// minimum over c != a; then the new scan copy replaces the old one.
+// K1 per centroid a of every active instance, from the FP32 scan copies,
+// in FP32 with directed rounding on the library's FP32 distance d~^2 (for
+// which d~^2 <= d^2 g + tiny and d^2 <= d~^2 g + tiny, g = 1/(1 - (d+2)
+// 2^-24)): the drift f(a) <= sqrt(d~^2 g + tiny) rounded up and added
+// (rounded up) to F(a); 1/2 d(c_a, c) >= 1/2 sqrt((d~^2 - tiny) / g)
+// rounded down; s(a) their minimum over c != a; then the new scan copy
+// replaces the old one.  (The single-problem table computes the same bounds
+// in FP64; these are a little looser but need no FP64 units, which matters
+// with up to 256 x 256 pairs per instance.)
 __global__ void k_btable(const BParams p, int32_t need_table) {
     const int g = blockIdx.x;
     const int i = p.cinst[g];
@@ -348,36 +489,19 @@ __global__ void k_btable(const BParams p, int32_t need_table) {
     const int a = g - I.koff, k = I.k, d = I.d, tid = threadIdx.x;
     const float *Cn = p.C32n + I.coff;
     float *Co = p.C32 + I.coff;
-    __shared__ double red[128];
     __shared__ float redf[128];
     if (need_table) {
-        double acc = 0.0;
-        for (int j = tid; j < d; j += blockDim.x) {
-            const double x = Cn[(size_t)a * d + j], y = Co[(size_t)a * d + j];
-            const double lo = __dsub_rd(x, y), hi = __dsub_ru(x, y);
-            const double mm = fmax(fabs(lo), fabs(hi));
-            acc = __dadd_ru(acc, __dmul_ru(mm, mm));
-        }
-        red[tid] = acc;
-        __syncthreads();
         if (tid == 0) {
-            double t = 0.0;
-            for (int q = 0; q < (int)blockDim.x; ++q) t = __dadd_ru(t, red[q]);
-            const float fa = __double2float_ru(__dsqrt_ru(t));
-            p.F[g] = __fadd_ru(p.F[g], fa);
+            const float d2 = d2_gen(Cn + (size_t)a * d, Co + (size_t)a * d, d);
+            p.F[g] = __fadd_ru(p.F[g], bound_up(d2, I.g_up, I.tiny));
         }
         float mymin = CUDART_INF_F;
         float *hrow = p.halfD + I.hoff + (size_t)a * k;
         for (int c = tid; c < k; c += blockDim.x) {
             if (c == a) { hrow[c] = 0.0f; continue; }
-            double sdd = 0.0;
-            for (int j = 0; j < d; ++j) {
-                const double x = Cn[(size_t)a * d + j], y = Cn[(size_t)c * d + j];
-                const double lo = __dsub_rd(x, y), hi = __dsub_ru(x, y);
-                const double mm = lo > 0.0 ? lo : (hi < 0.0 ? -hi : 0.0);
-                sdd = __dadd_rd(sdd, __dmul_rd(mm, mm));
-            }
-            const float h = __double2float_rd(__dmul_rd(0.5, __dsqrt_rd(sdd)));
+            const float d2 = d2_gen(Cn + (size_t)a * d, Cn + (size_t)c * d, d);
+            const float lo2 = fmaxf(__fdiv_rd(__fsub_rd(d2, I.tiny), I.g_up), 0.0f);
+            const float h = __fmul_rd(0.5f, __fsqrt_rd(lo2));
             hrow[c] = h;
             mymin = fminf(mymin, h);
         }
@@ -451,6 +575,7 @@ struct knor_batch {
     unsigned *qctr = nullptr;
     int32_t *active = nullptr, *iters = nullptr, *cinst = nullptr, *flags = nullptr;
     BCounters *bctr = nullptr;
+    unsigned long long *work = nullptr;
     IterStats *stats = nullptr;
     int64_t *d_idx = nullptr;
     size_t smem = 0;
@@ -491,7 +616,7 @@ knor_status balloc(knor_batch *b, T **p, size_t count) {
 void bfree_all(knor_batch *b) {
     void *bufs[] = {b->X,    b->C32,   b->C32n, b->halfD, b->s,      b->F,     b->st,     b->C0,
                     b->C64,  b->S,     b->D,    b->cnt,   b->Dcnt,   b->changed_last, b->inst, b->units,
-                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx};
+                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx, b->work};
     for (void *p : bufs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : b->ev)
@@ -525,6 +650,7 @@ BParams params_of(const knor_batch *b, int dry, unsigned long long cond, const B
     p.changed_last = b->changed_last;
     p.bctr = b->bctr;
     p.cinst = b->cinst;
+    p.work = b->work;
     p.stats = b->stats;
     p.run_iter = b->flags + BF_RUN_ITER;
     p.total_iter = b->flags + BF_TOTAL_ITER;
@@ -645,6 +771,7 @@ knor_status breset(knor_batch *b) {
     BCUDA(b, cudaMemsetAsync(b->Dcnt, 0, tk * sizeof(long long), s));
     BCUDA(b, cudaMemsetAsync(b->F, 0, tk * sizeof(float), s));
     BCUDA(b, cudaMemsetAsync(b->bctr, 0, (size_t)b->m * sizeof(BCounters), s));
+    BCUDA(b, cudaMemsetAsync(b->work, 0, 2 * sizeof(unsigned long long), s));
     BCUDA(b, cudaMemsetAsync(b->iters, 0, (size_t)b->m * sizeof(int32_t), s));
     BCUDA(b, cudaMemsetAsync(b->changed_last, 0, (size_t)b->m * sizeof(long long), s));
     std::vector<int32_t> ones((size_t)b->m, 1);
@@ -942,6 +1069,7 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     BC(balloc(b, &b->iters, (size_t)m));
     BC(balloc(b, &b->changed_last, (size_t)m));
     BC(balloc(b, &b->bctr, (size_t)m));
+    BC(balloc(b, &b->work, 2));
     BC(balloc(b, &b->qctr, 1));
     BC(balloc(b, &b->flags, BF_COUNT));
     BC(balloc(b, &b->stats, kBStatsCap));
@@ -980,7 +1108,8 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     }
     // scan launch shape
     b->smem = sizeof(float) * ((size_t)b->kd_max + 2 * b->k_max + 1) +
-              sizeof(double) * (size_t)std::min(b->kd_max, B_PART_CAP) + sizeof(long long) * b->k_max + 16;
+              sizeof(double) * (size_t)std::min(b->kd_max, B_PART_CAP) + sizeof(long long) * b->k_max +
+              2 * sizeof(int2) * B_QC + sizeof(int) * (b->k_max + 2) + 16;
     BCU(cudaFuncSetAttribute(k_bscan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     BC(breset(b));
     BC(autotune(b));
@@ -1144,6 +1273,18 @@ knor_status knor_batch_get_instance(const knor_batch *bc, int32_t instance, knor
     out->iterations = it;
     out->converged = (it > 0 && ch == 0) ? 1 : 0;
     out->changed_last = ch;
+    return KNOR_OK;
+}
+
+knor_status knor_batch_get_work(const knor_batch *bc, int64_t *point_iterations, int64_t *scan_bytes) {
+    knor_batch *b = const_cast<knor_batch *>(bc);
+    if (!b) return KNOR_ERR_ARG;
+    b->err.clear();
+    unsigned long long w[2] = {0, 0};
+    BCUDA(b, cudaMemcpyAsync(w, b->work, sizeof(w), cudaMemcpyDeviceToHost, b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    if (point_iterations) *point_iterations = (int64_t)w[0];
+    if (scan_bytes) *scan_bytes = (int64_t)w[1];
     return KNOR_OK;
 }
 

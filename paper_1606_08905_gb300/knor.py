@@ -98,6 +98,8 @@ _SIGS = {
     "knor_batch_get_centroids_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "knor_batch_get_init_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "knor_batch_get_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(BatchInstance)]),
+    "knor_batch_get_work": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "knor_batch_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "knor_batch_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int32]),
     "knor_batch_kernel_name": (ctypes.c_char_p, [ctypes.c_void_p, ctypes.c_int32]),
@@ -378,6 +380,12 @@ class Batch:
         r = BatchInstance()
         _bcheck(load().knor_batch_get_instance(self._b, int(i), ctypes.byref(r)), self._b)
         return r.as_dict()
+
+    def work(self):
+        """(point-iterations, scan algorithmic bytes) since the last reset."""
+        pi, by = ctypes.c_int64(0), ctypes.c_int64(0)
+        _bcheck(load().knor_batch_get_work(self._b, ctypes.byref(pi), ctypes.byref(by)), self._b)
+        return int(pi.value), int(by.value)
 
     def set_profiling(self, on: bool):
         _bcheck(load().knor_batch_set_profiling(self._b, 1 if on else 0), self._b)

@@ -180,12 +180,16 @@ WORKLOADS = {
                             max_iters=50, prune=True),
     "precision_10m_d128_k1024": dict(kind="aniso", n=10_000_000, d=128, k=1024,
                                      data_seed=1003, max_iters=30, prune=False, precision="fp16"),
+    # 512 instances: n log-uniform in [1e3, 1e6], d in {8, 16, 32, 64}, k in
+    # {4..256}; n is the total over the instances (batched_specs(512, 1004))
+    "batched_512": dict(kind="batched", m=512, n=0, d=0, k=0, data_seed=1004, max_iters=25, prune=True),
     "scale_1b_d16_k100_uniform": dict(kind="uniform", n=1_000_000_000, d=16, k=100,
                                       data_seed=1005, max_iters=20, prune=True),
     "scale_1b_d16_k100_mixture": dict(kind="spd_scaled", n=1_000_000_000, d=16, k=100,
                                       data_seed=1006, max_iters=20, prune=True),
 }
 INIT_SEED = 42
+WORKLOADS["batched_512"]["n"] = sum(s.n for s in batched_specs(512, 1004))
 
 
 def make(kind: str, n: int, d: int, k: int, seed: int, device="cpu"):

@@ -74,6 +74,10 @@ def test_batch_matches_single_problem_contexts():
                 check_centroids(b.centroids(i), c.centroids(), f"instance {i}")
         assert done == max(b.instance(i)["iterations"] for i in range(len(Xs)))
         assert recs[-1]["changed"] == 0
+        pit, byts = b.work()
+        assert pit == sum(X.shape[0] * b.instance(i)["iterations"] for i, X in enumerate(Xs))
+        skipped = sum(r["clause1_skipped"] for r in recs)
+        assert byts >= 8 * pit and byts <= 8 * pit + (pit - skipped) * (4 * 64 + 8)
 
 
 def test_batch_pruned_equals_plain():
