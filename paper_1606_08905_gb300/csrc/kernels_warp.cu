@@ -120,6 +120,16 @@ __device__ __forceinline__ void warp_sort_by_cluster(int2 *q, int2 *tmp, int *hi
     __syncwarp();
 }
 
+// Warp w's accumulators: shared memory, or its slot of p.wacc.
+__device__ __forceinline__ float *warp_acc_hi(const IterParams &p, unsigned char *sm, int w) {
+    if (p.wacc) return p.wacc + ((size_t)blockIdx.x * WPC + w) * 2 * (size_t)p.k * p.d;
+    return reinterpret_cast<float *>(sm + p.w_base + w * p.w_stride + p.w_acc_hi);
+}
+__device__ __forceinline__ float *warp_acc_lo(const IterParams &p, unsigned char *sm, int w) {
+    if (p.wacc) return p.wacc + ((size_t)blockIdx.x * WPC + w) * 2 * (size_t)p.k * p.d + (size_t)p.k * p.d;
+    return reinterpret_cast<float *>(sm + p.w_base + w * p.w_stride + p.w_acc_lo);
+}
+
 // The CTA's partial slot: its warps' accumulators added in warp order.
 __device__ __forceinline__ void flush_warp_partials(const IterParams &p, unsigned char *sm) {
     const int kd = p.k * p.d;
@@ -127,9 +137,8 @@ __device__ __forceinline__ void flush_warp_partials(const IterParams &p, unsigne
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < WPC; ++w) {
-            const unsigned char *wr = sm + p.w_base + w * p.w_stride;
-            s += (double)reinterpret_cast<const float *>(wr + p.w_acc_hi)[e];
-            s += (double)reinterpret_cast<const float *>(wr + p.w_acc_lo)[e];
+            s += (double)warp_acc_hi(p, sm, w)[e];
+            s += (double)warp_acc_lo(p, sm, w)[e];
         }
         p.part_S[(size_t)e * p.part_stride + blockIdx.x] = s;
     }
@@ -268,16 +277,18 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
 // per lane (Clause 3 tightening, Clause 2 per centroid) and the rows that
 // changed cluster move between the warp's sums (read back from global
 // memory, where the scan has just loaded them).
+// d <= 32: 5 resident CTAs x 4 warps per SM (registers capped at 96, no
+// spills); wider points keep their registers
 template <int DV>
-__global__ void __launch_bounds__(WT) k_mti_w(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
-                                              int32_t *fresh) {
+__global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams p, const int32_t *mode_dense,
+                                                                int32_t *nslots, int32_t *fresh) {
     if (*mode_dense != 0) return;
     extern __shared__ __align__(16) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int k = p.k;
     unsigned char *wr = sm + p.w_base + w * p.w_stride;
-    float *acc_hi = reinterpret_cast<float *>(wr + p.w_acc_hi);
-    float *acc_lo = reinterpret_cast<float *>(wr + p.w_acc_lo);
+    float *acc_hi = warp_acc_hi(p, sm, w);
+    float *acc_lo = warp_acc_lo(p, sm, w);
     int *cnt = reinterpret_cast<int *>(wr + p.w_cnt);
     int2 *queue = reinterpret_cast<int2 *>(wr + p.w_queue);
     int2 *queue2 = queue + WQCAP;

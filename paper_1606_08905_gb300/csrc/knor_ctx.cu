@@ -130,6 +130,7 @@ struct knor_ctx {
     float *rm1 = nullptr, *rxn = nullptr;
     alignas(64) unsigned char tmXc[128] = {};
     PrecParams pp2{};
+    float *wacc = nullptr; // k_mti_w warp accumulators
     float *xn = nullptr, *cn = nullptr, *absmax = nullptr;
     PrecIter *pit = nullptr;
     int32_t fmt = PREC_FMT_BF16;
@@ -191,7 +192,7 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
-                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn};
+                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -302,8 +303,9 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
         woff = (woff + bytes + 15) & ~(size_t)15;
         return (int32_t)o;
     };
-    p.w_acc_hi = wtake(kd * 4);
-    p.w_acc_lo = wtake(kd * 4);
+    // the MTI kernel keeps its warps' accumulators in global memory
+    p.w_acc_hi = mti ? 0 : wtake(kd * 4);
+    p.w_acc_lo = mti ? 0 : wtake(kd * 4);
     p.w_cnt = wtake((size_t)k * 4);
     p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4); // dense: two row tiles
     p.sort_queue = (mti && k <= 1024) ? 1 : 0;
@@ -690,6 +692,11 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     KC(dalloc(c, &c->part_cnt, (size_t)k * c->part_stride));
     fill_common(c, c->ip_dense);
     fill_common(c, c->ip_mti);
+    if (c->ip_mti.warp_kernels) {
+        // per-warp TwoSum accumulators of k_mti_w (global, warp-private)
+        KC(dalloc(c, &c->wacc, (size_t)c->grid_mti * WPC * 2 * kd));
+        c->ip_mti.wacc = c->wacc;
+    }
     c->ip_dense.part_stride = c->part_stride;
     c->ip_mti.part_stride = c->part_stride;
     c->ip_dense.acc_global = c->ip_mti.acc_global = acc_global;

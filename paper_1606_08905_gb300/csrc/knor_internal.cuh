@@ -90,6 +90,11 @@ struct IterParams {
     int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_queue, w_state;
     int32_t sort_queue;    // k_mti_w: sort each warp's queue by cluster (k <= 1024)
     int32_t ubins;         // k_mti_w: bins of u / s(a) in the sort key (1 = by cluster only)
+    // k_mti_w: when non-null, each warp's TwoSum accumulators (hi then lo,
+    // k x d each) live in this global array, slot blockIdx.x * WPC + warp,
+    // instead of shared memory (few points change cluster in an MTI
+    // iteration; the freed shared memory holds more warps per SM)
+    float *wacc;
 };
 
 // Parameters of the reduction / finalize kernels.
