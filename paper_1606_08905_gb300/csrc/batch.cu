@@ -45,6 +45,11 @@ constexpr int BT = 256;            // threads of the scan CTA
 constexpr int B_KMAX = 256;        // largest k of an instance
 constexpr int B_PART_CAP = 2048;   // k x d up to which a unit sums in shared memory
 constexpr int B_QC = 1024;         // points per chunk of the pruned scan's queue
+// sort key of a queued point: (a + 1) * UB + bin of u / s(a) on a
+// quarter-octave scale -- points of one cluster with similar bounds keep
+// nearly the same Clause-2 candidates, so a warp's union stays small
+constexpr int B_UB_SMALLK = 8;     // bins when k <= 128
+constexpr int B_UB_LARGEK = 4;     // bins when k > 128
 
 struct BInst {
     int64_t n;      // points
@@ -65,7 +70,8 @@ struct BUnit {
 
 struct BCounters {
     unsigned long long changed, skipped, evals, empty;
-    unsigned long long bytes; // algorithmic bytes of the scan: 8 per point, + 4d + 8 per scanned point
+    unsigned long long bytes;  // algorithmic bytes of the scan: 8 per point, + 4d + 8 per scanned point
+    unsigned long long passed; // points Clause 1 cannot skip (counted in dense scans too)
 };
 
 struct BParams {
@@ -79,8 +85,10 @@ struct BParams {
     float *C32, *C32n;
     double *C64, *S, *D;
     long long *cnt, *Dcnt;
-    float *halfD, *s, *F;
+    float *halfD, *s, *F;     // halfD: per centroid a, 1/2 d(c_a, c) over c != a sorted ascending
+    int32_t *order;           // ... and the centroid c of each entry (row a of k entries, +inf padded)
     int32_t *active;          // per instance: still iterating
+    int32_t *dense;           // per instance: the next iteration scans every point
     int32_t *iters;           // per instance: iterations since reset
     long long *changed_last;  // per instance: changed count of its last iteration
     BCounters *bctr;          // per instance, this iteration
@@ -152,7 +160,8 @@ template <int DV>
 __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int64_t lo, int64_t hi,
                                           const float *cent, const float *s_s, const float *F_s, double *part,
                                           long long *pcnt, int2 *queue, int2 *sorted, int *hist, int *qn,
-                                          long long &changed, long long &skipped, long long &evals) {
+                                          bool dense, long long &changed, long long &skipped, long long &evals,
+                                          long long &passed) {
     const int k = I.k;
     const float *X = p.X + I.xoff;
     PtState *st = p.st + I.poff;
@@ -160,9 +169,17 @@ __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int6
     double *D = p.D + I.coff;
     long long *Dc = p.Dcnt + I.koff;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (!p.mti) {
+    if (!p.mti || dense) {
         for (int64_t i = lo + tid; i < hi; i += BT) {
-            const int a = st[i].a;
+            const PtState ps = st[i];
+            const int a = ps.a;
+            // Clause 1 is evaluated (not used): how many points an MTI scan
+            // would have to scan decides the instance's next mode
+            if (p.mti) {
+                bool pass = true;
+                if (a >= 0) pass = !(__fmaf_ru(__fadd_ru(ps.ub, F_s[a]), I.onepk, I.tau) < s_s[a]);
+                passed += pass ? 1 : 0;
+            }
             unsigned long long x[DV / 2];
             ldg_x2<DV>(x, X + i * DV);
             int best;
@@ -176,13 +193,15 @@ __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int6
     for (int64_t c0 = lo; c0 < hi; c0 += B_QC) {
         const int64_t c1 = min(hi, c0 + (int64_t)B_QC);
         // ---- Clause 1; survivors into the queue (warp-aggregated appends)
+        const int UB = k <= 128 ? B_UB_SMALLK : B_UB_LARGEK;
+        const int nkey = (k + 1) * UB;
         if (tid == 0) *qn = 0;
-        for (int c = tid; c <= k; c += BT) hist[c] = 0;
+        for (int c = tid; c < nkey; c += BT) hist[c] = 0;
         __syncthreads();
         for (int64_t base = c0; base < c1; base += BT) {
             const int64_t i = base + tid;
             bool act = false;
-            int a = -1;
+            int a = -1, key = 0;
             if (i < c1) {
                 const PtState ps = st[i];
                 a = ps.a;
@@ -190,6 +209,8 @@ __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int6
                 if (a >= 0) {
                     const float uu = __fadd_ru(ps.ub, F_s[a]);
                     act = !(__fmaf_ru(uu, I.onepk, I.tau) < s_s[a]);
+                    const float r = __fdividef(uu, fmaxf(s_s[a], 1e-30f));
+                    key = (a + 1) * UB + min(UB - 1, max(0, (int)(4.0f * __log2f(fmaxf(r, 1.0f)))));
                 }
                 if (!act) ++skipped;
             }
@@ -200,35 +221,36 @@ __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int6
                 pos = __shfl_sync(FULL_MASK, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
             }
             if (act) {
-                queue[pos] = make_int2((int)(i - c0), a);
-                atomicAdd(&hist[a + 1], 1); // key a + 1: a = -1 (no centroid yet) first
+                queue[pos] = make_int2((int)(i - c0), key); // key 0: no centroid yet
+                atomicAdd(&hist[key], 1);
             }
         }
         __syncthreads();
         const int n_act = *qn;
+        if (tid == 0) passed += n_act;
         if (n_act == 0) {
             __syncthreads();
             continue;
         }
-        // ---- counting sort by cluster
+        // ---- counting sort by key
         if (warp == 0) {
             int carry = 0;
-            for (int base = 0; base <= k; base += 32) {
+            for (int base = 0; base < nkey; base += 32) {
                 const int c = base + lane;
-                const int v = c <= k ? hist[c] : 0;
+                const int v = c < nkey ? hist[c] : 0;
                 int incl = v;
                 for (int o = 1; o < 32; o <<= 1) {
                     const int t = __shfl_up_sync(FULL_MASK, incl, o);
                     if (lane >= o) incl += t;
                 }
-                if (c <= k) hist[c] = carry + incl - v; // exclusive start
+                if (c < nkey) hist[c] = carry + incl - v; // exclusive start
                 carry += __shfl_sync(FULL_MASK, incl, 31);
             }
         }
         __syncthreads();
         for (int e = tid; e < n_act; e += BT) {
             const int2 q = queue[e];
-            sorted[atomicAdd(&hist[q.y + 1], 1)] = q;
+            sorted[atomicAdd(&hist[q.y], 1)] = make_int2(q.x, q.y == 0 ? -1 : q.y / UB - 1);
         }
         __syncthreads();
         // ---- pruned scans, 32 queued points per warp at a time
@@ -254,37 +276,23 @@ __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int6
                     evals += k;
                 }
             }
-            float test = 0.0f;
-            const float *hrow = halfD;
             if (has && a >= 0) {
                 bd = d2_reg<DV>(x, cent + (size_t)a * DV);
                 best = a;
                 ++evals;
-                test = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
-                hrow = halfD + (size_t)a * k;
-            }
-            const bool pruned_scan = has && a >= 0;
-            if (__any_sync(FULL_MASK, pruned_scan)) {
-                for (int wbase = 0; wbase < k; wbase += 32) {
-                    unsigned word = 0;
-                    if (pruned_scan) {
-                        const int lim = min(32, k - wbase);
-                        for (int b = 0; b < lim; ++b) {
-                            const int c = wbase + b;
-                            if (c != a && !(test < __ldg(hrow + c))) word |= 1u << b;
-                        }
-                    }
-                    unsigned uni = __reduce_or_sync(FULL_MASK, word);
-                    while (uni) {
-                        const int b = __ffs(uni) - 1;
-                        uni &= uni - 1;
-                        const int c = wbase + b;
-                        const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
-                        if ((word >> b) & 1u) {
-                            ++evals;
-                            if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
-                        }
-                    }
+                const float test = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
+                // Clause 2 over a's neighbours sorted by 1/2 d(c_a, c): the
+                // survivors are a prefix of the list, the scan stops at the
+                // first entry above the bound (the argmin with lowest-index
+                // ties does not depend on the evaluation order)
+                const float *hs = halfD + (size_t)a * k;
+                const int32_t *od = p.order + I.hoff + (size_t)a * k;
+                for (int j = 0; j < k - 1; ++j) {
+                    if (test < __ldg(hs + j)) break;
+                    const int c = __ldg(od + j);
+                    const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
+                    ++evals;
+                    if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
                 }
             }
             if (has && !p.dry) commit_point<DV>(I, st, i, a, best, bd, x, F_s, part, pcnt, D, Dc, changed);
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
     int2 *queue = reinterpret_cast<int2 *>(pcnt + p.k_max);
     int2 *sorted = queue + B_QC;
     int *hist = reinterpret_cast<int *>(sorted + B_QC);
-    int *qn = hist + p.k_max + 1;
+    int *qn = hist + (p.k_max + 1) * B_UB_SMALLK;
     const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) s_unit = (int)atomicAdd(p.qctr, 1u);
@@ -342,14 +350,15 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
             for (int c = tid; c < I.k; c += BT) pcnt[c] = 0;
         }
         __syncthreads();
-        long long ch = 0, sk = 0, ev = 0;
+        long long ch = 0, sk = 0, ev = 0, pa = 0;
+        const bool dense = p.mti && p.dense[U.inst];
         double *pp = use_part ? part : nullptr;
         long long *pc = use_part ? pcnt : nullptr;
         switch (I.d) {
-        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
-        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
-        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
-        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, ch, sk, ev); break;
+        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
+        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
+        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
+        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
         }
         __syncthreads();
         if (use_part) {
@@ -363,12 +372,14 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
         ch = block_sum(ch, red);
         sk = block_sum(sk, red);
         ev = block_sum(ev, red);
+        pa = block_sum(pa, red);
         if (tid == 0 && !p.dry) {
             BCounters *b = p.bctr + U.inst;
             const long long np = U.hi - U.lo;
             if (ch) atomicAdd(&b->changed, (unsigned long long)ch);
             if (sk) atomicAdd(&b->skipped, (unsigned long long)sk);
             if (ev) atomicAdd(&b->evals, (unsigned long long)ev);
+            if (pa) atomicAdd(&b->passed, (unsigned long long)pa);
             atomicAdd(&b->bytes, (unsigned long long)(8 * np + (np - sk) * (4LL * I.d + 8)));
         }
         __syncthreads();
@@ -429,9 +440,19 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
             pts += (unsigned long long)p.inst[i].n;
             by += b.bytes;
             if (b.changed == 0) p.active[i] = 0;
+            // next mode: after an MTI iteration in which Clause 1 let most
+            // points through and Clause 2 pruned little (at least 70 % of
+            // their k distances evaluated), scan every point once -- an MTI
+            // scan then costs more than the plain one; after a dense
+            // iteration, MTI again (its counters tell whether pruning pays)
+            const unsigned long long nk = (unsigned long long)p.inst[i].k;
+            p.dense[i] = (p.mti && !p.dense[i] && 2 * b.passed > (unsigned long long)p.inst[i].n &&
+                          10 * b.evals >= 7 * b.passed * nk)
+                             ? 1
+                             : 0;
         }
         any |= p.active[i];
-        p.bctr[i] = BCounters{0, 0, 0, 0, 0};
+        p.bctr[i] = BCounters{0, 0, 0, 0, 0, 0};
     }
     if (any) atomicOr(&any_s, 1);
     if (snapshot) {
@@ -489,29 +510,54 @@ __global__ void k_btable(const BParams p, int32_t need_table) {
     const int a = g - I.koff, k = I.k, d = I.d, tid = threadIdx.x;
     const float *Cn = p.C32n + I.coff;
     float *Co = p.C32 + I.coff;
-    __shared__ float redf[128];
+    __shared__ float hv[B_KMAX];
+    __shared__ int cv[B_KMAX];
     if (need_table) {
         if (tid == 0) {
             const float d2 = d2_gen(Cn + (size_t)a * d, Co + (size_t)a * d, d);
             p.F[g] = __fadd_ru(p.F[g], bound_up(d2, I.g_up, I.tiny));
         }
-        float mymin = CUDART_INF_F;
-        float *hrow = p.halfD + I.hoff + (size_t)a * k;
-        for (int c = tid; c < k; c += blockDim.x) {
-            if (c == a) { hrow[c] = 0.0f; continue; }
-            const float d2 = d2_gen(Cn + (size_t)a * d, Cn + (size_t)c * d, d);
-            const float lo2 = fmaxf(__fdiv_rd(__fsub_rd(d2, I.tiny), I.g_up), 0.0f);
-            const float h = __fmul_rd(0.5f, __fsqrt_rd(lo2));
-            hrow[c] = h;
-            mymin = fminf(mymin, h);
+        // 1/2 d(c_a, c) for c != a, then the row sorted ascending (bitonic,
+        // 256 entries, +inf padded) with its centroid indices; s(a) is the
+        // first entry
+        for (int j = tid; j < B_KMAX; j += blockDim.x) {
+            float h = CUDART_INF_F;
+            int c = a;
+            if (j < k - 1) {
+                c = j < a ? j : j + 1;
+                const float d2 = d2_gen(Cn + (size_t)a * d, Cn + (size_t)c * d, d);
+                const float lo2 = fmaxf(__fdiv_rd(__fsub_rd(d2, I.tiny), I.g_up), 0.0f);
+                h = __fmul_rd(0.5f, __fsqrt_rd(lo2));
+            }
+            hv[j] = h;
+            cv[j] = c;
         }
-        redf[tid] = mymin;
+        for (int size = 2; size <= B_KMAX; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                __syncthreads();
+                for (int t = tid; t < B_KMAX / 2; t += blockDim.x) {
+                    const int lo = 2 * t - (t & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const float x = hv[lo], y = hv[hi];
+                    if ((x > y) == up) {
+                        hv[lo] = y;
+                        hv[hi] = x;
+                        const int ci = cv[lo];
+                        cv[lo] = cv[hi];
+                        cv[hi] = ci;
+                    }
+                }
+            }
+        }
         __syncthreads();
-        if (tid == 0) {
-            float mn = CUDART_INF_F;
-            for (int q = 0; q < (int)blockDim.x; ++q) mn = fminf(mn, redf[q]);
-            p.s[g] = mn;
+        float *hrow = p.halfD + I.hoff + (size_t)a * k;
+        int32_t *orow = p.order + I.hoff + (size_t)a * k;
+        for (int j = tid; j < k; j += blockDim.x) {
+            hrow[j] = hv[j];
+            orow[j] = cv[j];
         }
+        if (tid == 0) p.s[g] = hv[0];
         __syncthreads();
     }
     for (int j = tid; j < d; j += blockDim.x) Co[(size_t)a * d + j] = Cn[(size_t)a * d + j];
@@ -566,6 +612,7 @@ struct knor_batch {
     int64_t total_n = 0, total_x = 0, total_c = 0, total_h = 0;
     int32_t total_k = 0, kd_max = 0, k_max = 0;
     float *X = nullptr, *C32 = nullptr, *C32n = nullptr, *halfD = nullptr, *s = nullptr, *F = nullptr;
+    int32_t *order = nullptr;
     PtState *st = nullptr;
     double *C0 = nullptr, *C64 = nullptr, *S = nullptr, *D = nullptr;
     long long *cnt = nullptr, *Dcnt = nullptr, *changed_last = nullptr;
@@ -573,7 +620,7 @@ struct knor_batch {
     BUnit *units = nullptr;
     int32_t nunits = 0;
     unsigned *qctr = nullptr;
-    int32_t *active = nullptr, *iters = nullptr, *cinst = nullptr, *flags = nullptr;
+    int32_t *active = nullptr, *iters = nullptr, *cinst = nullptr, *flags = nullptr, *dense = nullptr;
     BCounters *bctr = nullptr;
     unsigned long long *work = nullptr;
     IterStats *stats = nullptr;
@@ -616,7 +663,7 @@ knor_status balloc(knor_batch *b, T **p, size_t count) {
 void bfree_all(knor_batch *b) {
     void *bufs[] = {b->X,    b->C32,   b->C32n, b->halfD, b->s,      b->F,     b->st,     b->C0,
                     b->C64,  b->S,     b->D,    b->cnt,   b->Dcnt,   b->changed_last, b->inst, b->units,
-                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx, b->work};
+                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx, b->work, b->dense, b->order};
     for (void *p : bufs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : b->ev)
@@ -643,9 +690,11 @@ BParams params_of(const knor_batch *b, int dry, unsigned long long cond, const B
     p.cnt = b->cnt;
     p.Dcnt = b->Dcnt;
     p.halfD = b->halfD;
+    p.order = b->order;
     p.s = b->s;
     p.F = b->F;
     p.active = b->active;
+    p.dense = b->dense;
     p.iters = b->iters;
     p.changed_last = b->changed_last;
     p.bctr = b->bctr;
@@ -773,6 +822,7 @@ knor_status breset(knor_batch *b) {
     BCUDA(b, cudaMemsetAsync(b->bctr, 0, (size_t)b->m * sizeof(BCounters), s));
     BCUDA(b, cudaMemsetAsync(b->work, 0, 2 * sizeof(unsigned long long), s));
     BCUDA(b, cudaMemsetAsync(b->iters, 0, (size_t)b->m * sizeof(int32_t), s));
+    BCUDA(b, cudaMemsetAsync(b->dense, 0, (size_t)b->m * sizeof(int32_t), s));
     BCUDA(b, cudaMemsetAsync(b->changed_last, 0, (size_t)b->m * sizeof(long long), s));
     std::vector<int32_t> ones((size_t)b->m, 1);
     BCUDA(b, cudaMemcpyAsync(b->active, ones.data(), ones.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -1059,6 +1109,7 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     BC(balloc(b, &b->C32, tc));
     BC(balloc(b, &b->C32n, tc));
     BC(balloc(b, &b->halfD, (size_t)b->total_h));
+    BC(balloc(b, &b->order, (size_t)b->total_h));
     BC(balloc(b, &b->s, tk));
     BC(balloc(b, &b->F, tk));
     BC(balloc(b, &b->cnt, tk));
@@ -1066,6 +1117,7 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     BC(balloc(b, &b->cinst, tk));
     BC(balloc(b, &b->inst, (size_t)m));
     BC(balloc(b, &b->active, (size_t)m));
+    BC(balloc(b, &b->dense, (size_t)m));
     BC(balloc(b, &b->iters, (size_t)m));
     BC(balloc(b, &b->changed_last, (size_t)m));
     BC(balloc(b, &b->bctr, (size_t)m));
@@ -1109,7 +1161,7 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     // scan launch shape
     b->smem = sizeof(float) * ((size_t)b->kd_max + 2 * b->k_max + 1) +
               sizeof(double) * (size_t)std::min(b->kd_max, B_PART_CAP) + sizeof(long long) * b->k_max +
-              2 * sizeof(int2) * B_QC + sizeof(int) * (b->k_max + 2) + 16;
+              2 * sizeof(int2) * B_QC + sizeof(int) * ((b->k_max + 1) * B_UB_SMALLK + 1) + 16;
     BCU(cudaFuncSetAttribute(k_bscan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     BC(breset(b));
     BC(autotune(b));
