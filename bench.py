@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=0, help="override the workload's n (profiling runs)")
+    ap.add_argument("--m", type=int, default=0, help="override the batched workload's instance count "
+                                                      "(profiling runs)")
     ap.add_argument("--precision", default="", choices=["", "bf16", "fp16"],
                     help="override the tensor-core operand format of a precision workload")
     return ap.parse_args()
@@ -125,12 +127,21 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def csrc_sha256() -> str:
-    """Hash of every CUDA source and header of the library."""
+KERNEL_SOURCES = {  # CUDA sources that define each profiled kernel
+    "k_mti_w": "kernels_warp.cu", "k_dense_w": "kernels_warp.cu", "k_mti": "kernels.cu", "k_dense": "kernels.cu",
+    "k_tc_assign": "precision.cu", "k_bscan": "batch.cu",
+}
+
+
+def csrc_sha256(kernel: str = "") -> str:
+    """Hash of the CUDA sources of `kernel` (its file plus the shared
+    headers), or of every CUDA source when kernel is empty."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1606_08905_gb300", "csrc")
+    base = re.sub(r"<.*", "", kernel)
+    want = {KERNEL_SOURCES[base], "device_common.cuh", "knor_internal.cuh"} if base in KERNEL_SOURCES else None
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) and (want is None or f in want):
             h.update(f.encode())
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()
@@ -138,8 +149,8 @@ def csrc_sha256() -> str:
 
 def ncu_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes of `kernel` (scaled to this workload) from the
-    committed ncu summary profiles/<kernel>_<workload>.md, if the CUDA sources
-    have not changed since the capture (else None)."""
+    committed ncu summary profiles/<kernel>_<workload>.md, if the kernel's
+    CUDA sources have not changed since the capture (else None)."""
     base = re.sub(r"[<>]", "", kernel)
     path = os.path.join(ROOT, "profiles", f"{base}_{workload}.md")
     if not os.path.exists(path):
@@ -147,7 +158,7 @@ def ncu_traffic(kernel: str, workload: str):
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"csrc_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h or h.group(1) != csrc_sha256():
+    if not m or not h or h.group(1) != csrc_sha256(kernel):
         return None
     return float(m.group(1))
 
@@ -444,7 +455,8 @@ def batch_bytes(wl):
 
 def config_of(wl, name, world):
     if wl["kind"] == "batched":
-        return {"workload": name, "instances": wl["m"], "total_points": wl["n"],
+        return {"workload": name if wl["n"] == synth_n(name) else f"{name} (m overridden)",
+                "instances": wl["m"], "total_points": wl["n"],
                 "n_i": "log-uniform in [1e3, 1e6]", "d_i": "uniform over {8, 16, 32, 64}",
                 "k_i": "uniform on {4..256}", "max_iters": wl["max_iters"],
                 "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42 + instance",
@@ -550,7 +562,8 @@ def our_arm(args, wl, world, rank, local):
         roof = {"kernel": ctx.kernel_name("dense"), "bound": "tensor", "achieved": tf,
                 "peak": peaks["bf16_tflops_sustained"], "peak_source": peak_src + " (bf16 sustained)",
                 "unit": "TFLOP/s", "frac": tf / peaks["bf16_tflops_sustained"],
-                "traffic": None, "share_of_kernel_time": ms_k / total_prof_ms,
+                "traffic": ncu_traffic(ctx.kernel_name("dense"), args.workload) if not args.n else None,
+                "share_of_kernel_time": ms_k / total_prof_ms,
                 "rechecked_fraction": rechecked / float(n * max(1, len(prof_recs))),
                 "fp32_evals_per_rechecked_point":
                     (sum(r["dist_evals"] for r in prof_recs) - n * k * len(prof_recs)) / float(max(1, rechecked))}
@@ -668,6 +681,9 @@ def main():
         wl["n"] = args.n
     if args.precision and wl.get("precision", "fp32") != "fp32":
         wl["precision"] = args.precision
+    if args.m and wl["kind"] == "batched":
+        wl["m"] = args.m
+        wl["n"] = sum(sp.n for sp in synth.batched_specs(args.m, wl["data_seed"]))
     if args.impl == "reference":
         (batch_reference_arm if wl["kind"] == "batched" else reference_arm)(args, wl, world, rank)
         return
