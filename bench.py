@@ -151,7 +151,7 @@ def ncu_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes of `kernel` (scaled to this workload) from the
     committed ncu summary profiles/<kernel>_<workload>.md, if the kernel's
     CUDA sources have not changed since the capture (else None)."""
-    base = re.sub(r"[<>]", "", kernel)
+    base = re.sub(r"<.*", "", kernel)
     path = os.path.join(ROOT, "profiles", f"{base}_{workload}.md")
     if not os.path.exists(path):
         return None
