@@ -57,7 +57,8 @@ typedef enum {
 typedef enum {
     KNOR_PREC_FP32 = 0, /* FP32 distances, direct form sum_i (x_i - c_i)^2 */
     KNOR_PREC_BF16 = 1, /* tensor-core BF16 distance block + exact FP32 recheck */
-    KNOR_PREC_FP8 = 2,  /* tensor-core FP8 e4m3 with per-dimension scales + recheck */
+    KNOR_PREC_FP8 = 2,  /* tensor-core FP8 e4m3 (power-of-two per-dimension scales,
+                           x_j / sigma_j and c_j sigma_j) + exact FP32 recheck; d = 128 */
     KNOR_PREC_FP16 = 3  /* tensor-core FP16 distance block (points and centroids
                            scaled by powers of two into range) + exact FP32 recheck */
 } knor_precision;
@@ -65,8 +66,9 @@ typedef enum {
  * a point whose two smallest approximate distances are further apart than
  * twice a proven bound on their error keeps the approximate argmin, every
  * other point is re-scored in FP32 over the centroids that can still be
- * nearest.  They need d = 64 or 128; k is limited by shared memory (8192 at
- * d = 128).  They never prune (every point is scanned each iteration). */
+ * nearest.  They need d = 64 or 128 (FP8: 128); k is limited by shared memory
+ * (8192 at d = 128).  They never prune (every point is scanned each
+ * iteration). */
 
 /* Options.  A zero-initialised struct gives the defaults: MTI pruning on,
  * FP32 distances, sums maintained by deltas, no debug checks. */

@@ -131,6 +131,8 @@ struct knor_ctx {
     alignas(64) unsigned char tmXc[128] = {};
     PrecParams pp2{};
     float *wacc = nullptr; // k_mti_w warp accumulators
+    float *xdn = nullptr, *rxdn = nullptr; // FP8: norms of x / sigma (else aliases of xn, rxn)
+    float *sigma = nullptr;                // FP8: sigma_j, then 1 / sigma_j (d each)
     float *xn = nullptr, *cn = nullptr, *absmax = nullptr;
     PrecIter *pit = nullptr;
     int32_t fmt = PREC_FMT_BF16;
@@ -192,7 +194,8 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
-                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc};
+                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma,
+                    c->xdn != c->xn ? c->xdn : nullptr, c->rxdn != c->rxn ? c->rxdn : nullptr};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -201,8 +204,8 @@ static void free_all(knor_ctx *c) {
 
 // A 2-D TMA descriptor over a row-major rows x inner BF16 matrix, boxes of
 // 64 columns (128 bytes) x box_rows rows, 128-byte swizzle, zero fill outside.
-// TMA map of a row-major matrix of 16-bit operands (rows x inner), 64-element
-// (128-byte) boxes of box_rows rows, 128-byte swizzle.
+// TMA map of a row-major matrix of operands (rows x inner; 16-bit or FP8),
+// 128-byte-wide boxes of box_rows rows, 128-byte swizzle.
 static knor_status encode_op_map(knor_ctx *c, void *out, void *base, uint64_t inner, uint64_t rows,
                                  uint32_t box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -214,12 +217,14 @@ static knor_status encode_op_map(knor_ctx *c, void *out, void *base, uint64_t in
             return fail(c, KNOR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
     }
+    const int esize = c->fmt == PREC_FMT_FP8 ? 1 : 2;
     cuuint64_t dims[2] = {inner, rows};
-    cuuint64_t strides[1] = {inner * 2};
-    cuuint32_t box[2] = {64, box_rows};
+    cuuint64_t strides[1] = {inner * esize};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esize), box_rows}; // 128-byte rows
     cuuint32_t es[2] = {1, 1};
-    const CUtensorMapDataType dt =
-        c->fmt == PREC_FMT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = c->fmt == PREC_FMT_FP8    ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : c->fmt == PREC_FMT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = fn(static_cast<CUtensorMap *>(out), dt, 2, base, dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -376,13 +381,14 @@ static knor_status enqueue_prec(knor_ctx *c, cudaStream_t s, unsigned long long 
     // marks one that did not (k_delta_sums counts it as a violation)
     KNOR_CUDA(c, cudaMemsetAsync(c->a_next, 0xFF, sizeof(int32_t) * (size_t)c->n, s));
     KNOR_CUDA(c, mark(0));
-    KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->fmt, c->sx, c->Cb, c->cn, c->pit, s));
+    KNOR_CUDA(c, prec_prep(c->C32, c->k, c->d, c->fmt, c->sx, c->sigma, c->Cb, c->cn, c->pit, s));
     KNOR_CUDA(c, prec_assign(c->tmX, c->tmC, c->pp, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, mark(1));
     // the points left uncertified: candidate pass over their gathered rows,
     // then the exact FP32 re-score
     KNOR_CUDA(c, mark(8));
-    KNOR_CUDA(c, prec_gather(c->dv, c->Xb, c->xn, c->rlist, c->rcount, c->Xc, c->rxn, 8 * c->num_sms, s));
+    KNOR_CUDA(c, prec_gather(c->d * (c->fmt == PREC_FMT_FP8 ? 1 : 2), c->Xb, c->xn, c->xdn, c->rlist, c->rcount,
+                             c->Xc, c->rxn, c->rxdn, 8 * c->num_sms, s));
     KNOR_CUDA(c, prec_assign(c->tmXc, c->tmC, c->pp2, c->prec_grid, c->prec_smem, s));
     KNOR_CUDA(c, prec_recheck(c->dv, c->X, c->C32, c->k, c->rlist, c->rcand, c->rcount, c->a_next, c->ctr,
                               4 * c->num_sms, s));
@@ -601,14 +607,14 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     if (init != KNOR_INIT_FORGY && init != KNOR_INIT_EXPLICIT) { g_create_err = "knor_create: bad init"; return KNOR_ERR_ARG; }
     knor_opts o{};
     if (opts) o = *opts;
-    if (o.precision != KNOR_PREC_FP32 && o.precision != KNOR_PREC_BF16 && o.precision != KNOR_PREC_FP16) {
-        g_create_err = "knor_create: precision must be KNOR_PREC_FP32, KNOR_PREC_BF16 or KNOR_PREC_FP16 "
-                       "(the FP8 variant is not built)";
+    if (o.precision != KNOR_PREC_FP32 && o.precision != KNOR_PREC_BF16 && o.precision != KNOR_PREC_FP16 &&
+        o.precision != KNOR_PREC_FP8) {
+        g_create_err = "knor_create: precision must be one of KNOR_PREC_FP32, _BF16, _FP16, _FP8";
         return KNOR_ERR_ARG;
     }
-    const bool tc_form = o.precision == KNOR_PREC_BF16 || o.precision == KNOR_PREC_FP16;
-    if (tc_form && ((d != 64 && d != 128) || k > 8192)) {
-        g_create_err = "knor_create: the tensor-core forms need d = 64 or 128 and k <= 8192";
+    const bool tc_form = o.precision != KNOR_PREC_FP32;
+    if (tc_form && ((d != 64 && d != 128) || k > 8192 || (o.precision == KNOR_PREC_FP8 && d != 128))) {
+        g_create_err = "knor_create: the tensor-core forms need d = 64 or 128 (FP8: 128) and k <= 8192";
         return KNOR_ERR_ARG;
     }
     if (o.full_recompute_every < 0) { g_create_err = "knor_create: full_recompute_every < 0"; return KNOR_ERR_ARG; }
@@ -720,8 +726,12 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         // its sums move by deltas through partial slot 0.
         c->prec = true;
         c->opts.no_prune = 1;
-        KC(dalloc(c, (uint16_t **)&c->Xb, nd));
-        KC(dalloc(c, (uint16_t **)&c->Cb, kd));
+        c->fmt = o.precision == KNOR_PREC_FP16 ? PREC_FMT_FP16
+                 : o.precision == KNOR_PREC_FP8 ? PREC_FMT_FP8
+                                                : PREC_FMT_BF16;
+        const size_t esize = c->fmt == PREC_FMT_FP8 ? 1 : 2;
+        KC(dalloc(c, (uint8_t **)&c->Xb, nd * esize));
+        KC(dalloc(c, (uint8_t **)&c->Cb, kd * esize));
         KC(dalloc(c, &c->xn, (size_t)n));
         KC(dalloc(c, &c->cn, (size_t)k));
         KC(dalloc(c, &c->pit, 1));
@@ -729,11 +739,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, &c->a_next, (size_t)n));
         KC(dalloc(c, &c->rlist, (size_t)n));
         KC(dalloc(c, &c->rcand, (size_t)n * PREC_CANDS));
-        KC(dalloc(c, (uint16_t **)&c->Xc, nd));
+        KC(dalloc(c, (uint8_t **)&c->Xc, nd * esize));
         KC(dalloc(c, &c->rm1, (size_t)n));
         KC(dalloc(c, &c->rxn, (size_t)n));
         KC(dalloc(c, &c->rcount, 1));
-        c->fmt = o.precision == KNOR_PREC_FP16 ? PREC_FMT_FP16 : PREC_FMT_BF16;
         int ex = 0;
         if (c->fmt == PREC_FMT_FP16) {
             // point scale 2^ex from the largest |x_j| (read back once)
@@ -743,12 +752,39 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
             KCU(cudaStreamSynchronize(c->stream));
             ex = prec_point_scale_exp(c->fmt, am);
         }
+        c->xdn = c->xn;
+        c->rxdn = c->rxn;
+        if (c->fmt == PREC_FMT_FP8) {
+            // per-dimension scales sigma_j = 2^ceil(log2 max_i |x_ij|) (so
+            // |x_ij / sigma_j| <= 1), the points' scale 2^7, and the norms of
+            // x / sigma for the bound
+            KC(dalloc(c, &c->xdn, (size_t)n));
+            KC(dalloc(c, &c->rxdn, (size_t)n));
+            KC(dalloc(c, &c->sigma, (size_t)2 * d));
+            std::vector<float> mx((size_t)d), sg((size_t)2 * d);
+            KCU(prec_dim_absmax(c->X, n, d, c->sigma, c->stream));
+            KCU(cudaMemcpyAsync(mx.data(), c->sigma, sizeof(float) * d, cudaMemcpyDeviceToHost, c->stream));
+            KCU(cudaStreamSynchronize(c->stream));
+            for (int j = 0; j < d; ++j) {
+                int e = 0;
+                if (mx[(size_t)j] > 0.0f) {
+                    const float m = std::frexp(mx[(size_t)j], &e); // mx = m 2^e, m in [0.5, 1)
+                    if (m == 0.5f) e -= 1;                          // e = ceil(log2 mx)
+                }
+                e = std::max(-60, std::min(60, e));
+                sg[(size_t)j] = std::ldexp(1.0f, e);          // sigma_j
+                sg[(size_t)d + j] = std::ldexp(1.0f, -e);     // 1 / sigma_j
+            }
+            KCU(cudaMemcpyAsync(c->sigma, sg.data(), sizeof(float) * 2 * d, cudaMemcpyHostToDevice, c->stream));
+            ex = prec_point_scale_exp(c->fmt, 1.0f);
+        }
         c->sx = std::ldexp(1.0f, ex);
-        KCU(prec_points(c->X, n, d, c->fmt, c->sx, c->Xb, c->xn, c->stream));
+        KCU(prec_points(c->X, n, d, c->fmt, c->sx, c->sigma ? c->sigma + d : nullptr, c->Xb, c->xn, c->xdn,
+                        c->stream));
         KC(encode_op_map(c, c->tmX, c->Xb, (uint64_t)d, (uint64_t)n, 128));
         KC(encode_op_map(c, c->tmC, c->Cb, (uint64_t)d, (uint64_t)k, 256));
         KC(encode_op_map(c, c->tmXc, c->Xc, (uint64_t)d, (uint64_t)n, 128));
-        c->prec_smem = prec_smem_bytes(d, k);
+        c->prec_smem = prec_smem_bytes(d, k, (int)esize);
         int smem_optin = 0;
         KCU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
         if (c->prec_smem > (size_t)smem_optin) {
@@ -762,6 +798,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         pp.n = n; pp.d = d; pp.k = k; pp.xn = c->xn; pp.cn = c->cn; pp.it = c->pit;
         pp.a_next = c->a_next; pp.rlist = c->rlist; pp.rcount = c->rcount; pp.rcand = c->rcand;
         pp.rm1 = c->rm1; pp.rxn = c->rxn; pp.mode = 0;
+        pp.xdn = c->xdn; pp.rxdn = c->rxdn;
         prec_error_constants(c->fmt, d, c->sx, pp);
         pp.err = c->flags + F_ERR;
         c->pp2 = pp;

@@ -128,19 +128,25 @@ constexpr int PREC_CANDS = 16;
 // before the tensor-core scan: norms and the centroid scale.
 struct PrecIter {
     float cnorm_max; // max ||c|| rounded up (atomicMax on the bits)
-    float cabs_max;  // max |c_j| (atomicMax on the bits)
+    float cabs_max;  // max |c_j sigma_j| (atomicMax on the bits)
+    float cdnorm_max; // max ||c . sigma|| rounded up (FP8: per-dimension scales; else = cnorm_max)
     float neg2inv;   // -2 / (s_x s_c): a power of two
     float eta_c;     // sqrt(d) * (absolute rounding error of a scaled coordinate) / s_c, rounded up
 };
 
 // Operand format of the precision form's tensor-core scan.
-enum PrecFormat : int32_t { PREC_FMT_BF16 = 0, PREC_FMT_FP16 = 1 };
+enum PrecFormat : int32_t { PREC_FMT_BF16 = 0, PREC_FMT_FP16 = 1, PREC_FMT_FP8 = 2 };
 
 // Parameters of the precision-form assignment (precision.cu).
 struct PrecParams {
     int64_t n;
     int32_t d, k;
     const float *xn;     // n: ||x||^2 (FP64 sum rounded to FP32)
+    const float *xdn;    // n: ||x / sigma||^2 (FP8: per-dimension scales; else = xn)
+    const float *rxdn;   // mode 1: the same for the gathered points
+    int32_t fp8;         // operands are FP8 e4m3 (kind::f8f6f4), else 16-bit (kind::f16)
+    int32_t nkc;         // 128-byte K chunks per row (d x operand bytes / 128)
+    int32_t tkb;         // operand elements per 128-byte chunk
     const float *cn;     // k: ||c||^2
     const PrecIter *it;  // this iteration's centroid quantities
     int32_t *a_next;     // n: new assignment of certified points
@@ -196,12 +202,13 @@ std::vector<int64_t> forgy_indices(int64_t n, int32_t k, uint64_t seed);
 float f32_up(double v); // smallest float >= v
 
 // precision form (precision.cu)
-size_t prec_smem_bytes(int d, int k);
+size_t prec_smem_bytes(int d, int k, int esize);
 cudaError_t prec_absmax(const float *X, int64_t count, float *out, cudaStream_t s);
-cudaError_t prec_points(const float *X, int64_t n, int32_t d, int32_t fmt, float sx, void *Xb, float *xn,
-                        cudaStream_t s);
-cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, int32_t fmt, float sx, void *Cb, float *cn,
-                      PrecIter *it, cudaStream_t s);
+cudaError_t prec_dim_absmax(const float *X, int64_t n, int32_t d, float *out, cudaStream_t s);
+cudaError_t prec_points(const float *X, int64_t n, int32_t d, int32_t fmt, float sx, const float *sigma_inv,
+                        void *Xb, float *xn, float *xdn, cudaStream_t s);
+cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, int32_t fmt, float sx, const float *sigma, void *Cb,
+                      float *cn, PrecIter *it, cudaStream_t s);
 int prec_point_scale_exp(int32_t fmt, float absmax); // s_x = 2^this
 cudaError_t prec_assign_attr(size_t smem);
 // tmX / tmC point to CUtensorMap objects (cuda.h) over the BF16 points / centroids
@@ -210,8 +217,8 @@ void prec_error_constants(int32_t fmt, int d, float sx, PrecParams &p);
 cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, const int32_t *rlist,
                          const int32_t *rcand, const unsigned *rcount, int32_t *a_next, Counters *ctr, int grid,
                          cudaStream_t s);
-cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
-                        void *Xc, float *rxn, int grid, cudaStream_t s);
+cudaError_t prec_gather(int row_bytes, const void *Xb, const float *xn, const float *xdn, const int32_t *rlist,
+                        const unsigned *rcount, void *Xc, float *rxn, float *rxdn, int grid, cudaStream_t s);
 cudaError_t prec_verify(const float *X, int64_t n, int32_t d, const float *C32, int32_t k, const int32_t *a_next,
                         unsigned long long *viol, cudaStream_t s);
 cudaError_t prec_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, const int32_t *a_next, double *S,

@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <cmath>
 
@@ -101,11 +102,20 @@ __host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t ab_f
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
+// kind::f8f6f4 uses the same fields; A and B format 0 = E4M3.
+__host__ __device__ constexpr uint32_t idesc_f8kind(int M, int N) { return idesc_f16kind(M, N, 0u); }
 
 __device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_f8kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
                  "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
                  : "memory");
 }
@@ -157,16 +167,19 @@ __device__ __forceinline__ void top2_merge(float &m1, float &m2, int &i1, float 
     if (b1 < m1) { m1 = b1; i1 = bi; }
 }
 
-// 2E(x) for a point with ||x||^2 = xn (see prec_error_constants), every
-// operation rounded up.  C bounds ||c||, zeta bounds ||c~ - c|| (c~ the scaled
-// and rounded centroid, unscaled), Cz = C + zeta.
-__device__ __forceinline__ float prec_two_e(float xn, float C, float zeta, float Cz, const PrecParams &p) {
+// 2E(x) for a point with ||x||^2 = xn and, in the space the operands are
+// rounded in (FP8: x / sigma and c . sigma, per-dimension scales; else x and
+// c), ||x'||^2 = xdn (see prec_error_constants); every operation rounded up.
+// C bounds ||c||, Cd bounds ||c'||, zeta bounds ||c~' - c'||, Czd = Cd + zeta.
+__device__ __forceinline__ float prec_two_e(float xn, float xdn, float C, float Cd, float zeta, float Czd,
+                                            const PrecParams &p) {
     const float X = __fsqrt_ru(__fmul_ru(fmaxf(xn, 0.0f), 1.0000005f)); // covers the rounding of xn
-    const float xi = __fmaf_ru(p.uq, X, p.eta_x);                       // bound on ||x~ - x||
-    const float Xx = __fadd_ru(X, xi);
-    // |x.c - acc| <= ||x|| zeta + xi (C + zeta) + g_tc (X + xi)(C + zeta)
-    const float etc = __fmaf_ru(X, zeta, __fmaf_ru(xi, Cz, __fmul_ru(p.gtc, __fmul_ru(Xx, Cz))));
-    const float e32 = __fmaf_ru(p.eA32, __fmul_ru(Xx, Cz), __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C))));
+    const float Xd = __fsqrt_ru(__fmul_ru(fmaxf(xdn, 0.0f), 1.0000005f));
+    const float xi = __fmaf_ru(p.uq, Xd, p.eta_x);                       // bound on ||x~' - x'||
+    const float Xx = __fadd_ru(Xd, xi);
+    // |x'.c' - acc| <= ||x'|| zeta + xi (C' + zeta) + g_tc (X' + xi)(C' + zeta)
+    const float etc = __fmaf_ru(Xd, zeta, __fmaf_ru(xi, Czd, __fmul_ru(p.gtc, __fmul_ru(Xx, Czd))));
+    const float e32 = __fmaf_ru(p.eA32, __fmul_ru(Xx, Czd), __fmul_ru(p.eB, __fmaf_ru(X, X, __fmul_ru(C, C))));
     return __fmul_ru(2.0f, __fmaf_ru(2.02f, etc, e32));
 }
 
@@ -174,7 +187,7 @@ __device__ __forceinline__ float prec_two_e(float xn, float C, float zeta, float
 
 constexpr int TM = 128;              // points per tile (MMA M)
 constexpr int TN = 256;              // centroids per chunk (MMA N)
-constexpr int TKB = 64;              // BF16 elements per 128-byte row of a TMA box
+// a TMA box row is 128 bytes: 64 16-bit or 128 FP8 elements (PrecParams tkb)
 constexpr int A_BOX = TM * 128;      // bytes of one A box (16 KB)
 constexpr int B_BOX = TN * 128;      // bytes of one B box (32 KB)
 constexpr int EPI_WARPS = 8;         // two epilogue warps per TMEM lane quarter
@@ -183,8 +196,8 @@ constexpr int HALF = TN / 2;         // columns of each chunk read by one epilog
 constexpr int TMEM_COLS = 2 * TN;    // two accumulator buffers
 constexpr int NBARS = 21;            // mbarriers, see the kernel
 
-size_t prec_smem_bytes(int d, int k) {
-    const int nkc = d / TKB;
+size_t prec_smem_bytes(int d, int k, int esize) {
+    const int nkc = d * esize / 128;
     const size_t kpad = (size_t)(k + TN - 1) / TN * TN;
     return 1024 /* alignment */ + 2 * (size_t)nkc * A_BOX + 2 * (size_t)nkc * B_BOX + kpad * 4 +
            3 * TM * 4 /* pair hand-off */ + NBARS * 8 + 16;
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int nkc = p.d / TKB;
+    const int nkc = p.nkc;
     unsigned char *sA = sm;                                  // [2][nkc][A_BOX]
     unsigned char *sB = sA + 2 * (size_t)nkc * A_BOX;        // [2][nkc][B_BOX]
     const int nchunk = (p.k + TN - 1) / TN;
@@ -262,7 +275,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                 if ((ia >> 1) >= 1 && !mbar_wait(&emptyA[sa], ((ia >> 1) - 1) & 1, p.err)) break;
                 mbar_expect_tx(&fullA[sa], (uint32_t)(nkc * A_BOX));
                 for (int kc = 0; kc < nkc; ++kc)
-                    tma_load_2d(sA + ((size_t)sa * nkc + kc) * A_BOX, &tmX, kc * TKB, (int)(t * TM), &fullA[sa]);
+                    tma_load_2d(sA + ((size_t)sa * nkc + kc) * A_BOX, &tmX, kc * p.tkb, (int)(t * TM), &fullA[sa]);
                 ++ia;
                 bool ok = true;
                 for (int j = 0; j < nchunk; ++j) {
@@ -270,7 +283,7 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                     if ((ib >> 1) >= 1 && !mbar_wait(&emptyB[sb], ((ib >> 1) - 1) & 1, p.err)) { ok = false; break; }
                     mbar_expect_tx(&fullB[sb], (uint32_t)(nkc * B_BOX));
                     for (int kc = 0; kc < nkc; ++kc)
-                        tma_load_2d(sB + ((size_t)sb * nkc + kc) * B_BOX, &tmC, kc * TKB, j * TN, &fullB[sb]);
+                        tma_load_2d(sB + ((size_t)sb * nkc + kc) * B_BOX, &tmC, kc * p.tkb, j * TN, &fullB[sb]);
                     ++ib;
                 }
                 if (!ok) break;
@@ -298,9 +311,16 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                     for (int kc = 0; kc < nkc; ++kc) {
                         const uint32_t a0 = smem_u32(sA + ((size_t)sa * nkc + kc) * A_BOX);
                         const uint32_t b0 = smem_u32(sB + ((size_t)sb * nkc + kc) * B_BOX);
-                        for (int kk = 0; kk < TKB / 16; ++kk)
-                            mma_f16kind(dcol, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
-                                     (kc | kk) != 0 ? 1u : 0u);
+                        // four MMAs per 128-byte chunk: K = 16 (16-bit) or 32
+                        // (FP8) elements, 32 bytes each
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if (p.fp8)
+                                mma_f8kind(dcol, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                           (kc | kk) != 0 ? 1u : 0u);
+                            else
+                                mma_f16kind(dcol, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                            (kc | kk) != 0 ? 1u : 0u);
+                        }
                     }
                     mma_commit(&emptyB[sb]); // B slot free once these MMAs are done
                     mma_commit(&tfull[buf]); // accumulator ready for the epilogue
@@ -335,14 +355,16 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
         uint32_t cons = 0;  // accumulators consumed
         uint32_t tiles = 0; // tiles handed between the quarter's two warps
         const float C = p.it->cnorm_max;
+        const float Cd = p.it->cdnorm_max;
         const float neg2inv = p.it->neg2inv;
-        const float zeta = __fmaf_ru(p.uq, C, p.it->eta_c); // bound on ||c~ - c||
-        const float Cz = __fadd_ru(C, zeta);
+        const float zeta = __fmaf_ru(p.uq, Cd, p.it->eta_c); // bound on ||c~' - c'||
+        const float Czd = __fadd_ru(Cd, zeta);
         for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
             const int64_t row = t * TM + rloc;
             const bool valid = row < nrows;
             const float xn = valid ? (p.mode ? p.rxn[row] : p.xn[row]) : 0.0f;
-            const float twoE = prec_two_e(xn, C, zeta, Cz, p);
+            const float xdn = valid ? (p.mode ? p.rxdn[row] : p.xdn[row]) : 0.0f;
+            const float twoE = prec_two_e(xn, xdn, C, Cd, zeta, Czd, p);
             // twoE = +inf (an unrepresentable scale) sends every point to the
             // full FP32 scan
             // rows past the end of the gathered list hold stale operands (any
@@ -586,22 +608,26 @@ __global__ void k_prec_verify(const float *X, int64_t n, int32_t d, const float 
     }
 }
 
-// Gathers the 16-bit operand rows (and ||x||^2) of the listed points into a compact
-// matrix for the candidate pass: one warp per point, 16 bytes per lane.
-template <int DV>
-__global__ void k_prec_gather(const uint16_t *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
-                              uint16_t *Xc, float *rxn) {
+// Gathers the operand rows (ROWB bytes each) and ||x||^2, ||x'||^2 of the
+// listed points into a compact matrix for the candidate pass: one warp per
+// point, 16 bytes per lane.
+template <int ROWB>
+__global__ void k_prec_gather(const unsigned char *Xb, const float *xn, const float *xdn, const int32_t *rlist,
+                              const unsigned *rcount, unsigned char *Xc, float *rxn, float *rxdn) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned cnt = *rcount;
-    constexpr int V = DV * 2 / 16; // 16-byte vectors per row
+    constexpr int V = ROWB / 16; // 16-byte vectors per row
     for (int64_t e = wid; e < cnt; e += nw) {
         const int32_t i = rlist[e];
         if (lane < V)
-            reinterpret_cast<int4 *>(Xc + (size_t)e * DV)[lane] =
-                reinterpret_cast<const int4 *>(Xb + (size_t)i * DV)[lane];
-        if (lane == 0) rxn[e] = xn[i];
+            reinterpret_cast<int4 *>(Xc + (size_t)e * ROWB)[lane] =
+                reinterpret_cast<const int4 *>(Xb + (size_t)i * ROWB)[lane];
+        if (lane == 0) {
+            rxn[e] = xn[i];
+            rxdn[e] = xdn[i];
+        }
     }
 }
 
@@ -659,72 +685,89 @@ __global__ void k_delta_sums(const float *X, int64_t n, int32_t d, PtState *st, 
     if (lane == 0 && changed) atomicAdd(&ctr->changed, changed);
 }
 
+// Storage of one operand of format FMT.
+template <int FMT> struct OpT { using T = uint16_t; };
+template <> struct OpT<PREC_FMT_FP8> { using T = uint8_t; };
+
 template <int FMT>
-__device__ __forceinline__ uint16_t to_op(float v) {
-    if (FMT == PREC_FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-    return __half_as_ushort(__float2half_rn(v));
+__device__ __forceinline__ typename OpT<FMT>::T to_op(float v) {
+    if constexpr (FMT == PREC_FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    else if constexpr (FMT == PREC_FMT_FP16) return __half_as_ushort(__float2half_rn(v));
+    else return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); // never saturates: |v| <= 2^7
 }
 
-// Exponent e of the scale 2^e of an FP16 operand: the largest with
-// absmax * 2^e <= 2^15 (half of the FP16 range), clamped to [-60, 60].
-// BF16 has the FP32 exponent range and is not scaled.
+// Exponent e of the scale 2^e of an operand: the largest with absmax * 2^e
+// <= 2^15 (FP16, half its range) or 2^7 (FP8 e4m3, whose largest value is
+// 448), clamped to [-60, 60].  BF16 has the FP32 exponent range and is not
+// scaled.
 __host__ __device__ inline int scale_exp(int32_t fmt, float absmax) {
     if (fmt == PREC_FMT_BF16) return 0;
     if (!(absmax > 0.0f)) return 60;
     int ex;
     const float m = frexpf(absmax, &ex); // absmax = m 2^ex, m in [0.5, 1)
     const int cl = (m == 0.5f) ? ex - 1 : ex; // ceil(log2(absmax))
-    const int e = 15 - cl;
+    const int e = (fmt == PREC_FMT_FP8 ? 7 : 15) - cl;
     return e < -60 ? -60 : (e > 60 ? 60 : e);
 }
 
+// Absolute error of one rounded scaled coordinate (half the smallest
+// subnormal, with a factor 2 of margin): FP16 2^-24, FP8 e4m3 2^-9; for BF16
+// anything above half its smallest subnormal (2^-134).
+__host__ __device__ inline double op_eta(int32_t fmt) {
+    return fmt == PREC_FMT_BF16 ? 0x1p-100 : (fmt == PREC_FMT_FP16 ? 0x1p-24 : 0x1p-9);
+}
+
 // Per iteration, step 1: ||c||^2 (FP64 sum of the FP32 values, rounded to
-// nearest), max ||c|| (rounded up) and max |c_j|; one CTA per centroid.
-__global__ void k_prec_cnorm(const float *C32, int32_t d, float *cn, PrecIter *it) {
+// nearest), max ||c|| (rounded up), and with the per-dimension scales sigma
+// (FP8; NULL = 1) max ||c . sigma|| and max |c_j sigma_j|; one CTA per centroid.
+__global__ void k_prec_cnorm(const float *C32, int32_t d, const float *sigma, float *cn, PrecIter *it) {
     const int c = blockIdx.x;
-    __shared__ double red[128];
+    __shared__ double red[128], redd[128];
     __shared__ float amax[128];
-    double acc = 0.0;
+    double acc = 0.0, accd = 0.0;
     float am = 0.0f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const float v = C32[(size_t)c * d + j];
+        const float vd = sigma ? v * sigma[j] : v; // a power of two: exact
         acc += (double)v * (double)v;
-        am = fmaxf(am, fabsf(v));
+        accd += (double)vd * (double)vd;
+        am = fmaxf(am, fabsf(vd));
     }
     red[threadIdx.x] = acc;
+    redd[threadIdx.x] = accd;
     amax[threadIdx.x] = am;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        double t = 0.0, td = 0.0;
         float m = 0.0f;
-        for (int i = 0; i < (int)blockDim.x; ++i) { t += red[i]; m = fmaxf(m, amax[i]); }
+        for (int i = 0; i < (int)blockDim.x; ++i) { t += red[i]; td += redd[i]; m = fmaxf(m, amax[i]); }
         cn[c] = __double2float_rn(t);
         const float nrm = __double2float_ru(__dsqrt_ru(__dmul_ru(t, 1.0 + 1e-15)));
+        const float nrmd = __double2float_ru(__dsqrt_ru(__dmul_ru(td, 1.0 + 1e-15)));
         // non-negative floats order as ints
         atomicMax(reinterpret_cast<int *>(&it->cnorm_max), __float_as_int(nrm));
+        atomicMax(reinterpret_cast<int *>(&it->cdnorm_max), __float_as_int(nrmd));
         atomicMax(reinterpret_cast<int *>(&it->cabs_max), __float_as_int(m));
     }
 }
 
-// Per iteration, step 2: the scaled, rounded centroids c~ = fmt(c s_c), and
-// (block 0) the scale-dependent constants.
+// Per iteration, step 2: the scaled, rounded centroids c~' = fmt(c . sigma
+// s_c), and (block 0) the scale-dependent constants.
 template <int FMT>
-__global__ void k_prec_conv(const float *C32, int64_t kd, int32_t d, float sx, uint16_t *Cb, PrecIter *it) {
+__global__ void k_prec_conv(const float *C32, int64_t kd, int32_t d, float sx, const float *sigma,
+                            typename OpT<FMT>::T *Cb, PrecIter *it) {
     const float M = it->cabs_max;
     const int ec = scale_exp(FMT, M);
     const float sc = ldexpf(1.0f, ec);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < kd; i += (int64_t)gridDim.x * blockDim.x)
-        Cb[i] = to_op<FMT>(C32[i] * sc); // a power-of-two scale: exact
+        Cb[i] = to_op<FMT>(C32[i] * (sigma ? sigma[i % d] : 1.0f) * sc); // powers of two: exact
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int ex;
         frexpf(sx, &ex); // sx = 2^(ex - 1)
         it->neg2inv = ldexpf(-2.0f, -(ex - 1) - ec);
-        // absolute error of one rounded coordinate in the scaled domain:
-        // half the smallest FP16 subnormal (2^-25), or for BF16 anything
-        // above half its smallest subnormal (2^-134); taken with a margin
-        const double eta = FMT == PREC_FMT_BF16 ? 0x1p-100 : 0x1p-24;
-        float ec_bound = __double2float_ru(sqrt((double)d) * 1.000001 * eta * ldexp(1.0, -ec));
-        if (FMT != PREC_FMT_BF16 && !(M * sc <= 32768.0f)) ec_bound = CUDART_INF_F; // unrepresentable
+        float ec_bound = __double2float_ru(sqrt((double)d) * 1.000001 * op_eta(FMT) * ldexp(1.0, -ec));
+        const float lim = FMT == PREC_FMT_FP8 ? 128.0f : 32768.0f;
+        if (FMT != PREC_FMT_BF16 && !(M * sc <= lim)) ec_bound = CUDART_INF_F; // unrepresentable
         it->eta_c = ec_bound;
     }
 }
@@ -738,53 +781,80 @@ __global__ void k_prec_absmax(const float *X, int64_t count, float *out) {
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
 }
 
-// Once per context: scaled, rounded points x~ = fmt(x s_x) and ||x||^2
-// (FP64 sum, rounded to nearest).
+// Largest |x_ij| per dimension j (FP8 per-dimension scales).
+__global__ void k_prec_dim_absmax(const float *X, int64_t n, int32_t d, float *out) {
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        float m = 0.0f;
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) m = fmaxf(m, fabsf(X[i * d + j]));
+        atomicMax(reinterpret_cast<int *>(out + j), __float_as_int(m));
+    }
+}
+
+// Once per context: scaled, rounded points x~' = fmt(x / sigma s_x),
+// ||x||^2 and ||x / sigma||^2 (FP64 sums, rounded to nearest).
 template <int FMT>
-__global__ void k_prec_points(const float *X, int64_t n, int32_t d, float sx, uint16_t *Xb, float *xn) {
+__global__ void k_prec_points(const float *X, int64_t n, int32_t d, float sx, const float *sigma_inv,
+                              typename OpT<FMT>::T *Xb, float *xn, float *xdn) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = wid; i < n; i += nw) {
-        double acc = 0.0;
+        double acc = 0.0, accd = 0.0;
         for (int j = lane; j < d; j += 32) {
             const float v = X[i * d + j];
-            Xb[i * d + j] = to_op<FMT>(v * sx);
+            const float vd = sigma_inv ? v * sigma_inv[j] : v; // a power of two: exact
+            Xb[i * d + j] = to_op<FMT>(vd * sx);
             acc += (double)v * (double)v;
+            accd += (double)vd * (double)vd;
         }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-        if (lane == 0) xn[i] = __double2float_rn(acc);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(FULL_MASK, acc, o);
+            accd += __shfl_xor_sync(FULL_MASK, accd, o);
+        }
+        if (lane == 0) {
+            xn[i] = __double2float_rn(acc);
+            if (xdn != xn) xdn[i] = __double2float_rn(accd);
+        }
     }
 }
 
 // ------------------------------------------------------------- launchers
 
-// Constants of the certification bound.  With x~, c~ the operands the tensor
-// cores see (unscaled), u_q the unit roundoff of the format (BF16 2^-8, FP16
-// 2^-11) and eta the absolute error of a rounded scaled coordinate (FP16
-// subnormals):
-//   ||x~ - x|| <= xi = u_q ||x|| + sqrt(d) eta / s_x,  ||c~ - c|| <= zeta
-//   |x.c - x~.c~| <= ||x|| zeta + xi (||c|| + zeta)
-//   tensor-core FP32 accumulation of d products: at most g_tc ||x~|| ||c~||
-//     with g_tc = 2d 2^-23 / (1 - 2d 2^-23) (truncating adds, a factor 2)
+// Constants of the certification bound.  With x', c' the vectors in the
+// space the operands are rounded in (FP8: x / sigma and c . sigma with
+// power-of-two per-dimension scales sigma, so that x'.c' = x.c; else x and
+// c), x~', c~' the operands the tensor cores see (unscaled), u_q the unit
+// roundoff of the format (BF16 2^-8, FP16 2^-11, FP8 e4m3 2^-4) and eta the
+// absolute error of a rounded scaled coordinate (subnormals):
+//   ||x~' - x'|| <= xi = u_q ||x'|| + sqrt(d) eta / s_x,  ||c~' - c'|| <= zeta
+//   |x.c - x~'.c~'| <= ||x'|| zeta + xi (||c'|| + zeta)
+//   tensor-core FP32 accumulation of d products: at most g_tc ||x~'|| ||c~'||
+//     with g_tc = 2d 2^-23 / (1 - 2d 2^-23) for 16-bit operands (truncating
+//     adds, a factor 2), 2d 2^-16 / (1 - 2d 2^-16) for FP8 (no accumulator
+//     width is assumed beyond 17 bits)
 //   epilogue t = fma(acc, -2/(s_x s_c), ||c||^2): ||c||^2 rounded once and
-//     the fma once, <= u (||c||^2 + |t|) <= 2u ||x~|| ||c~|| + 2u ||c||^2
+//     the fma once, <= u (||c||^2 + |t|) <= 2u ||x~'|| ||c~'|| + 2u ||c||^2
 //   FP32 distance of the plain path: relative (d + 2) u / (1 - (d + 2) u)
 //     of d^2 <= 2 (||x||^2 + ||c||^2)
-// with u = 2^-24.  E = 2 (1.01) (dot error + accumulation) + eA32 ||x~|| ||c~||
-// + eB (||x||^2 + ||c||^2), eA32 = 1.01 (2u), eB = 1.01 (3u + 2 g_d), each
-// rounded up (prec_two_e evaluates it per point).
+// with u = 2^-24.  E = 2 (1.01) (dot error + accumulation) + eA32 ||x~'||
+// ||c~'|| + eB (||x||^2 + ||c||^2), eA32 = 1.01 (2u), eB = 1.01 (3u + 2 g_d),
+// each rounded up (prec_two_e evaluates it per point).
 void prec_error_constants(int32_t fmt, int d, float sx, PrecParams &p) {
     const double u = std::ldexp(1.0, -24);
-    const double gtc = 2.0 * d * std::ldexp(1.0, -23) / (1.0 - 2.0 * d * std::ldexp(1.0, -23));
+    const double ua = fmt == PREC_FMT_FP8 ? std::ldexp(1.0, -16) : std::ldexp(1.0, -23);
+    const double gtc = 2.0 * d * ua / (1.0 - 2.0 * d * ua);
     const double g = (d + 2) * u / (1.0 - (d + 2) * u);
-    const double eta = fmt == PREC_FMT_BF16 ? std::ldexp(1.0, -100) : std::ldexp(1.0, -24);
-    p.uq = fmt == PREC_FMT_BF16 ? std::ldexp(1.0f, -8) : std::ldexp(1.0f, -11);
+    p.uq = fmt == PREC_FMT_BF16 ? std::ldexp(1.0f, -8) : (fmt == PREC_FMT_FP16 ? std::ldexp(1.0f, -11)
+                                                                               : std::ldexp(1.0f, -4));
     p.gtc = std::nextafter((float)gtc, INFINITY);
-    p.eta_x = std::nextafter((float)(std::sqrt((double)d) * 1.000001 * eta / sx), INFINITY);
+    p.eta_x = std::nextafter((float)(std::sqrt((double)d) * 1.000001 * op_eta(fmt) / sx), INFINITY);
     p.eA32 = std::nextafter((float)(1.01 * 2 * u), INFINITY);
     p.eB = std::nextafter((float)(1.01 * (3 * u + 2 * g)), INFINITY);
-    p.idesc = idesc_f16kind(TM, TN, fmt == PREC_FMT_BF16 ? 1u : 0u);
+    p.idesc = fmt == PREC_FMT_FP8 ? idesc_f8kind(TM, TN) : idesc_f16kind(TM, TN, fmt == PREC_FMT_BF16 ? 1u : 0u);
+    p.fp8 = fmt == PREC_FMT_FP8 ? 1 : 0;
+    const int esize = fmt == PREC_FMT_FP8 ? 1 : 2;
+    p.nkc = d * esize / 128;
+    p.tkb = 128 / esize;
 }
 
 int prec_point_scale_exp(int32_t fmt, float absmax) { return scale_exp(fmt, absmax); }
@@ -796,25 +866,40 @@ cudaError_t prec_absmax(const float *X, int64_t count, float *out, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t prec_points(const float *X, int64_t n, int32_t d, int32_t fmt, float sx, void *Xb, float *xn,
-                        cudaStream_t s) {
-    uint16_t *o = static_cast<uint16_t *>(Xb);
-    if (fmt == PREC_FMT_BF16) k_prec_points<PREC_FMT_BF16><<<1024, 256, 0, s>>>(X, n, d, sx, o, xn);
-    else k_prec_points<PREC_FMT_FP16><<<1024, 256, 0, s>>>(X, n, d, sx, o, xn);
+cudaError_t prec_dim_absmax(const float *X, int64_t n, int32_t d, float *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * d, s);
+    if (e != cudaSuccess) return e;
+    k_prec_dim_absmax<<<1024, 128, 0, s>>>(X, n, d, out);
     return cudaGetLastError();
 }
 
-cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, int32_t fmt, float sx, void *Cb, float *cn,
-                      PrecIter *it, cudaStream_t s) {
+cudaError_t prec_points(const float *X, int64_t n, int32_t d, int32_t fmt, float sx, const float *sigma_inv,
+                        void *Xb, float *xn, float *xdn, cudaStream_t s) {
+    if (fmt == PREC_FMT_BF16)
+        k_prec_points<PREC_FMT_BF16><<<1024, 256, 0, s>>>(X, n, d, sx, nullptr, static_cast<uint16_t *>(Xb), xn, xn);
+    else if (fmt == PREC_FMT_FP16)
+        k_prec_points<PREC_FMT_FP16><<<1024, 256, 0, s>>>(X, n, d, sx, nullptr, static_cast<uint16_t *>(Xb), xn, xn);
+    else
+        k_prec_points<PREC_FMT_FP8><<<1024, 256, 0, s>>>(X, n, d, sx, sigma_inv, static_cast<uint8_t *>(Xb), xn,
+                                                         xdn);
+    return cudaGetLastError();
+}
+
+cudaError_t prec_prep(const float *C32, int32_t k, int32_t d, int32_t fmt, float sx, const float *sigma, void *Cb,
+                      float *cn, PrecIter *it, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(it, 0, sizeof(PrecIter), s);
     if (e != cudaSuccess) return e;
-    k_prec_cnorm<<<k, 128, 0, s>>>(C32, d, cn, it);
+    const float *sg = fmt == PREC_FMT_FP8 ? sigma : nullptr;
+    k_prec_cnorm<<<k, 128, 0, s>>>(C32, d, sg, cn, it);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t kd = (int64_t)k * d;
     const int grid = (int)std::min<int64_t>((kd + 255) / 256, 1024);
-    uint16_t *o = static_cast<uint16_t *>(Cb);
-    if (fmt == PREC_FMT_BF16) k_prec_conv<PREC_FMT_BF16><<<grid, 256, 0, s>>>(C32, kd, d, sx, o, it);
-    else k_prec_conv<PREC_FMT_FP16><<<grid, 256, 0, s>>>(C32, kd, d, sx, o, it);
+    if (fmt == PREC_FMT_BF16)
+        k_prec_conv<PREC_FMT_BF16><<<grid, 256, 0, s>>>(C32, kd, d, sx, nullptr, static_cast<uint16_t *>(Cb), it);
+    else if (fmt == PREC_FMT_FP16)
+        k_prec_conv<PREC_FMT_FP16><<<grid, 256, 0, s>>>(C32, kd, d, sx, nullptr, static_cast<uint16_t *>(Cb), it);
+    else
+        k_prec_conv<PREC_FMT_FP8><<<grid, 256, 0, s>>>(C32, kd, d, sx, sg, static_cast<uint8_t *>(Cb), it);
     return cudaGetLastError();
 }
 
@@ -846,13 +931,13 @@ cudaError_t prec_recheck(int dv, const float *X, const float *C32, int32_t k, co
     return cudaGetLastError();
 }
 
-cudaError_t prec_gather(int dv, const void *Xb, const float *xn, const int32_t *rlist, const unsigned *rcount,
-                        void *Xc, float *rxn, int grid, cudaStream_t s) {
-    const uint16_t *a = static_cast<const uint16_t *>(Xb);
-    uint16_t *b = static_cast<uint16_t *>(Xc);
-    switch (dv) {
-    case 64: k_prec_gather<64><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;
-    case 128: k_prec_gather<128><<<grid, 256, 0, s>>>(a, xn, rlist, rcount, b, rxn); break;
+cudaError_t prec_gather(int row_bytes, const void *Xb, const float *xn, const float *xdn, const int32_t *rlist,
+                        const unsigned *rcount, void *Xc, float *rxn, float *rxdn, int grid, cudaStream_t s) {
+    const unsigned char *a = static_cast<const unsigned char *>(Xb);
+    unsigned char *b = static_cast<unsigned char *>(Xc);
+    switch (row_bytes) {
+    case 128: k_prec_gather<128><<<grid, 256, 0, s>>>(a, xn, xdn, rlist, rcount, b, rxn, rxdn); break;
+    case 256: k_prec_gather<256><<<grid, 256, 0, s>>>(a, xn, xdn, rlist, rcount, b, rxn, rxdn); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

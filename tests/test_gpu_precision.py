@@ -27,7 +27,7 @@ def _lib():
     knor.load()
 
 
-FORMS = ["bf16", "fp16"]
+FORMS = ["bf16", "fp16", "fp8"]  # FP8 e4m3 needs d = 128
 
 
 def _run_checked(X, k, iters, seed=42, init=None, form="bf16"):
@@ -62,6 +62,8 @@ def _run_checked(X, k, iters, seed=42, init=None, form="bf16"):
 @pytest.mark.parametrize("n,d,k", [(5000, 128, 64), (20011, 128, 300), (9000, 64, 256), (30000, 128, 1024),
                                    (100, 64, 3), (130, 128, 129)])
 def test_precision_form_equals_fp32_assignments(n, d, k, form):
+    if form == "fp8" and d != 128:
+        pytest.skip("the FP8 form needs d = 128")
     X = synth.aniso_mixture(n, d, min(k, 64), 200 + k).numpy()
     _run_checked(X, k, 12, form=form)
 
@@ -89,6 +91,8 @@ def test_fp16_form_rechecks_fewer_points_than_bf16():
 def test_precision_form_many_tiles_per_cta(n, d, k, form):
     """Enough points that every CTA of the persistent kernel reuses its tile
     stages and accumulator buffers many times."""
+    if form == "fp8" and d != 128:
+        pytest.skip("the FP8 form needs d = 128")
     X = synth.aniso_mixture(n, d, min(k, 64), 300 + k).numpy()
     Xd = torch.as_tensor(X).cuda()
     with knor.Context(Xd, k, seed=5, precision=form) as c:
@@ -120,7 +124,7 @@ def test_planted_ties_are_rechecked(form):
     """Points exactly between two centroids have a zero top-2 gap: they must be
     re-scored in FP32 (and land on the lower index)."""
     rng = np.random.default_rng(3)
-    d, k = 64, 32
+    d, k = (128 if form == "fp8" else 64), 32
     C = rng.uniform(-5, 5, (k, d)).astype(np.float32)
     mids = ((C[0:8].astype(np.float64) + C[8:16].astype(np.float64)) / 2).astype(np.float32)
     X = np.concatenate([mids, C + 0.01 * rng.standard_normal((k, d)).astype(np.float32),
@@ -143,13 +147,15 @@ def test_stale_operand_rows_never_enter_candidate_lists(form):
     freed memory with 16-bit infinities first (so the context's buffers very
     likely start out holding them): those rows must record no candidates,
     in particular not into the first listed point's list."""
-    inf16 = 0x7C00 if form == "fp16" else 0x7F80
+    # 16-bit infinities; for FP8 e4m3 (no infinity) the byte pair 0x7F7F is
+    # two NaNs, the worst it can hold
+    inf16 = {"fp16": 0x7C00, "bf16": 0x7F80, "fp8": 0x7F7F}[form]
     junk = torch.full((256 << 20,), inf16, dtype=torch.int16, device="cuda")
     del junk
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     rng = np.random.default_rng(11)
-    d, k = 64, 48
+    d, k = (128 if form == "fp8" else 64), 48
     C = rng.uniform(-5, 5, (k, d)).astype(np.float32)
     X = rng.uniform(-5, 5, (20000, d)).astype(np.float32)
     with knor.Context(torch.as_tensor(X).cuda(), k, init="explicit", precision=form, debug_invariants=True) as c:
@@ -165,10 +171,11 @@ def test_stale_operand_rows_never_enter_candidate_lists(form):
 
 @pytest.mark.parametrize("form", FORMS)
 def test_precision_form_rejects_unsupported_shapes(form):
-    X = torch.zeros((100, 32), device="cuda")
-    with pytest.raises(knor.KnorError) as e:
-        knor.Context(X, 4, precision=form)
-    assert e.value.status == knor.KNOR_ERR_ARG
+    for d in ((32, 64) if form == "fp8" else (32,)):
+        X = torch.zeros((100, d), device="cuda")
+        with pytest.raises(knor.KnorError) as e:
+            knor.Context(X, 4, precision=form)
+        assert e.value.status == knor.KNOR_ERR_ARG
 
 
 @pytest.mark.parametrize("form", FORMS)
