@@ -60,6 +60,8 @@ def _datasets():
         ("iso_d8", lambda: synth.isotropic_mixture(6000, 8, 10, 11).numpy(), 10),
         ("spd_d32", lambda: synth.spd_mixture(9000, 32, 20, 12).numpy(), 20),
         ("spd_d16_k37", lambda: synth.spd_mixture(7777, 16, 37, 13).numpy(), 37),
+        # k x k table above 16 KB: the warp MTI scan reads it from global memory
+        ("uniform_d16_k100", lambda: synth.uniform_cube(6000, 16, 20).numpy(), 100),
         ("uniform_d4", lambda: synth.uniform_cube(5000, 4, 14).numpy(), 25),
         ("aniso_d64", lambda: synth.aniso_mixture(4000, 64, 30, 15).numpy(), 30),
         ("aniso_d128", lambda: synth.aniso_mixture(3000, 128, 17, 16).numpy(), 17),
