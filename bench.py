@@ -69,6 +69,20 @@ def dist_env():
     return world, rank, local
 
 
+def aggregate(ms: float, work: float, world: int, device: str = "cuda"):
+    """Whole-job figures of N replicas: the slowest rank's time and the work
+    of all ranks (point-iterations).  Returns (ms_max, work_total)."""
+    if world <= 1:
+        return ms, work
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(work)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi while timing."""
 
@@ -323,14 +337,7 @@ def batch_arm(args, wl, world, rank, local):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms, float(pit)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, pts_all = float(mx[0]), float(t[1])
-    else:
-        ms_max, pts_all = ms, float(pit)
+    ms_max, pts_all = aggregate(ms, float(pit), world)
     value = pts_all / (ms_max / 1000.0)
     launches = sum(3 + 4 * it for it in iters)
 
@@ -514,14 +521,7 @@ def our_arm(args, wl, world, rank, local):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     pts = float(n) * sum(iters)
-    if world > 1:
-        t = torch.tensor([ms, pts], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, pts_all = float(mx[0]), float(t[1])
-    else:
-        ms_max, pts_all = ms, pts
+    ms_max, pts_all = aggregate(ms, pts, world)
     value = pts_all / (ms_max / 1000.0)
     per_it = 9 if wl.get("precision", "fp32") != "fp32" else (4 if wl["prune"] else 3)
     launches = sum(3 + it * per_it for it in iters)
