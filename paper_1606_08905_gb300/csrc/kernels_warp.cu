@@ -78,48 +78,6 @@ __device__ __forceinline__ void warp_group_accumulate(RowFn rowsrc, int cl, bool
     }
 }
 
-// Stable counting sort of a warp's queue entries (local index, key) by key
-// modulo nkeys.  The key is a * UBINS + bin(u / s(a)): the points of a batch
-// then share their row of the k x k table, and since for a fixed a the
-// centroids that survive Clause 2 are exactly those with 1/2 d(c_a, c) below
-// the point's bound, points with similar u keep nearly the same candidates.
-// Stable and order-independent in its counts, hence deterministic.
-__device__ __forceinline__ void warp_sort_by_cluster(int2 *q, int2 *tmp, int *hist, int qlen, int k) {
-    const int lane = threadIdx.x & 31;
-    for (int c = lane; c < k; c += 32) hist[c] = 0;
-    __syncwarp();
-    for (int e = lane; e < qlen; e += 32) atomicAdd(&hist[max(q[e].y, 0) % k], 1);
-    __syncwarp();
-    int carry = 0;
-    for (int c0 = 0; c0 < k; c0 += 32) {
-        const int c = c0 + lane;
-        const int v = c < k ? hist[c] : 0;
-        int incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (c < k) hist[c] = carry + incl - v;
-        carry += __shfl_sync(FULL_MASK, incl, 31);
-    }
-    __syncwarp();
-    for (int base = 0; base < qlen; base += 32) {
-        const int e = base + lane;
-        const bool valid = e < qlen;
-        const int2 ent = valid ? q[e] : make_int2(0, 0);
-        const int key = valid ? max(ent.y, 0) % k : -1 - lane;
-        const unsigned m = __match_any_sync(FULL_MASK, key);
-        const int rank = __popc(m & ((1u << lane) - 1u));
-        if (valid) tmp[hist[key] + rank] = ent;
-        __syncwarp();
-        if (valid && rank == 0) hist[key] += __popc(m);
-        __syncwarp();
-    }
-    for (int e = lane; e < qlen; e += 32) q[e] = tmp[e];
-    __syncwarp();
-}
-
 // Warp w's accumulators: shared memory, or its slot of p.wacc.
 __device__ __forceinline__ float *warp_acc_hi(const IterParams &p, unsigned char *sm, int w) {
     if (p.wacc) return p.wacc + ((size_t)blockIdx.x * WPC + w) * 2 * (size_t)p.k * p.d;
@@ -272,11 +230,13 @@ __global__ void __launch_bounds__(WT) k_dense_w(const IterParams p, const int32_
 // --------------------------------------------------------------- MTI scan
 
 // Per warp: the packed state of its chunks streams into shared memory with
-// cp.async (WSTAGES chunks in flight); the Clause-1 test queues the points
-// it cannot skip (in point order); every 32 queued points are scanned one
-// per lane (Clause 3 tightening, Clause 2 per centroid) and the rows that
-// changed cluster move between the warp's sums (read back from global
-// memory, where the scan has just loaded them).
+// cp.async (WSTAGES chunks in flight); the points that Clause 1 cannot skip
+// go, in point order, to the bucket of their cluster; every bucket that
+// reaches 32 points is scanned one point per lane (Clause 3 tightening,
+// Clause 2 per centroid), and the warp's partial buckets after its last
+// chunk.  The rows that changed cluster move between the warp's sums (read
+// back from global memory, where the scan has just loaded them).  Bucket
+// order depends only on the point order, so the sums stay deterministic.
 // d <= 32: 5 resident CTAs x 4 warps per SM (registers capped at 96, no
 // spills); wider points keep their registers
 template <int DV>
@@ -290,13 +250,16 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
     float *acc_hi = warp_acc_hi(p, sm, w);
     float *acc_lo = warp_acc_lo(p, sm, w);
     int *cnt = reinterpret_cast<int *>(wr + p.w_cnt);
-    int2 *queue = reinterpret_cast<int2 *>(wr + p.w_queue);
-    int2 *queue2 = queue + WQCAP;
-    int *hist = reinterpret_cast<int *>(queue2 + WQCAP);
+    // per-cluster buckets: bucket c (c < k: points assigned to cluster c;
+    // c = k: unassigned points) is a ring of WBCAP local indices
+    int *bk = reinterpret_cast<int *>(wr + p.w_bucket);
+    int *bhead = bk + (k + 1) * WBCAP;
+    int *bcnt = bhead + (k + 1);
     PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
     for (int e = lane; e < k * DV; e += 32) { acc_hi[e] = 0.0f; acc_lo[e] = 0.0f; }
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
+    for (int c = lane; c <= k; c += 32) { bhead[c] = 0; bcnt[c] = 0; }
     const Shared sh = stage_shared(p, sm, true);
     __syncthreads();
     int64_t lo, hi;
@@ -317,7 +280,86 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
     };
 
     long long my_skipped = 0, my_evals = 0, my_changed = 0;
-    int qlen = 0;
+
+    // Phases B and C on the first nb (<= 32) points of bucket cb: every
+    // lane of the batch shares a = cb, hence the row of the k x k table, and
+    // the candidate sets of Clause 2 are nested (all centroids c with
+    // 1/2 d(c_a, c) below the point's bound), so the walk over the union of
+    // the lanes' masks leaves few lanes idle.
+    auto run_batch = [&](int cb, int nb) {
+        const int a = cb == k ? -1 : cb;
+        const int *ring = bk + cb * WBCAP;
+        const int h0 = bhead[cb];
+        int best = -1;
+        int64_t i = 0;
+        bool changed = false;
+        unsigned long long xk[DV / 2];
+        float bd = CUDART_INF_F, tst = 0.0f;
+        if (lane < nb) {
+            i = lo + ring[(h0 + lane) & (WBCAP - 1)];
+            ldg_x2<DV>(xk, p.X + i * DV);
+            if (a < 0) {
+                best = 0;
+                for (int c = 0; c < k; ++c) {
+                    const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
+                    if (r < bd) { bd = r; best = c; }
+                }
+                my_evals += k;
+            } else {
+                // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
+                bd = d2_reg<DV>(xk, sh.cent + (size_t)a * DV);
+                best = a;
+                ++my_evals;
+            }
+            tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
+        }
+        // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives;
+        // the warp walks the union of the lanes' masks in index order and
+        // each lane scores its own survivors.
+        if (a >= 0) {
+            const float *hrow = sh.halfD + (size_t)a * k;
+            for (int cw = 0; cw < k; cw += 32) {
+                unsigned mask = 0;
+                if (lane < nb) {
+                    const int lim = min(32, k - cw);
+                    for (int b = 0; b < lim; ++b)
+                        mask |= (!(tst < hrow[cw + b]) && cw + b != a ? 1u : 0u) << b;
+                }
+                unsigned uni = __reduce_or_sync(FULL_MASK, mask);
+                while (uni) {
+                    const int b = __ffs(uni) - 1;
+                    uni &= uni - 1;
+                    if ((mask >> b) & 1u) {
+                        const int c = cw + b;
+                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
+                        ++my_evals;
+                        if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+                    }
+                }
+            }
+        }
+        if (lane < nb) {
+            PtState ns;
+            ns.a = best;
+            ns.ub = __fsub_ru(bound_up(bd, p.g_up, p.tiny), sh.F[best]);
+            p.st[i] = ns;
+            changed = best != a;
+            my_changed += changed ? 1 : 0;
+        }
+        // member pl's row, by its bucket entry (no shuffles: the member loop
+        // of warp_group_accumulate is lane-divergent)
+        const float *X = p.X;
+        auto row = [&](int pl, int j) { return __ldg(X + (lo + ring[(h0 + pl) & (WBCAP - 1)]) * DV + j); };
+        warp_group_accumulate<DV>(row, best, changed, 1.0f, acc_hi, acc_lo, cnt);
+        warp_group_accumulate<DV>(row, a, changed && a >= 0, -1.0f, acc_hi, acc_lo, cnt);
+        __syncwarp();
+        if (lane == 0) {
+            bhead[cb] = (h0 + nb) & (WBCAP - 1);
+            bcnt[cb] -= nb;
+        }
+        __syncwarp();
+    };
+
 #pragma unroll
     for (int s = 0; s < WSTAGES - 1; ++s) prefetch(s, w + (int64_t)s * WPC);
     int stage = 0;
@@ -347,22 +389,15 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
         }
         unsigned amask = 0;
         int nvalid = 0;
-        int ubin[PA];
 #pragma unroll
         for (int u = 0; u < PA; ++u) {
             const int a = ps[u].a;
-            ubin[u] = 0;
             if (a == -2) continue;
             ++nvalid;
             bool act = true;
             if (a >= 0) {
                 const float uu = __fadd_ru(ps[u].ub, sh.F[a]); // u^t = ub + F^t(a)
                 act = !(__fmaf_ru(uu, p.onepk, p.tau) < sh.s[a]);
-                // bin of u / s(a) on a quarter-octave scale (sort key only)
-                if (p.ubins > 1) {
-                    const float r = __fdividef(uu, fmaxf(sh.s[a], 1e-30f));
-                    ubin[u] = min(p.ubins - 1, max(0, (int)(4.0f * __log2f(fmaxf(r, 1.0f)))));
-                }
             }
             amask |= (act ? 1u : 0u) << u;
         }
@@ -375,98 +410,52 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
             if (lane >= o) incl += v;
         }
         const int total = __shfl_sync(FULL_MASK, incl, 31);
-        int pos = qlen + incl - na;
+        // the points that pass Clause 1, in point order, staged in the state
+        // buffer just read (its next prefetch comes after this chunk)
+        int2 *stg = reinterpret_cast<int2 *>(stbuf + stage * WCH);
+        __syncwarp();
+        int pos = incl - na;
 #pragma unroll
         for (int u = 0; u < PA; ++u) {
             if ((amask >> u) & 1u) {
-                queue[pos] = make_int2((int)(i0 + u - lo), ps[u].a < 0 ? -1 : ps[u].a * p.ubins + ubin[u]);
+                stg[pos] = make_int2((int)(i0 + u - lo), ps[u].a);
                 ++pos;
             }
         }
-        qlen += total;
         __syncwarp();
         stage = (stage + 1) % WSTAGES;
 
-        // ---- phases B and C on every full batch of 32 (and the rest at the end)
-        const bool last = m + WPC >= nchunk;
-        if (p.sort_queue && (qlen >= 32 || last)) warp_sort_by_cluster(queue, queue2, hist, qlen, k * p.ubins);
-        int qhead = 0;
-        while (qlen >= 32 || (last && qlen > 0)) {
-            const int nb = min(32, qlen);
-            int best = -1, a = -1;
-            int64_t i = 0;
-            bool changed = false;
-            unsigned long long xk[DV / 2];
-            float bd = CUDART_INF_F, tst = 0.0f;
-            if (lane < nb) {
-                const int2 e = queue[qhead + lane];
-                i = lo + e.x;
-                a = e.y < 0 ? -1 : e.y / p.ubins;
-                ldg_x2<DV>(xk, p.X + i * DV);
-                if (a < 0) {
-                    best = 0;
-                    for (int c = 0; c < k; ++c) {
-                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
-                        if (r < bd) { bd = r; best = c; }
-                    }
-                    my_evals += k;
-                } else {
-                    // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
-                    bd = d2_reg<DV>(xk, sh.cent + (size_t)a * DV);
-                    best = a;
-                    ++my_evals;
-                }
-                tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
+        // ---- append to the buckets 32 at a time; a bucket that reaches 32
+        // points runs as one batch
+        for (int base = 0; base < total; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < total;
+            const int2 ent = valid ? stg[e] : make_int2(0, 0);
+            const int key = valid ? (ent.y < 0 ? k : ent.y) : -1 - lane;
+            const unsigned grp = __match_any_sync(FULL_MASK, key);
+            const int rank = __popc(grp & ((1u << lane) - 1u));
+            int now = 0;
+            if (valid) {
+                const int c0 = bcnt[key];
+                bk[key * WBCAP + ((bhead[key] + c0 + rank) & (WBCAP - 1))] = ent.x;
+                now = c0 + __popc(grp);
             }
-            // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives;
-            // each lane's survivors form a bit mask per 32 centroids, the warp
-            // walks the union of the masks in index order, and each lane
-            // scores its own survivors.
-            for (int cw = 0; cw < k; cw += 32) {
-                unsigned mask = 0;
-                if (lane < nb && a >= 0) {
-                    const float *hrow = sh.halfD + (size_t)a * k + cw;
-                    const int lim = min(32, k - cw);
-                    for (int b = 0; b < lim; ++b)
-                        mask |= (!(tst < hrow[b]) && cw + b != a ? 1u : 0u) << b;
-                }
-                unsigned uni = __reduce_or_sync(FULL_MASK, mask);
-                while (uni) {
-                    const int b = __ffs(uni) - 1;
-                    uni &= uni - 1;
-                    if ((mask >> b) & 1u) {
-                        const int c = cw + b;
-                        const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
-                        ++my_evals;
-                        if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
-                    }
-                }
-            }
-            if (lane < nb) {
-                PtState ns;
-                ns.a = best;
-                ns.ub = __fsub_ru(bound_up(bd, p.g_up, p.tiny), sh.F[best]);
-                p.st[i] = ns;
-                changed = best != a;
-                my_changed += changed ? 1 : 0;
-            }
-            // member pl's row, by its queue entry (no shuffles: the member
-            // loop of warp_group_accumulate is lane-divergent)
-            const float *X = p.X;
-            const int2 *qb = queue + qhead;
-            auto row = [&](int pl, int j) { return __ldg(X + (lo + qb[pl].x) * DV + j); };
-            warp_group_accumulate<DV>(row, best, changed, 1.0f, acc_hi, acc_lo, cnt);
-            warp_group_accumulate<DV>(row, a, changed && a >= 0, -1.0f, acc_hi, acc_lo, cnt);
-            qhead += nb;
-            qlen -= nb;
-        }
-        if (qhead > 0 && qlen > 0) { // qlen < 32: move the rest to the front
-            int2 v = make_int2(0, 0);
-            if (lane < qlen) v = queue[qhead + lane];
             __syncwarp();
-            if (lane < qlen) queue[lane] = v;
+            if (valid && rank == 0) bcnt[key] = now;
+            __syncwarp();
+            unsigned full = __ballot_sync(FULL_MASK, valid && rank == 0 && now >= 32);
+            while (full) {
+                const int leader = __ffs(full) - 1;
+                full &= full - 1;
+                run_batch(__shfl_sync(FULL_MASK, key, leader), 32);
+            }
         }
         __syncwarp();
+    }
+    // the warp's partial buckets
+    for (int cb = 0; cb <= k; ++cb) {
+        const int left = bcnt[cb];
+        if (left > 0) run_batch(cb, left);
     }
     cp_async_wait<0>();
     const long long t1 = warp_sum_ll(my_changed);

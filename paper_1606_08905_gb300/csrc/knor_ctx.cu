@@ -313,9 +313,9 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     p.w_acc_lo = mti ? 0 : wtake(kd * 4);
     p.w_cnt = wtake((size_t)k * 4);
     p.w_tile = wtake(mti ? 0 : 2 * 32 * (size_t)p.dpad * 4); // dense: two row tiles
-    p.sort_queue = (mti && k <= 1024) ? 1 : 0;
-    p.ubins = k <= 128 ? 8 : 1;
-    p.w_queue = wtake(mti ? 2 * WQCAP * sizeof(int2) + (p.sort_queue ? (size_t)k * p.ubins * 4 : 0) : 0);
+    // MTI: k + 1 point buckets (one per cluster, one for unassigned points)
+    // of WBCAP local indices, then their heads and counts
+    p.w_bucket = wtake(mti ? (size_t)(k + 1) * (WBCAP + 2) * 4 : 0);
     p.w_state = wtake(mti ? (size_t)WSTAGES * WCH * sizeof(PtState) : 0);
     p.w_stride = (int32_t)woff;
     const size_t total = off + (size_t)WPC * woff;

@@ -16,11 +16,12 @@ constexpr int PA = 8;
 constexpr int QCAP = NT * PA + NT;
 
 // Warp-autonomous kernels (k_dense_w, k_mti_w): warps per CTA, points per
-// warp chunk of the bound test (PA per lane), per-warp queue capacity and
-// state chunks in flight per warp.
+// warp chunk of the bound test (PA per lane), capacity of each per-cluster
+// bucket of k_mti_w (fewer than 32 left plus one append of 32; a power of
+// two, used as a ring) and state chunks in flight per warp.
 constexpr int WPC = 4;
 constexpr int WCH = 32 * PA;
-constexpr int WQCAP = 32 + WCH;
+constexpr int WBCAP = 64;
 constexpr int WSTAGES = 2;
 
 // Per-point MTI state, packed so that the bound test reads 8 bytes per point.
@@ -87,9 +88,7 @@ struct IterParams {
     // w_base + w * w_stride; offsets below are within that region
     int32_t warp_kernels;  // 1: k_dense_w / k_mti_w; 0: the CTA kernels
     int32_t w_base, w_stride;
-    int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_queue, w_state;
-    int32_t sort_queue;    // k_mti_w: sort each warp's queue by cluster (k <= 1024)
-    int32_t ubins;         // k_mti_w: bins of u / s(a) in the sort key (1 = by cluster only)
+    int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_bucket, w_state;
     // k_mti_w: when non-null, each warp's TwoSum accumulators (hi then lo,
     // k x d each) live in this global array, slot blockIdx.x * WPC + warp,
     // instead of shared memory (few points change cluster in an MTI
