@@ -313,24 +313,23 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
             }
             tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
         }
-        // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives;
-        // the warp walks the union of the lanes' masks in index order and
-        // each lane scores its own survivors.
+        // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives.
+        // The lanes share the row 1/2 d(c_a, .), so the union of their
+        // survivors is the survivor set of the largest bound: lane b tests
+        // centroid cw + b against it, and the warp walks the union in index
+        // order, each lane scoring its own survivors.
         if (a >= 0) {
             const float *hrow = sh.halfD + (size_t)a * k;
+            // tst >= 0 (sign bit cleared for -0): its bit pattern orders like the value
+            const float tmax = __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(tst) & 0x7fffffffu));
             for (int cw = 0; cw < k; cw += 32) {
-                unsigned mask = 0;
-                if (lane < nb) {
-                    const int lim = min(32, k - cw);
-                    for (int b = 0; b < lim; ++b)
-                        mask |= (!(tst < hrow[cw + b]) && cw + b != a ? 1u : 0u) << b;
-                }
-                unsigned uni = __reduce_or_sync(FULL_MASK, mask);
+                const int cl = cw + lane;
+                unsigned uni = __ballot_sync(FULL_MASK, cl < k && cl != a && !(tmax < hrow[min(cl, k - 1)]));
                 while (uni) {
                     const int b = __ffs(uni) - 1;
                     uni &= uni - 1;
-                    if ((mask >> b) & 1u) {
-                        const int c = cw + b;
+                    const int c = cw + b;
+                    if (lane < nb && !(tst < hrow[c])) {
                         const float r = d2_reg<DV>(xk, sh.cent + (size_t)c * DV);
                         ++my_evals;
                         if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
