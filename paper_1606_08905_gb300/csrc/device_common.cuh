@@ -76,6 +76,24 @@ __device__ __forceinline__ void ldg_x2(unsigned long long (&x2)[DV / 2], const f
     }
 }
 
+// The same from a 32-byte-aligned row (DV a multiple of 8) with 32-byte
+// loads: one request per lane and sector, where 16-byte loads take two.
+template <int DV>
+__device__ __forceinline__ void ldg_x2_w32(unsigned long long (&x2)[DV / 2], const float *row) {
+    static_assert(DV % 8 == 0, "32-byte row loads need DV % 8 == 0");
+#pragma unroll
+    for (int j = 0; j < DV; j += 8) {
+        float v0, v1, v2, v3, v4, v5, v6, v7;
+        asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3), "=f"(v4), "=f"(v5), "=f"(v6), "=f"(v7)
+                     : "l"(row + j));
+        x2[j / 2] = pack2(v0, v1);
+        x2[j / 2 + 1] = pack2(v2, v3);
+        x2[j / 2 + 2] = pack2(v4, v5);
+        x2[j / 2 + 3] = pack2(v6, v7);
+    }
+}
+
 // d^2 to one centroid (16-byte aligned, smem or global).
 template <int DV>
 __device__ __forceinline__ float d2_reg(const unsigned long long (&x2)[DV / 2], const float *c) {

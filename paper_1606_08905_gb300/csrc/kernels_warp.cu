@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
         float bd = CUDART_INF_F, tst = 0.0f;
         if (lane < nb) {
             i = lo + ring[(h0 + lane) & (WBCAP - 1)];
-            ldg_x2<DV>(xk, p.X + i * DV);
+            // rows of >= 8 floats start on 32-byte boundaries (cudaMalloc base)
+            if constexpr (DV % 8 == 0) ldg_x2_w32<DV>(xk, p.X + i * DV);
+            else ldg_x2<DV>(xk, p.X + i * DV);
             if (a < 0) {
                 best = 0;
                 for (int c = 0; c < k; ++c) {
