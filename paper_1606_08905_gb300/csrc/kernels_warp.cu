@@ -263,23 +263,25 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
     const Shared sh = stage_shared(p, sm, true);
     __syncthreads();
     int64_t lo, hi;
-    block_range(p.n, PA, lo, hi);
+    block_range(p.n, WPA, lo, hi);
     const int64_t nchunk = (hi - lo + WCH - 1) / WCH;
 
     auto prefetch = [&](int stage, int64_t m) {
         if (m < nchunk) {
-            const int64_t i0 = lo + m * WCH + (int64_t)lane * PA;
-            if (i0 + PA <= hi) {
+            const int64_t i0 = lo + m * WCH + (int64_t)lane * WPA;
+            if (i0 + WPA <= hi) {
                 const char *src = reinterpret_cast<const char *>(p.st + i0);
-                char *dst = reinterpret_cast<char *>(stbuf + stage * WCH + lane * PA);
+                char *dst = reinterpret_cast<char *>(stbuf + stage * WCH + lane * WPA);
 #pragma unroll
-                for (int v = 0; v < PA * 8 / 16; ++v) cp_async16(dst + 16 * v, src + 16 * v);
+                for (int v = 0; v < WPA * 8 / 16; ++v) cp_async16(dst + 16 * v, src + 16 * v);
             }
         }
         cp_async_commit();
     };
 
-    long long my_skipped = 0, my_evals = 0, my_changed = 0;
+    // per-lane counts: a lane sees at most n / (32 x warps) points, each
+    // with at most k evaluations, far below 2^32 for any resident n
+    unsigned my_skipped = 0, my_evals = 0, my_changed = 0;
 
     // Phases B and C on the first nb (<= 32) points of bucket cb: every
     // lane of the batch shares a = cb, hence the row of the k x k table, and
@@ -368,13 +370,13 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
         prefetch((stage + WSTAGES - 1) % WSTAGES, m + (int64_t)(WSTAGES - 1) * WPC);
         cp_async_wait<WSTAGES - 1>();
         __syncwarp();
-        // ---- phase A: Clause 1 on PA consecutive points per lane
-        const int64_t i0 = lo + m * WCH + (int64_t)lane * PA;
-        PtState ps[PA];
-        if (i0 + PA <= hi) {
-            const int4 *src = reinterpret_cast<const int4 *>(stbuf + stage * WCH + lane * PA);
+        // ---- phase A: Clause 1 on WPA consecutive points per lane
+        const int64_t i0 = lo + m * WCH + (int64_t)lane * WPA;
+        PtState ps[WPA];
+        if (i0 + WPA <= hi) {
+            const int4 *src = reinterpret_cast<const int4 *>(stbuf + stage * WCH + lane * WPA);
 #pragma unroll
-            for (int v = 0; v < PA / 2; ++v) {
+            for (int v = 0; v < WPA / 2; ++v) {
                 const int4 q = src[v];
                 ps[2 * v].ub = __int_as_float(q.x);
                 ps[2 * v].a = q.y;
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < PA; ++u) {
+            for (int u = 0; u < WPA; ++u) {
                 if (i0 + u < hi) ps[u] = p.st[i0 + u];
                 else { ps[u].ub = 0.0f; ps[u].a = -2; }
             }
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
         unsigned amask = 0;
         int nvalid = 0;
 #pragma unroll
-        for (int u = 0; u < PA; ++u) {
+        for (int u = 0; u < WPA; ++u) {
             const int a = ps[u].a;
             if (a == -2) continue;
             ++nvalid;
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
         __syncwarp();
         int pos = incl - na;
 #pragma unroll
-        for (int u = 0; u < PA; ++u) {
+        for (int u = 0; u < WPA; ++u) {
             if ((amask >> u) & 1u) {
                 stg[pos] = make_int2((int)(i0 + u - lo), ps[u].a);
                 ++pos;
@@ -459,9 +461,9 @@ __global__ void __launch_bounds__(WT, DV <= 32 ? 5 : 1) k_mti_w(const IterParams
         if (left > 0) run_batch(cb, left);
     }
     cp_async_wait<0>();
-    const long long t1 = warp_sum_ll(my_changed);
-    const long long t2 = warp_sum_ll(my_skipped);
-    const long long t3 = warp_sum_ll(my_evals);
+    const long long t1 = warp_sum_ll((long long)my_changed);
+    const long long t2 = warp_sum_ll((long long)my_skipped);
+    const long long t3 = warp_sum_ll((long long)my_evals);
     if (lane == 0) {
         atomicAdd(&p.ctr->changed, (unsigned long long)t1);
         atomicAdd(&p.ctr->skipped, (unsigned long long)t2);

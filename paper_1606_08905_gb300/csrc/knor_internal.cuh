@@ -16,11 +16,12 @@ constexpr int PA = 8;
 constexpr int QCAP = NT * PA + NT;
 
 // Warp-autonomous kernels (k_dense_w, k_mti_w): warps per CTA, points per
-// warp chunk of the bound test (PA per lane), capacity of each per-cluster
+// lane and per warp chunk of the bound test, capacity of each per-cluster
 // bucket of k_mti_w (fewer than 32 left plus one append of 32; a power of
 // two, used as a ring) and state chunks in flight per warp.
 constexpr int WPC = 4;
-constexpr int WCH = 32 * PA;
+constexpr int WPA = 4;
+constexpr int WCH = 32 * WPA;
 constexpr int WBCAP = 64;
 constexpr int WSTAGES = 2;
 
