@@ -44,12 +44,6 @@ namespace knor {
 constexpr int BT = 256;            // threads of the scan CTA
 constexpr int B_KMAX = 256;        // largest k of an instance
 constexpr int B_PART_CAP = 2048;   // k x d up to which a unit sums in shared memory
-constexpr int B_QC = 1024;         // points per chunk of the pruned scan's queue
-// sort key of a queued point: (a + 1) * UB + bin of u / s(a) on a
-// quarter-octave scale -- points of one cluster with similar bounds keep
-// nearly the same Clause-2 candidates, so a warp's union stays small
-constexpr int B_UB_SMALLK = 8;     // bins when k <= 128
-constexpr int B_UB_LARGEK = 4;     // bins when k > 128
 
 struct BInst {
     int64_t n;      // points
@@ -72,6 +66,7 @@ struct BCounters {
     unsigned long long changed, skipped, evals, empty;
     unsigned long long bytes;  // algorithmic bytes of the scan: 8 per point, + 4d + 8 per scanned point
     unsigned long long passed; // points Clause 1 cannot skip (counted in dense scans too)
+    unsigned long long overflow; // points that found their cluster's segment full (never expected)
 };
 
 struct BParams {
@@ -100,7 +95,27 @@ struct BParams {
     unsigned long long cond_handle;
     int32_t mti, dry;
     int32_t kd_max, k_max;    // shared-memory layout of the scan
+    int32_t total_k;
+    // sort-segmented MTI scan: per centroid g the segment seg[sbase[g] ..
+    // sbase[g] + cnt[g]) of the points assigned to it, of which acnt[g]
+    // failed Clause 1 this iteration; bdesc: (g, first entry) per batch of
+    // 32, grouped by the instance's width
+    int32_t *seg;
+    int64_t *sbase;
+    unsigned *acnt;
+    int2 *bdesc;
+    unsigned *ctr2;           // [0] units of k_bclause1, [1 + q] batches of width class q,
+                              // [5 + q] batches of class q handed out by k_bmti
+    int64_t boff[4];          // first descriptor of width class q (d = 8, 16, 32, 64)
 };
+
+__host__ __device__ __forceinline__ int width_class(int d) { return d <= 8 ? 0 : (d <= 16 ? 1 : (d <= 32 ? 2 : 3)); }
+
+// An instance whose iteration runs the sort-segmented MTI scan (its points
+// all have a cluster; pruning is on and has been paying).
+__device__ __forceinline__ bool seg_iter(const BParams &p, int i) {
+    return p.mti && !p.dry && p.active[i] && !p.dense[i] && p.iters[i] > 0;
+}
 
 // ------------------------------------------------------------------- scan
 
@@ -147,157 +162,34 @@ __device__ __forceinline__ void full_scan(const unsigned long long (&x)[DV / 2],
     }
 }
 
-// One unit.  Plain Lloyd and points without a centroid yet: thread per
-// point, full scans (every lane runs the same loop).  MTI: the unit is taken
-// in chunks of B_QC points; Clause 1 (u^t = ub + F^t(a) against s(a)) drops
-// most points, the survivors are queued and counting-sorted by their cluster
-// so that a warp's lanes share a row of the half-distance table; each lane
-// tightens u to d(v, c_a) (Clause 3), builds its candidate mask 32 centroids
-// at a time (Clause 2: c survives unless u < 1/2 d(c_a, c)), and the warp
-// evaluates the union of its lanes' masks in index order -- a lane adopts c
-// only if c is in its own mask, exactly as in its own pruned scan.
+// Full scan of a unit's points (iteration 1, plain Lloyd, and MTI
+// instances in dense mode), one point per thread.
 template <int DV>
 __device__ __forceinline__ void scan_unit(const BParams &p, const BInst &I, int64_t lo, int64_t hi,
                                           const float *cent, const float *s_s, const float *F_s, double *part,
-                                          long long *pcnt, int2 *queue, int2 *sorted, int *hist, int *qn,
-                                          bool dense, long long &changed, long long &skipped, long long &evals,
-                                          long long &passed) {
+                                          long long *pcnt, long long &changed, long long &evals, long long &passed) {
     const int k = I.k;
     const float *X = p.X + I.xoff;
     PtState *st = p.st + I.poff;
-    const float *halfD = p.halfD + I.hoff;
     double *D = p.D + I.coff;
     long long *Dc = p.Dcnt + I.koff;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (!p.mti || dense) {
-        for (int64_t i = lo + tid; i < hi; i += BT) {
-            const PtState ps = st[i];
-            const int a = ps.a;
-            // Clause 1 is evaluated (not used): how many points an MTI scan
-            // would have to scan decides the instance's next mode
-            if (p.mti) {
-                bool pass = true;
-                if (a >= 0) pass = !(__fmaf_ru(__fadd_ru(ps.ub, F_s[a]), I.onepk, I.tau) < s_s[a]);
-                passed += pass ? 1 : 0;
-            }
-            unsigned long long x[DV / 2];
-            ldg_x2<DV>(x, X + i * DV);
-            int best;
-            float bd;
-            full_scan<DV>(x, cent, k, best, bd);
-            evals += k;
-            if (!p.dry) commit_point<DV>(I, st, i, a, best, bd, x, F_s, part, pcnt, D, Dc, changed);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += BT) {
+        const PtState ps = st[i];
+        const int a = ps.a;
+        // Clause 1 is evaluated (not used): how many points an MTI scan
+        // would have to scan decides the instance's next mode
+        if (p.mti) {
+            bool pass = true;
+            if (a >= 0) pass = !(__fmaf_ru(__fadd_ru(ps.ub, F_s[a]), I.onepk, I.tau) < s_s[a]);
+            passed += pass ? 1 : 0;
         }
-        return;
-    }
-    for (int64_t c0 = lo; c0 < hi; c0 += B_QC) {
-        const int64_t c1 = min(hi, c0 + (int64_t)B_QC);
-        // ---- Clause 1; survivors into the queue (warp-aggregated appends)
-        const int UB = k <= 128 ? B_UB_SMALLK : B_UB_LARGEK;
-        const int nkey = (k + 1) * UB;
-        if (tid == 0) *qn = 0;
-        for (int c = tid; c < nkey; c += BT) hist[c] = 0;
-        __syncthreads();
-        for (int64_t base = c0; base < c1; base += BT) {
-            const int64_t i = base + tid;
-            bool act = false;
-            int a = -1, key = 0;
-            if (i < c1) {
-                const PtState ps = st[i];
-                a = ps.a;
-                act = true;
-                if (a >= 0) {
-                    const float uu = __fadd_ru(ps.ub, F_s[a]);
-                    act = !(__fmaf_ru(uu, I.onepk, I.tau) < s_s[a]);
-                    const float r = __fdividef(uu, fmaxf(s_s[a], 1e-30f));
-                    key = (a + 1) * UB + min(UB - 1, max(0, (int)(4.0f * __log2f(fmaxf(r, 1.0f)))));
-                }
-                if (!act) ++skipped;
-            }
-            const unsigned m = __ballot_sync(FULL_MASK, act);
-            int pos = 0;
-            if (m) {
-                if (lane == __ffs(m) - 1) pos = atomicAdd(qn, __popc(m));
-                pos = __shfl_sync(FULL_MASK, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
-            }
-            if (act) {
-                queue[pos] = make_int2((int)(i - c0), key); // key 0: no centroid yet
-                atomicAdd(&hist[key], 1);
-            }
-        }
-        __syncthreads();
-        const int n_act = *qn;
-        if (tid == 0) passed += n_act;
-        if (n_act == 0) {
-            __syncthreads();
-            continue;
-        }
-        // ---- counting sort by key
-        if (warp == 0) {
-            int carry = 0;
-            for (int base = 0; base < nkey; base += 32) {
-                const int c = base + lane;
-                const int v = c < nkey ? hist[c] : 0;
-                int incl = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(FULL_MASK, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                if (c < nkey) hist[c] = carry + incl - v; // exclusive start
-                carry += __shfl_sync(FULL_MASK, incl, 31);
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < n_act; e += BT) {
-            const int2 q = queue[e];
-            sorted[atomicAdd(&hist[q.y], 1)] = make_int2(q.x, q.y == 0 ? -1 : q.y / UB - 1);
-        }
-        __syncthreads();
-        // ---- pruned scans, 32 queued points per warp at a time
-        for (int wb = warp * 32; wb < n_act; wb += BT) {
-            const int e = wb + lane;
-            const bool has = e < n_act;
-            const int2 q = has ? sorted[e] : make_int2(0, -2);
-            const int64_t i = c0 + q.x;
-            const int a = q.y;
-            unsigned long long x[DV / 2];
-            if (has) ldg_x2<DV>(x, X + i * DV);
-            else {
-#pragma unroll
-                for (int j = 0; j < DV / 2; ++j) x[j] = 0ULL;
-            }
-            int best = 0;
-            float bd = CUDART_INF_F;
-            const bool anyfull = __any_sync(FULL_MASK, has && a < 0);
-            if (anyfull) {
-                // points without a centroid yet (all full scans, run together)
-                if (has && a < 0) {
-                    full_scan<DV>(x, cent, k, best, bd);
-                    evals += k;
-                }
-            }
-            if (has && a >= 0) {
-                bd = d2_reg<DV>(x, cent + (size_t)a * DV);
-                best = a;
-                ++evals;
-                const float test = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
-                // Clause 2 over a's neighbours sorted by 1/2 d(c_a, c): the
-                // survivors are a prefix of the list, the scan stops at the
-                // first entry above the bound (the argmin with lowest-index
-                // ties does not depend on the evaluation order)
-                const float *hs = halfD + (size_t)a * k;
-                const int32_t *od = p.order + I.hoff + (size_t)a * k;
-                for (int j = 0; j < k - 1; ++j) {
-                    if (test < __ldg(hs + j)) break;
-                    const int c = __ldg(od + j);
-                    const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
-                    ++evals;
-                    if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
-                }
-            }
-            if (has && !p.dry) commit_point<DV>(I, st, i, a, best, bd, x, F_s, part, pcnt, D, Dc, changed);
-        }
-        __syncthreads();
+        unsigned long long x[DV / 2];
+        ldg_x2<DV>(x, X + i * DV);
+        int best;
+        float bd;
+        full_scan<DV>(x, cent, k, best, bd);
+        evals += k;
+        if (!p.dry) commit_point<DV>(I, st, i, a, best, bd, x, F_s, part, pcnt, D, Dc, changed);
     }
 }
 
@@ -312,9 +204,11 @@ __device__ __forceinline__ long long block_sum(long long v, long long *red) {
 }
 
 // Persistent: every CTA takes units from the LPT-ordered list until it is
-// drained.  Per unit: stage the instance's centroids, s and F in shared
-// memory, scan the unit's points (thread per point), merge the unit's delta
-// sums into the instance's (FP64 atomics), add the unit's counters.
+// drained and full-scans the units of the instances that are not in a
+// sort-segmented MTI iteration.  Per unit: stage the instance's centroids, s
+// and F in shared memory, scan the unit's points (thread per point), merge
+// the unit's delta sums into the instance's (FP64 atomics), add the unit's
+// counters.
 __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_unit;
@@ -324,10 +218,6 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
     float *F_s = s_s + p.k_max;
     double *part = reinterpret_cast<double *>(F_s + p.k_max + ((p.kd_max + 2 * p.k_max) & 1));
     long long *pcnt = reinterpret_cast<long long *>(part + min(p.kd_max, B_PART_CAP));
-    int2 *queue = reinterpret_cast<int2 *>(pcnt + p.k_max);
-    int2 *sorted = queue + B_QC;
-    int *hist = reinterpret_cast<int *>(sorted + B_QC);
-    int *qn = hist + (p.k_max + 1) * B_UB_SMALLK;
     const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) s_unit = (int)atomicAdd(p.qctr, 1u);
@@ -336,7 +226,7 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
         __syncthreads();
         if (u >= p.nunits) break;
         const BUnit U = p.units[u];
-        if (!p.active[U.inst]) continue;
+        if (!p.active[U.inst] || seg_iter(p, U.inst)) continue;
         const BInst I = p.inst[U.inst];
         const int kd = I.k * I.d;
         const bool use_part = !p.dry && kd <= B_PART_CAP;
@@ -350,15 +240,14 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
             for (int c = tid; c < I.k; c += BT) pcnt[c] = 0;
         }
         __syncthreads();
-        long long ch = 0, sk = 0, ev = 0, pa = 0;
-        const bool dense = p.mti && p.dense[U.inst];
+        long long ch = 0, ev = 0, pa = 0;
         double *pp = use_part ? part : nullptr;
         long long *pc = use_part ? pcnt : nullptr;
         switch (I.d) {
-        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
-        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
-        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
-        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, queue, sorted, hist, qn, dense, ch, sk, ev, pa); break;
+        case 8: scan_unit<8>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, ev, pa); break;
+        case 16: scan_unit<16>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, ev, pa); break;
+        case 32: scan_unit<32>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, ev, pa); break;
+        default: scan_unit<64>(p, I, U.lo, U.hi, cent, s_s, F_s, pp, pc, ch, ev, pa); break;
         }
         __syncthreads();
         if (use_part) {
@@ -370,19 +259,276 @@ __global__ void __launch_bounds__(BT) k_bscan(const BParams p) {
                 if (pcnt[c] != 0) atomicAdd(reinterpret_cast<unsigned long long *>(Dc + c), (unsigned long long)pcnt[c]);
         }
         ch = block_sum(ch, red);
-        sk = block_sum(sk, red);
         ev = block_sum(ev, red);
         pa = block_sum(pa, red);
         if (tid == 0 && !p.dry) {
             BCounters *b = p.bctr + U.inst;
             const long long np = U.hi - U.lo;
             if (ch) atomicAdd(&b->changed, (unsigned long long)ch);
-            if (sk) atomicAdd(&b->skipped, (unsigned long long)sk);
             if (ev) atomicAdd(&b->evals, (unsigned long long)ev);
             if (pa) atomicAdd(&b->passed, (unsigned long long)pa);
+            atomicAdd(&b->bytes, (unsigned long long)(np * (4LL * I.d + 16)));
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------- sort-segmented MTI scan
+//
+// An MTI iteration of an instance runs in three launches over the whole
+// batch.  k_bclause1 applies Clause 1 to every point and appends the points
+// it cannot skip to the segment of their cluster; k_bbatches cuts every
+// segment into batches of 32; k_bmti scans one batch per warp.  All points
+// of a batch share their cluster a, so the warp walks the row 1/2 d(c_a, .)
+// (sorted ascending) once -- the union of its lanes' Clause 2 survivor sets
+// is the prefix below the largest bound -- and every centroid and table
+// load is a broadcast.  Per point the arithmetic is that of the unit scan.
+
+// Segment bases (exclusive prefix of the cluster counts within each
+// instance) and zero active counts.  One CTA of BT >= k threads per instance.
+__global__ void __launch_bounds__(BT) k_bseg(const BParams p) {
+    __shared__ long long wsum[BT / 32];
+    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const BInst I = p.inst[i];
+    const bool on = seg_iter(p, i);
+    const long long v = (on && tid < I.k) ? p.cnt[I.koff + tid] : 0;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    long long base = 0;
+    for (int ww = 0; ww < w; ++ww) base += wsum[ww];
+    if (tid < I.k) {
+        p.sbase[I.koff + tid] = I.poff + base + incl - v;
+        p.acnt[I.koff + tid] = 0;
+    }
+}
+
+// Clause 1 over the units of the segment instances; warp-aggregated appends
+// (one atomic per cluster present in a warp's 32 points).
+__global__ void __launch_bounds__(BT) k_bclause1(const BParams p) {
+    __shared__ int s_unit;
+    __shared__ long long red[BT / 32];
+    const int tid = threadIdx.x, lane = tid & 31;
+    while (true) {
+        if (tid == 0) s_unit = (int)atomicAdd(p.ctr2, 1u);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= p.nunits) break;
+        const BUnit U = p.units[u];
+        if (!seg_iter(p, U.inst)) continue;
+        const BInst I = p.inst[U.inst];
+        const PtState *st = p.st + I.poff;
+        const float *s_g = p.s + I.koff, *F_g = p.F + I.koff;
+        long long sk = 0, ov = 0;
+        for (int64_t base = U.lo; base < U.hi; base += BT) {
+            const int64_t i = base + tid;
+            bool act = false;
+            int a = 0;
+            if (i < U.hi) {
+                const PtState ps = st[i];
+                a = ps.a;
+                // every point has a cluster here; a point without one
+                // (impossible) is reported, not scanned
+                if (a < 0 || a >= I.k) {
+                    ++ov;
+                } else {
+                    const float uu = __fadd_ru(ps.ub, __ldg(F_g + a)); // u^t = ub + F^t(a)
+                    act = !(__fmaf_ru(uu, I.onepk, I.tau) < __ldg(s_g + a));
+                    if (!act) ++sk;
+                }
+            }
+            const int key = act ? a : -1 - lane;
+            const unsigned grp = __match_any_sync(FULL_MASK, key);
+            if (act) {
+                const int leader = __ffs(grp) - 1;
+                const int g = I.koff + a;
+                unsigned pos = 0;
+                if (lane == leader) pos = atomicAdd(p.acnt + g, (unsigned)__popc(grp));
+                pos = __shfl_sync(grp, pos, leader) + __popc(grp & ((1u << lane) - 1u));
+                // the segment of cluster a has room for the cnt[g] points
+                // assigned to it (and stays inside the instance's range)
+                const int64_t slot = p.sbase[g] + pos;
+                if ((long long)pos < p.cnt[g] && slot < I.poff + I.n) p.seg[slot] = (int32_t)i;
+                else ++ov;
+            }
+        }
+        sk = block_sum(sk, red);
+        ov = block_sum(ov, red);
+        if (tid == 0) {
+            BCounters *b = p.bctr + U.inst;
+            const long long np = U.hi - U.lo;
+            if (sk) atomicAdd(&b->skipped, (unsigned long long)sk);
+            if (ov) atomicAdd(&b->overflow, (unsigned long long)ov);
+            atomicAdd(&b->passed, (unsigned long long)(np - sk));
             atomicAdd(&b->bytes, (unsigned long long)(8 * np + (np - sk) * (4LL * I.d + 8)));
         }
         __syncthreads();
+    }
+}
+
+// Batches of 32 per non-empty segment: (g, first entry), in the region of
+// the instance's width class.  One CTA of BT >= k threads per instance: its
+// batches are contiguous and in cluster order, so that the warps of a CTA of
+// k_bmti, which take consecutive batches, share the instance's centroids and
+// table rows in L1.
+__global__ void __launch_bounds__(BT) k_bbatches(const BParams p) {
+    __shared__ int wsum[BT / 32];
+    __shared__ unsigned s_base;
+    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (!seg_iter(p, i)) return;
+    const BInst I = p.inst[i];
+    const int g = I.koff + tid;
+    int nb = 0;
+    if (tid < I.k) {
+        const long long na = min((long long)p.acnt[g], min(p.cnt[g], (long long)(I.poff + I.n - p.sbase[g])));
+        nb = (int)((na + 31) / 32);
+    }
+    int incl = nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int ww = 0; ww < BT / 32; ++ww) {
+        before += ww < w ? wsum[ww] : 0;
+        total += wsum[ww];
+    }
+    const int q = width_class(I.d);
+    if (tid == 0) s_base = total ? atomicAdd(p.ctr2 + 1 + q, (unsigned)total) : 0u;
+    __syncthreads();
+    int2 *out = p.bdesc + p.boff[q] + s_base + before + incl - nb;
+    for (int j = 0; j < nb; ++j) out[j] = make_int2(g, 32 * j);
+}
+
+// One batch: up to 32 points of the segment of centroid g (instance I,
+// cluster a = g - I.koff), entries [first, first + 32).
+template <int DV>
+__device__ __forceinline__ void seg_batch(const BParams &p, const BInst &I, int inst, int g, int first,
+                                          const float *cent) {
+    const int lane = threadIdx.x & 31;
+    const int k = I.k, a = g - I.koff;
+    const long long na = min((long long)p.acnt[g], min(p.cnt[g], (long long)(I.poff + I.n - p.sbase[g])));
+    const int nb = (int)min((long long)32, na - first);
+    PtState *st = p.st + I.poff;
+    int64_t i = 0;
+    unsigned long long x[DV / 2];
+    float bd = CUDART_INF_F, tst = 0.0f;
+    int best = a;
+    unsigned ev = 0;
+    if (lane < nb) {
+        i = p.seg[p.sbase[g] + first + lane];
+        ldg_x2_stream<DV>(x, p.X + I.xoff + i * DV);
+        // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
+        bd = d2_reg<DV>(x, cent + (size_t)a * DV);
+        ev = 1;
+        tst = __fmaf_ru(bound_up(bd, I.g_up, I.tiny), I.onepk, I.tau);
+    } else {
+#pragma unroll
+        for (int j = 0; j < DV / 2; ++j) x[j] = 0ULL;
+    }
+    // Clause 2 along the sorted row: each lane's survivors are the prefix
+    // of entries not above its bound; the warp stops after the longest
+    // (the argmin with lowest-index ties does not depend on the order).
+    // Four entries per step, scored side by side; a lane adopts an entry
+    // only if it is one of its own survivors.
+    const float tmax = __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(tst) & 0x7fffffffu));
+    const float *hs = p.halfD + I.hoff + (size_t)a * k;
+    const int32_t *od = p.order + I.hoff + (size_t)a * k;
+    float h[4];
+    int c[4];
+    auto fetch = [&](int j, float (&hh)[4], int (&cc)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool in = j + q < k - 1;
+            hh[q] = in ? __ldg(hs + j + q) : CUDART_INF_F;
+            cc[q] = in ? __ldg(od + j + q) : a;
+        }
+    };
+    fetch(0, h, c);
+    for (int j = 0; j < k - 1; j += 4) {
+        if (tmax < h[0]) break;
+        float hn[4];
+        int cn[4];
+        fetch(j + 4, hn, cn); // the next step's entries, in flight during this one
+        float r[4];
+        d2_reg4<DV>(x, cent + (size_t)c[0] * DV, cent + (size_t)c[1] * DV, cent + (size_t)c[2] * DV,
+                    cent + (size_t)c[3] * DV, r);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (lane < nb && !(tst < h[q])) {
+                ++ev;
+                if (r[q] < bd || (r[q] == bd && c[q] < best)) { bd = r[q]; best = c[q]; }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { h[q] = hn[q]; c[q] = cn[q]; }
+    }
+    long long ch = 0;
+    if (lane < nb)
+        commit_point<DV>(I, st, i, a, best, bd, x, p.F + I.koff, nullptr, nullptr, p.D + I.coff,
+                         p.Dcnt + I.koff, ch);
+    unsigned chu = (unsigned)ch;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_xor_sync(FULL_MASK, ev, o);
+        chu += __shfl_xor_sync(FULL_MASK, chu, o);
+    }
+    if (lane == 0) {
+        BCounters *b = p.bctr + inst;
+        atomicAdd(&b->evals, (unsigned long long)ev);
+        if (chu) atomicAdd(&b->changed, (unsigned long long)chu);
+    }
+}
+
+// Persistent, one launch per width class.  A CTA takes B_CHUNK consecutive
+// batches at a time (one atomic), its warps every (BTM / 32)-th of them, so
+// the batches of one instance and neighbouring clusters run on one SM; the
+// centroids of the chunk's first instance are staged in shared memory (a
+// batch of another instance in the same chunk reads them from global).
+constexpr int B_CHUNK = 64;
+constexpr int BTM = 128; // threads of a k_bmti CTA
+template <int DV>
+__global__ void __launch_bounds__(BTM, DV >= 64 ? 3 : (DV >= 32 ? 4 : 5)) k_bmti(const BParams p) {
+    constexpr int q = DV <= 8 ? 0 : (DV <= 16 ? 1 : (DV <= 32 ? 2 : 3));
+    extern __shared__ __align__(16) float cs[];
+    __shared__ unsigned s_chunk;
+    const unsigned nb = p.ctr2[1 + q];
+    const int2 *desc = p.bdesc + p.boff[q];
+    const int w = threadIdx.x >> 5;
+    int staged = -1;
+    while (true) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(p.ctr2 + 5 + q, (unsigned)B_CHUNK);
+        __syncthreads();
+        const unsigned c0 = s_chunk;
+        if (c0 >= nb) break;
+        const unsigned c1 = min(nb, c0 + B_CHUNK);
+        const int i0 = p.cinst[desc[c0].x];
+        if (i0 != staged) {
+            const BInst I0 = p.inst[i0];
+            const float4 *src = reinterpret_cast<const float4 *>(p.C32 + I0.coff);
+            float4 *dst = reinterpret_cast<float4 *>(cs);
+            for (int e = threadIdx.x; e < I0.k * DV / 4; e += BTM) dst[e] = src[e];
+            staged = i0;
+        }
+        __syncthreads();
+        for (unsigned b = c0 + w; b < c1; b += BTM / 32) {
+            const int2 dsc = desc[b];
+            const int inst = p.cinst[dsc.x];
+            const BInst I = p.inst[inst];
+            // two call sites, so that the staged path reads shared memory directly
+            if (inst == staged) seg_batch<DV>(p, I, inst, dsc.x, dsc.y, cs);
+            else seg_batch<DV>(p, I, inst, dsc.x, dsc.y, p.C32 + I.coff);
+        }
+        __syncthreads(); // the staged centroids stay until every warp is done
     }
 }
 
@@ -422,9 +568,9 @@ __global__ void k_breduce(const BParams p) {
 // changed; the run's record (sums over the instances active in it) and the
 // device-side loop condition.  One CTA.
 __global__ void k_bstep(const BParams p, int32_t snapshot) {
-    __shared__ unsigned long long red[4][32];
+    __shared__ unsigned long long red[5][32];
     __shared__ int any_s;
-    unsigned long long ch = 0, sk = 0, ev = 0, em = 0, pts = 0, by = 0;
+    unsigned long long ch = 0, sk = 0, ev = 0, em = 0, pts = 0, by = 0, ov = 0;
     int any = 0;
     if (threadIdx.x == 0) any_s = 0;
     __syncthreads();
@@ -437,6 +583,7 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
             sk += b.skipped;
             ev += b.evals;
             em += b.empty;
+            ov += b.overflow;
             pts += (unsigned long long)p.inst[i].n;
             by += b.bytes;
             if (b.changed == 0) p.active[i] = 0;
@@ -452,7 +599,7 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
                              : 0;
         }
         any |= p.active[i];
-        p.bctr[i] = BCounters{0, 0, 0, 0, 0, 0};
+        p.bctr[i] = BCounters{0, 0, 0, 0, 0, 0, 0};
     }
     if (any) atomicOr(&any_s, 1);
     if (snapshot) {
@@ -464,14 +611,15 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
         sk += __shfl_xor_sync(FULL_MASK, sk, o);
         ev += __shfl_xor_sync(FULL_MASK, ev, o);
         em += __shfl_xor_sync(FULL_MASK, em, o);
+        ov += __shfl_xor_sync(FULL_MASK, ov, o);
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { red[0][w] = ch; red[1][w] = sk; red[2][w] = ev; red[3][w] = em; }
+    if (lane == 0) { red[0][w] = ch; red[1][w] = sk; red[2][w] = ev; red[3][w] = em; red[4][w] = ov; }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    ch = sk = ev = em = 0;
+    ch = sk = ev = em = ov = 0;
     for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
-        ch += red[0][ww]; sk += red[1][ww]; ev += red[2][ww]; em += red[3][ww];
+        ch += red[0][ww]; sk += red[1][ww]; ev += red[2][ww]; em += red[3][ww]; ov += red[4][ww];
     }
     if (!snapshot) return;
     const int it = *p.run_iter;
@@ -483,7 +631,7 @@ __global__ void k_bstep(const BParams p, int32_t snapshot) {
     r.rechecked = 0;
     r.empty = (int32_t)em;
     r.iteration = total;
-    r.violations = 0;
+    r.violations = (long long)ov; // points that found their segment full (never expected)
     p.stats[it] = r;
     *p.run_iter = it + 1;
     *p.total_iter = total;
@@ -619,7 +767,13 @@ struct knor_batch {
     BInst *inst = nullptr;
     BUnit *units = nullptr;
     int32_t nunits = 0;
-    unsigned *qctr = nullptr;
+    unsigned *qctr = nullptr, *ctr2 = nullptr, *acnt = nullptr;
+    int32_t *seg = nullptr;
+    int64_t *sbase = nullptr;
+    int2 *bdesc = nullptr;
+    int grid_c1 = 0, grid_mti[4] = {};
+    size_t smem_mti[4] = {};
+    int64_t boff[4] = {};
     int32_t *active = nullptr, *iters = nullptr, *cinst = nullptr, *flags = nullptr, *dense = nullptr;
     BCounters *bctr = nullptr;
     unsigned long long *work = nullptr;
@@ -663,7 +817,8 @@ knor_status balloc(knor_batch *b, T **p, size_t count) {
 void bfree_all(knor_batch *b) {
     void *bufs[] = {b->X,    b->C32,   b->C32n, b->halfD, b->s,      b->F,     b->st,     b->C0,
                     b->C64,  b->S,     b->D,    b->cnt,   b->Dcnt,   b->changed_last, b->inst, b->units,
-                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx, b->work, b->dense, b->order};
+                    b->qctr, b->active, b->iters, b->cinst, b->flags, b->bctr,  b->stats,  b->d_idx, b->work, b->dense, b->order,
+                    b->ctr2, b->acnt, b->seg, b->sbase, b->bdesc};
     for (void *p : bufs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : b->ev)
@@ -709,6 +864,13 @@ BParams params_of(const knor_batch *b, int dry, unsigned long long cond, const B
     p.dry = dry;
     p.kd_max = b->kd_max;
     p.k_max = b->k_max;
+    p.total_k = b->total_k;
+    p.seg = b->seg;
+    p.sbase = b->sbase;
+    p.acnt = b->acnt;
+    p.bdesc = b->bdesc;
+    p.ctr2 = b->ctr2;
+    for (int q = 0; q < 4; ++q) p.boff[q] = b->boff[q];
     return p;
 }
 
@@ -748,9 +910,23 @@ knor_status enqueue_iter(knor_batch *b, cudaStream_t s, unsigned long long cond,
     const BParams p = params_of(b, 0, cond, b->units, b->nunits);
     auto mark = [&](int i) -> cudaError_t { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     BCUDA(b, cudaMemsetAsync(b->qctr, 0, sizeof(unsigned), s));
+    BCUDA(b, cudaMemsetAsync(b->ctr2, 0, 9 * sizeof(unsigned), s));
     BCUDA(b, mark(0));
     k_bscan<<<b->grid, BT, b->smem, s>>>(p);
     BCUDA(b, cudaGetLastError());
+    if (p.mti) {
+        k_bseg<<<b->m, BT, 0, s>>>(p);
+        BCUDA(b, cudaGetLastError());
+        k_bclause1<<<b->grid_c1, BT, 0, s>>>(p);
+        BCUDA(b, cudaGetLastError());
+        k_bbatches<<<b->m, BT, 0, s>>>(p);
+        BCUDA(b, cudaGetLastError());
+        if (b->grid_mti[0]) k_bmti<8><<<b->grid_mti[0], BTM, b->smem_mti[0], s>>>(p);
+        if (b->grid_mti[1]) k_bmti<16><<<b->grid_mti[1], BTM, b->smem_mti[1], s>>>(p);
+        if (b->grid_mti[2]) k_bmti<32><<<b->grid_mti[2], BTM, b->smem_mti[2], s>>>(p);
+        if (b->grid_mti[3]) k_bmti<64><<<b->grid_mti[3], BTM, b->smem_mti[3], s>>>(p);
+        BCUDA(b, cudaGetLastError());
+    }
     BCUDA(b, mark(1));
     k_breduce<<<b->total_k, 64, 0, s>>>(p);
     BCUDA(b, cudaGetLastError());
@@ -1123,6 +1299,19 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     BC(balloc(b, &b->bctr, (size_t)m));
     BC(balloc(b, &b->work, 2));
     BC(balloc(b, &b->qctr, 1));
+    BC(balloc(b, &b->ctr2, 9));
+    BC(balloc(b, &b->acnt, tk));
+    BC(balloc(b, &b->sbase, tk));
+    if (!b->opts.no_prune) {
+        // descriptor regions per width class: an instance's segments need
+        // at most n / 32 + k batches
+        int64_t cap[4] = {0, 0, 0, 0};
+        for (const BInst &I : b->h_inst) cap[width_class(I.d)] += I.n / 32 + I.k + 1;
+        int64_t off = 0;
+        for (int q = 0; q < 4; ++q) { b->boff[q] = off; off += cap[q]; }
+        BC(balloc(b, &b->seg, (size_t)b->total_n));
+        BC(balloc(b, &b->bdesc, (size_t)off));
+    }
     BC(balloc(b, &b->flags, BF_COUNT));
     BC(balloc(b, &b->stats, kBStatsCap));
     BC(balloc(b, &b->d_idx, (size_t)b->k_max));
@@ -1160,9 +1349,30 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     }
     // scan launch shape
     b->smem = sizeof(float) * ((size_t)b->kd_max + 2 * b->k_max + 1) +
-              sizeof(double) * (size_t)std::min(b->kd_max, B_PART_CAP) + sizeof(long long) * b->k_max +
-              2 * sizeof(int2) * B_QC + sizeof(int) * ((b->k_max + 1) * B_UB_SMALLK + 1) + 16;
+              sizeof(double) * (size_t)std::min(b->kd_max, B_PART_CAP) + sizeof(long long) * b->k_max + 16;
     BCU(cudaFuncSetAttribute(k_bscan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    {
+        int q1 = 1, qm[4] = {1, 1, 1, 1};
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q1, k_bclause1, BT, 0));
+        // k_bmti stages k x d centroids of the largest k of its width class
+        int kmax_w[4] = {0, 0, 0, 0};
+        for (const BInst &I : b->h_inst) kmax_w[width_class(I.d)] = std::max(kmax_w[width_class(I.d)], I.k);
+        const int widths[4] = {8, 16, 32, 64};
+        for (int q = 0; q < 4; ++q) b->smem_mti[q] = sizeof(float) * (size_t)std::max(1, kmax_w[q]) * widths[q];
+        BCU(cudaFuncSetAttribute(k_bmti<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_mti[0]));
+        BCU(cudaFuncSetAttribute(k_bmti<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_mti[1]));
+        BCU(cudaFuncSetAttribute(k_bmti<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_mti[2]));
+        BCU(cudaFuncSetAttribute(k_bmti<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_mti[3]));
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qm[0], k_bmti<8>, BTM, b->smem_mti[0]));
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qm[1], k_bmti<16>, BTM, b->smem_mti[1]));
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qm[2], k_bmti<32>, BTM, b->smem_mti[2]));
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qm[3], k_bmti<64>, BTM, b->smem_mti[3]));
+        b->grid_c1 = b->num_sms * std::max(1, q1);
+        // a width class without instances gets no launch
+        bool has[4] = {false, false, false, false};
+        for (const BInst &I : b->h_inst) has[width_class(I.d)] = true;
+        for (int q = 0; q < 4; ++q) b->grid_mti[q] = has[q] ? b->num_sms * std::max(1, qm[q]) : 0;
+    }
     BC(breset(b));
     BC(autotune(b));
     const std::vector<BUnit> units = make_units(b, b->unit_pts);
@@ -1359,7 +1569,7 @@ knor_status knor_batch_get_profile(knor_batch *b, knor_profile *out, int32_t res
 const char *knor_batch_kernel_name(const knor_batch *b, int32_t kernel) {
     if (!b) return "";
     switch (kernel) {
-    case KNOR_KERNEL_MTI: return "k_bscan";
+    case KNOR_KERNEL_MTI: return "k_bscan + k_bclause1 + k_bmti";
     case KNOR_KERNEL_REDUCE: return "k_breduce";
     case KNOR_KERNEL_TABLE: return "k_bstep + k_btable";
     default: return "";

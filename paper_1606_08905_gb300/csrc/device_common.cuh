@@ -76,6 +76,21 @@ __device__ __forceinline__ void ldg_x2(unsigned long long (&x2)[DV / 2], const f
     }
 }
 
+// The same for rows read once: not kept in L1 (which then holds the data
+// that is reused, such as centroids and table rows).
+template <int DV>
+__device__ __forceinline__ void ldg_x2_stream(unsigned long long (&x2)[DV / 2], const float *row) {
+#pragma unroll
+    for (int j = 0; j < DV; j += 4) {
+        float v0, v1, v2, v3;
+        asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3)
+                     : "l"(row + j));
+        x2[j / 2] = pack2(v0, v1);
+        x2[j / 2 + 1] = pack2(v2, v3);
+    }
+}
+
 // The same from a 32-byte-aligned row (DV a multiple of 8) with 32-byte
 // loads: one request per lane and sector, where 16-byte loads take two.
 template <int DV>
@@ -124,6 +139,43 @@ __device__ __forceinline__ void d2_regN(const unsigned long long (&x2)[DV / 2], 
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) r[q] = fold2(acc[q]);
+}
+
+// d^2 to two centroids anywhere (independent chains, same values as d2_reg).
+template <int DV>
+__device__ __forceinline__ void d2_reg2(const unsigned long long (&x2)[DV / 2], const float *c0, const float *c1,
+                                        float (&r)[2]) {
+    unsigned long long a0 = 0ULL, a1 = 0ULL;
+#pragma unroll
+    for (int j = 0; j < DV; j += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(c0 + j);
+        const float4 w = *reinterpret_cast<const float4 *>(c1 + j);
+        a0 = sqacc2(sub2(x2[j / 2], pack2(v.x, v.y)), a0);
+        a1 = sqacc2(sub2(x2[j / 2], pack2(w.x, w.y)), a1);
+        a0 = sqacc2(sub2(x2[j / 2 + 1], pack2(v.z, v.w)), a0);
+        a1 = sqacc2(sub2(x2[j / 2 + 1], pack2(w.z, w.w)), a1);
+    }
+    r[0] = fold2(a0);
+    r[1] = fold2(a1);
+}
+
+// d^2 to four centroids anywhere (independent chains, same values as d2_reg).
+template <int DV>
+__device__ __forceinline__ void d2_reg4(const unsigned long long (&x2)[DV / 2], const float *c0, const float *c1,
+                                        const float *c2, const float *c3, float (&r)[4]) {
+    const float *cs[4] = {c0, c1, c2, c3};
+    unsigned long long acc[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+#pragma unroll
+    for (int j = 0; j < DV; j += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = *reinterpret_cast<const float4 *>(cs[q] + j);
+            acc[q] = sqacc2(sub2(x2[j / 2], pack2(v.x, v.y)), acc[q]);
+            acc[q] = sqacc2(sub2(x2[j / 2 + 1], pack2(v.z, v.w)), acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = fold2(acc[q]);
 }
 
 // Generic width: the same definition with scalar operations and a runtime d.
