@@ -149,14 +149,24 @@ __device__ __forceinline__ void commit_point(const BInst &I, PtState *st, int64_
         atomicAdd(reinterpret_cast<unsigned long long *>(pcnt ? pcnt + a : Dc + a), (unsigned long long)-1LL);
 }
 
-// Full scan of one point (iteration 1 and plain Lloyd): strict <, so the
-// lowest index wins ties.
+// Full scan of one point (iteration 1 and plain Lloyd): strict <, in index
+// order, so the lowest index wins ties; NC consecutive centroids per step
+// (independent chains, the same values as one at a time).
 template <int DV>
 __device__ __forceinline__ void full_scan(const unsigned long long (&x)[DV / 2], const float *cent, int k,
                                           int &best, float &bd) {
+    constexpr int NC = DV <= 32 ? 4 : 2;
     bd = CUDART_INF_F;
     best = 0;
-    for (int c = 0; c < k; ++c) {
+    int c = 0;
+    for (; c + NC <= k; c += NC) {
+        float r[NC];
+        d2_regN<DV, NC>(x, cent + (size_t)c * DV, r);
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+            if (r[q] < bd) { bd = r[q]; best = c + q; }
+    }
+    for (; c < k; ++c) {
         const float r = d2_reg<DV>(x, cent + (size_t)c * DV);
         if (r < bd) { bd = r; best = c; }
     }
@@ -308,12 +318,17 @@ __global__ void __launch_bounds__(BT) k_bseg(const BParams p) {
     }
 }
 
-// Clause 1 over the units of the segment instances; warp-aggregated appends
-// (one atomic per cluster present in a warp's 32 points).
+// Clause 1 over the units of the segment instances.  Appends are
+// aggregated per CTA: a round of BT x B_C1PA points counts its survivors per
+// cluster in shared memory (each survivor gets its rank there), reserves one
+// range per cluster present with a single global atomic, then writes.
+constexpr int B_C1PA = 4;
 __global__ void __launch_bounds__(BT) k_bclause1(const BParams p) {
     __shared__ int s_unit;
     __shared__ long long red[BT / 32];
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ unsigned hcnt[B_KMAX], hbase[B_KMAX];
+    const int tid = threadIdx.x;
+    for (int c = tid; c < B_KMAX; c += BT) hcnt[c] = 0;
     while (true) {
         if (tid == 0) s_unit = (int)atomicAdd(p.ctr2, 1u);
         __syncthreads();
@@ -326,36 +341,51 @@ __global__ void __launch_bounds__(BT) k_bclause1(const BParams p) {
         const PtState *st = p.st + I.poff;
         const float *s_g = p.s + I.koff, *F_g = p.F + I.koff;
         long long sk = 0, ov = 0;
-        for (int64_t base = U.lo; base < U.hi; base += BT) {
-            const int64_t i = base + tid;
-            bool act = false;
-            int a = 0;
-            if (i < U.hi) {
-                const PtState ps = st[i];
-                a = ps.a;
-                // every point has a cluster here; a point without one
-                // (impossible) is reported, not scanned
-                if (a < 0 || a >= I.k) {
-                    ++ov;
-                } else {
-                    const float uu = __fadd_ru(ps.ub, __ldg(F_g + a)); // u^t = ub + F^t(a)
-                    act = !(__fmaf_ru(uu, I.onepk, I.tau) < __ldg(s_g + a));
-                    if (!act) ++sk;
+        for (int64_t base = U.lo; base < U.hi; base += (int64_t)BT * B_C1PA) {
+            int a[B_C1PA];
+            unsigned rank[B_C1PA];
+#pragma unroll
+            for (int v = 0; v < B_C1PA; ++v) {
+                const int64_t i = base + (int64_t)v * BT + tid;
+                a[v] = -1;
+                if (i < U.hi) {
+                    const PtState ps = st[i];
+                    // every point has a cluster here; a point without one
+                    // (impossible) is reported, not scanned
+                    if (ps.a < 0 || ps.a >= I.k) {
+                        ++ov;
+                    } else {
+                        const float uu = __fadd_ru(ps.ub, __ldg(F_g + ps.a)); // u^t = ub + F^t(a)
+                        if (!(__fmaf_ru(uu, I.onepk, I.tau) < __ldg(s_g + ps.a))) {
+                            a[v] = ps.a;
+                            rank[v] = atomicAdd(&hcnt[ps.a], 1u);
+                        } else {
+                            ++sk;
+                        }
+                    }
                 }
             }
-            const int key = act ? a : -1 - lane;
-            const unsigned grp = __match_any_sync(FULL_MASK, key);
-            if (act) {
-                const int leader = __ffs(grp) - 1;
-                const int g = I.koff + a;
-                unsigned pos = 0;
-                if (lane == leader) pos = atomicAdd(p.acnt + g, (unsigned)__popc(grp));
-                pos = __shfl_sync(grp, pos, leader) + __popc(grp & ((1u << lane) - 1u));
+            __syncthreads();
+            for (int c = tid; c < I.k; c += BT) {
+                const unsigned h = hcnt[c];
+                if (h) {
+                    hbase[c] = atomicAdd(p.acnt + I.koff + c, h);
+                    hcnt[c] = 0; // for the next round, past the barrier below
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < B_C1PA; ++v) {
+                if (a[v] < 0) continue;
+                const int g = I.koff + a[v];
+                const unsigned pos = hbase[a[v]] + rank[v];
                 // the segment of cluster a has room for the cnt[g] points
                 // assigned to it (and stays inside the instance's range)
                 const int64_t slot = p.sbase[g] + pos;
-                if ((long long)pos < p.cnt[g] && slot < I.poff + I.n) p.seg[slot] = (int32_t)i;
-                else ++ov;
+                if ((long long)pos < p.cnt[g] && slot < I.poff + I.n)
+                    p.seg[slot] = (int32_t)(base + (int64_t)v * BT + tid);
+                else
+                    ++ov;
             }
         }
         sk = block_sum(sk, red);
