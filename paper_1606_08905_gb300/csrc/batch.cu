@@ -695,10 +695,12 @@ __global__ void k_btable(const BParams p, int32_t need_table) {
             const float d2 = d2_gen(Cn + (size_t)a * d, Co + (size_t)a * d, d);
             p.F[g] = __fadd_ru(p.F[g], bound_up(d2, I.g_up, I.tiny));
         }
-        // 1/2 d(c_a, c) for c != a, then the row sorted ascending (bitonic,
-        // 256 entries, +inf padded) with its centroid indices; s(a) is the
-        // first entry
-        for (int j = tid; j < B_KMAX; j += blockDim.x) {
+        // 1/2 d(c_a, c) for c != a, then the row sorted ascending (bitonic
+        // over the first P entries, P the power of two >= k - 1; the rest
+        // is +inf padding) with its centroid indices; s(a) is the first entry
+        int P = 1;
+        while (P < k - 1) P <<= 1;
+        for (int j = tid; j < max(P, k); j += blockDim.x) { // every entry written out below
             float h = CUDART_INF_F;
             int c = a;
             if (j < k - 1) {
@@ -710,10 +712,10 @@ __global__ void k_btable(const BParams p, int32_t need_table) {
             hv[j] = h;
             cv[j] = c;
         }
-        for (int size = 2; size <= B_KMAX; size <<= 1) {
+        for (int size = 2; size <= P; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
                 __syncthreads();
-                for (int t = tid; t < B_KMAX / 2; t += blockDim.x) {
+                for (int t = tid; t < P / 2; t += blockDim.x) {
                     const int lo = 2 * t - (t & (stride - 1));
                     const int hi = lo + stride;
                     const bool up = (lo & size) == 0;
