@@ -93,7 +93,9 @@ typedef struct {
     int64_t violations;      /* debug_invariants: MTI bounds found below the true distance,
                                 or (precision forms) points whose assignment differs from a
                                 full FP32 scan; precision forms always: points left without a
-                                new assignment.  Always 0 unless the library is faulty. */
+                                new assignment; batched form always: points that found their
+                                cluster's segment full (the sort-segmented MTI scan).  Always 0
+                                unless the library is faulty. */
 } knor_iter_stats;
 
 /* Creates a context holding a copy of the n x d FP32 points (host or device)
