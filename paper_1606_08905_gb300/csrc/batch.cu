@@ -9,11 +9,15 @@
 // counterpart of the paper's task queue with work stealing ("Parallel Lloyd's
 // Algorithm", NUMA-aware task scheduling): a CTA that finishes early simply
 // takes the next unit, and the costly units are handed out first so the tail
-// is short.  Within a unit every point runs the same MTI test and pruned scan
-// as the single-problem scan (Clauses 1-3 with the rounding slack), so an
-// instance gets exactly the assignments it would get alone from the same
-// centroids; cluster sums move by the deltas of the points that changed
-// cluster (FP64).  K5 (merge + finalize) and K1 (drift, half distances, s)
+// is short.  That kernel full-scans (iteration 1, plain Lloyd, instances in
+// dense mode); an MTI iteration runs sort-segmented over the whole batch
+// instead: Clause 1 on every point appends the survivors to the segment of
+// their cluster, and warps scan batches of 32 survivors of one cluster.
+// Every point runs the same MTI test and pruned scan as in the single-problem
+// scan (Clauses 1-3 with the rounding slack), so an instance gets exactly the
+// assignments it would get alone from the same centroids; cluster sums move
+// by the deltas of the points that changed cluster (FP64).  K5 (merge +
+// finalize) and K1 (drift, half distances, s)
 // are batched launches over all centroids of all active instances; a small
 // bookkeeping kernel masks the instances that converged.  An iteration is one
 // CUDA graph; a run is a graph with a device-side WHILE loop.
