@@ -141,24 +141,6 @@ __device__ __forceinline__ void d2_regN(const unsigned long long (&x2)[DV / 2], 
     for (int q = 0; q < NC; ++q) r[q] = fold2(acc[q]);
 }
 
-// d^2 to two centroids anywhere (independent chains, same values as d2_reg).
-template <int DV>
-__device__ __forceinline__ void d2_reg2(const unsigned long long (&x2)[DV / 2], const float *c0, const float *c1,
-                                        float (&r)[2]) {
-    unsigned long long a0 = 0ULL, a1 = 0ULL;
-#pragma unroll
-    for (int j = 0; j < DV; j += 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(c0 + j);
-        const float4 w = *reinterpret_cast<const float4 *>(c1 + j);
-        a0 = sqacc2(sub2(x2[j / 2], pack2(v.x, v.y)), a0);
-        a1 = sqacc2(sub2(x2[j / 2], pack2(w.x, w.y)), a1);
-        a0 = sqacc2(sub2(x2[j / 2 + 1], pack2(v.z, v.w)), a0);
-        a1 = sqacc2(sub2(x2[j / 2 + 1], pack2(w.z, w.w)), a1);
-    }
-    r[0] = fold2(a0);
-    r[1] = fold2(a1);
-}
-
 // d^2 to four centroids anywhere (independent chains, same values as d2_reg).
 template <int DV>
 __device__ __forceinline__ void d2_reg4(const unsigned long long (&x2)[DV / 2], const float *c0, const float *c1,
