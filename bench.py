@@ -558,7 +558,7 @@ def our_arm(args, wl, world, rank, local):
         prof_recs.extend(recs)
     prof = ctx.profile(reset=True)
     ctx.set_profiling(False)
-    # algorithmic work per launch (see DESIGN.md): dense scan n(4d + 16) bytes;
+    # algorithmic work per launch: dense scan n(4d + 16) bytes;
     # MTI scan 8n + active (4d + 8) bytes with active = n - clause1_skipped;
     # tensor-core scan 2 n k d flops
     peaks, peak_src = measured_peaks()

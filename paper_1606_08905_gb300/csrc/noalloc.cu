@@ -152,7 +152,15 @@ extern "C" knor_status knor_lloyd_step_noalloc(const float *points, int64_t n, i
                          "array (use a context from knor_create instead)");
         return KNOR_ERR_ARG;
     }
-    // every buffer must be device memory: a host pointer would fault the kernel
+    // every buffer must be device memory of the current device: a host
+    // pointer, or memory of another GPU without peer access, would fault the
+    // kernel (and the scratch array looked up below is the current device's)
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        set_global_error("knor_lloyd_step_noalloc: no current CUDA device");
+        return KNOR_ERR_CUDA;
+    }
     const void *bufs[] = {points, centroids, assign_out, sums_out, counts_out};
     for (const void *b : bufs) {
         cudaPointerAttributes at{};
@@ -160,6 +168,10 @@ extern "C" knor_status knor_lloyd_step_noalloc(const float *points, int64_t n, i
             (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
             cudaGetLastError();
             set_global_error("knor_lloyd_step_noalloc: every buffer must be device memory");
+            return KNOR_ERR_ARG;
+        }
+        if (at.type == cudaMemoryTypeDevice && at.device != cur) {
+            set_global_error("knor_lloyd_step_noalloc: a buffer is on another device than the current one");
             return KNOR_ERR_ARG;
         }
     }

@@ -411,15 +411,37 @@ def lloyd_step_noalloc(points, centroids, assign_out, sums_out, counts_out, stre
     allocation (knor_lloyd_step_noalloc): points n x d FP32, centroids k x d
     FP32; fills assign_out (n int32), sums_out (k x d FP64) and counts_out
     (k int64).  For callers that cannot allocate device memory; all tensors
-    must be on the GPU."""
+    must be CUDA tensors on one device.  The C ABI cannot see buffer sizes,
+    so every shape is checked here, before anything is launched."""
+    import torch
+    bufs = {"points": points, "centroids": centroids, "assign_out": assign_out, "sums_out": sums_out,
+            "counts_out": counts_out}
+    for name, t in bufs.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"lloyd_step_noalloc: {name} must be a CUDA tensor")
+    dev = points.device
+    for name, t in bufs.items():
+        if t.device != dev:
+            raise ValueError(f"lloyd_step_noalloc: {name} is on {t.device}, points on {dev}")
+    if points.dim() != 2 or centroids.dim() != 2:
+        raise ValueError("lloyd_step_noalloc: points and centroids must be 2-D")
     n, d = int(points.shape[0]), int(points.shape[1])
     k = int(centroids.shape[0])
+    if int(centroids.shape[1]) != d:
+        raise ValueError(f"lloyd_step_noalloc: centroids are {tuple(centroids.shape)}, points have d = {d}")
+    if assign_out.numel() < n:
+        raise ValueError(f"lloyd_step_noalloc: assign_out holds {assign_out.numel()} < n = {n} entries")
+    if sums_out.numel() < k * d:
+        raise ValueError(f"lloyd_step_noalloc: sums_out holds {sums_out.numel()} < k * d = {k * d} entries")
+    if counts_out.numel() < k:
+        raise ValueError(f"lloyd_step_noalloc: counts_out holds {counts_out.numel()} < k = {k} entries")
     p0, _ = _ptr(points, np.float32)
     p1, _ = _ptr(centroids, np.float32)
     p2, _ = _ptr(assign_out, np.int32)
     p3, _ = _ptr(sums_out, np.float64)
     p4, _ = _ptr(counts_out, np.int64)
-    _check(load().knor_lloyd_step_noalloc(p0, n, d, k, p1, p2, p3, p4, stream or None), None)
+    with torch.cuda.device(dev):
+        _check(load().knor_lloyd_step_noalloc(p0, n, d, k, p1, p2, p3, p4, stream or None), None)
 
 
 def version() -> str:

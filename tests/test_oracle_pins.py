@@ -10,13 +10,14 @@ test_oracle_planted.py compiles such mistakes into throwaway oracle variants
 and checks that these pins reject them.
 """
 import itertools
+import os
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
 import oracle
-from conftest import read_golden
+from conftest import GOLDEN, read_golden
 from paper_1606_08905_gb300 import synth
 
 
@@ -53,6 +54,21 @@ def test_floyd_distinct_in_range_and_uniform():
     expect = trials / 10
     chi2 = sum((c - expect) ** 2 / expect for c in counts.values())
     assert chi2 < 27.9  # 9 dof, p = 0.001
+
+
+def test_floyd_hand_worked_indices():
+    """Pin: Forgy indices worked by hand from the published SplitMix64
+    outputs (tests/golden/floyd_splitmix64.txt), including a repeated draw
+    that must keep j.  This fixes the multiply-shift reduction: a remainder
+    reduction passes the identity and uniformity pins but not this one."""
+    with open(os.path.join(GOLDEN, "floyd_splitmix64.txt")) as fh:
+        rows = [ln.split() for ln in fh if ln.startswith("case ")]
+    assert len(rows) == 8
+    for row in rows:
+        seed, n, k = int(row[1]), int(row[2]), int(row[3])
+        bars = [i for i, v in enumerate(row) if v == "|"]
+        kept = [int(v) for v in row[bars[1] + 1:]]
+        assert list(oracle.forgy_indices(n, k, seed)) == kept, row
 
 
 def test_forgy_rejects_bad_sizes():

@@ -59,3 +59,24 @@ def test_noalloc_rejects_sizes_beyond_the_scratch_array():
     assert e.value.status == knor.KNOR_ERR_ARG and "4096" in str(e.value)
     with pytest.raises(knor.KnorError):  # host buffers are refused, not dereferenced
         knor.lloyd_step_noalloc(X, C[:8].cpu(), a, S[:8], N[:8])
+
+
+def test_noalloc_accepts_the_largest_size():
+    """k (d + 1) = 4096 exactly (d = 63, k = 64): the largest slot stride and
+    shared-memory size the fixed array allows, against the context path."""
+    n, d, k = 30_000, 63, 64
+    X = synth.aniso_mixture(n, d, 16, 77).cuda()
+    with knor.Context(X, k, seed=3, prune=False) as ctx:
+        C32 = torch.as_tensor(ctx.centroids_f32()).cuda()
+        C_before = ctx.centroids()
+        a = torch.empty(n, dtype=torch.int32, device="cuda")
+        S = torch.empty((k, d), dtype=torch.float64, device="cuda")
+        N = torch.empty(k, dtype=torch.int64, device="cuda")
+        knor.lloyd_step_noalloc(X, C32, a, S, N)
+        ctx.iterate()
+        a_ref = ctx.assignments()
+        assert np.array_equal(a.cpu().numpy(), a_ref)
+        Nn = N.cpu().numpy()
+        assert np.array_equal(Nn, np.bincount(a_ref, minlength=k))
+        means = np.where(Nn[:, None] > 0, S.cpu().numpy() / np.maximum(Nn, 1)[:, None], C_before)
+        check_centroids(means, ctx.centroids(), "k (d + 1) = 4096")
