@@ -220,6 +220,17 @@ knor_status knor_lloyd_step_noalloc(const float *points, int64_t n, int32_t d, i
                                     const float *centroids, int32_t *assign_out, double *sums_out,
                                     int64_t *counts_out, void *stream);
 
+/* Measurement helper (the paper has no counterpart: it measures the roof that
+ * the FP32-bound scans are judged against).  Times, with CUDA events on a
+ * private stream of the current device, a kernel that issues only fused
+ * multiply-adds (eight independent chains per thread, 8 CTAs of 256 threads
+ * per SM): kind 0 FP32 fma.rn.f32, 1 packed fma.rn.f32x2 (two FP32 FMAs per
+ * instruction), 2 FP64.  *tflops_out receives the best of three timed runs
+ * after one warm-up, counting 2 flops per FMA; *ms_out (may be NULL) that
+ * run's time.  Allocates nothing on the device.  Errors: KNOR_ERR_ARG (bad
+ * kind or NULL output), KNOR_ERR_CUDA; message from knor_last_error(NULL). */
+knor_status knor_probe_alu(int32_t kind, double *tflops_out, float *ms_out);
+
 /* Message for the last error on this context ("" if none).  Valid until the
  * next call on the context.  ctx may be NULL for errors of knor_create. */
 const char *knor_last_error(const knor_ctx *ctx);

@@ -1,0 +1,572 @@
+// kernels_split.cu -- the MTI iteration's point work as two kernels.
+//
+// k_mti_sel   Clause 1 ("Minimal Triangle Inequality (MTI) Pruning") on the
+//             packed state of every point.  Each warp owns a contiguous range
+//             of points, streams its state, and puts the points that Clause 1
+//             cannot skip into per-cluster buckets in shared memory (rings of
+//             WBCAP local indices); a bucket that reaches 32 points is written
+//             out as one batch record (cluster, count, 32 point indices) to
+//             the warp's own list, and the partial buckets follow at the end.
+//             Nothing but the 8-byte state of a point is read here.
+// k_mti_scan  Clauses 3 and 2 on the records: warp w scans list w in order.
+//             While it scores one batch, the rows of its next batch are
+//             already on their way into the warp's second shared-memory slot
+//             (cp.async), so the row gathers overlap the arithmetic.  The
+//             points of a batch share their cluster a, hence the row of the
+//             k x k table, and their Clause-2 candidate sets are nested, so
+//             the warp walks one union.  New state; the points that changed
+//             cluster go to the warp's change list (point, new and old
+//             cluster).
+// k_mti_delta Phase II by deltas: warp w adds the rows of change list w to
+//             their new clusters and subtracts them from their old ones
+//             (TwoSum pairs in shared memory), rows again double-buffered.
+//
+// Record and change lists are a pure function of the state, and each is
+// processed by one warp in order, so the sums (each CTA adds its warps'
+// accumulators in warp order) do not depend on timing.
+#include "device_common.cuh"
+#include "knor_internal.cuh"
+
+namespace knor {
+namespace {
+
+constexpr int SPW = SP_WPB; // warps per CTA of both kernels
+constexpr int SPT = SPW * 32;
+
+// Contiguous point range of global warp gw of nw, boundaries on multiples of
+// WPA (so that state chunks start 32-byte aligned).
+__device__ __forceinline__ void warp_range(int64_t n, int gw, int nw, int64_t &lo, int64_t &hi) {
+    const int64_t units = (n + WPA - 1) / WPA;
+    lo = min(n, units * gw / nw * WPA);
+    hi = min(n, units * (gw + 1) / nw * WPA);
+}
+
+__device__ __forceinline__ long long sp_warp_sum(long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+} // namespace
+
+// ---------------------------------------------------------------- Clause 1
+
+__global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32_t *mode_dense) {
+    if (*mode_dense != 0) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = p.k;
+    float *s_s = reinterpret_cast<float *>(sm + p.off_s);
+    float *F_s = reinterpret_cast<float *>(sm + p.off_F);
+    for (int c = tid; c < k; c += SPT) { s_s[c] = p.s[c]; F_s[c] = p.F[c]; }
+    unsigned char *wr = sm + p.w_base + w * p.w_stride;
+    int *bk = reinterpret_cast<int *>(wr + p.w_bucket); // (k + 1) rings of WBCAP local indices
+    int *bhead = bk + (k + 1) * WBCAP;
+    int *bcnt = bhead + (k + 1);
+    PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
+    for (int c = lane; c <= k; c += 32) { bhead[c] = 0; bcnt[c] = 0; }
+    __syncthreads();
+    const int gw = blockIdx.x * SPW + w, nw = gridDim.x * SPW;
+    int64_t lo, hi;
+    warp_range(p.n, gw, nw, lo, hi);
+    const int64_t nchunk = (hi - lo + WCH - 1) / WCH;
+    int32_t *rec = p.rec + (size_t)gw * p.rec_cap * SP_REC;
+    int nrec = 0;
+
+    auto prefetch = [&](int stage, int64_t m) {
+        if (m < nchunk) {
+            const int64_t i0 = lo + m * WCH + (int64_t)lane * WPA;
+            if (i0 + WPA <= hi) {
+                const char *src = reinterpret_cast<const char *>(p.st + i0);
+                char *dst = reinterpret_cast<char *>(stbuf + stage * WCH + lane * WPA);
+#pragma unroll
+                for (int v = 0; v < WPA * 8 / 16; ++v) cp_async16(dst + 16 * v, src + 16 * v);
+            }
+        }
+        cp_async_commit();
+    };
+    // Writes the first nb (<= 32) points of bucket cb as the next record.
+    auto emit = [&](int cb, int nb) {
+        int32_t *r = rec + (size_t)nrec * SP_REC;
+        if (lane < nb) r[4 + lane] = (int32_t)(lo + bk[cb * WBCAP + ((bhead[cb] + lane) & (WBCAP - 1))]);
+        __syncwarp(); // every lane has read bhead before lane 0 moves it
+        if (lane == 0) {
+            r[0] = cb;
+            r[1] = nb;
+            bhead[cb] = (bhead[cb] + nb) & (WBCAP - 1);
+            bcnt[cb] -= nb;
+        }
+        __syncwarp();
+        ++nrec;
+    };
+
+    unsigned my_skipped = 0;
+#pragma unroll
+    for (int s = 0; s < WSTAGES - 1; ++s) prefetch(s, s);
+    int stage = 0;
+    for (int64_t m = 0; m < nchunk; ++m) {
+        prefetch((stage + WSTAGES - 1) % WSTAGES, m + WSTAGES - 1);
+        cp_async_wait<WSTAGES - 1>();
+        __syncwarp();
+        const int64_t i0 = lo + m * WCH + (int64_t)lane * WPA;
+        PtState ps[WPA];
+        if (i0 + WPA <= hi) {
+            const int4 *src = reinterpret_cast<const int4 *>(stbuf + stage * WCH + lane * WPA);
+#pragma unroll
+            for (int v = 0; v < WPA / 2; ++v) {
+                const int4 q = src[v];
+                ps[2 * v].ub = __int_as_float(q.x);
+                ps[2 * v].a = q.y;
+                ps[2 * v + 1].ub = __int_as_float(q.z);
+                ps[2 * v + 1].a = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < WPA; ++u) {
+                if (i0 + u < hi) ps[u] = p.st[i0 + u];
+                else { ps[u].ub = 0.0f; ps[u].a = -2; }
+            }
+        }
+        unsigned amask = 0;
+        int nvalid = 0;
+#pragma unroll
+        for (int u = 0; u < WPA; ++u) {
+            const int a = ps[u].a;
+            if (a == -2) continue;
+            ++nvalid;
+            bool act = true;
+            if (a >= 0) {
+                const float uu = __fadd_ru(ps[u].ub, F_s[a]); // u^t = ub + F^t(a)
+                act = !(__fmaf_ru(uu, p.onepk, p.tau) < s_s[a]);
+            }
+            amask |= (act ? 1u : 0u) << u;
+        }
+        const int na = __popc(amask);
+        my_skipped += nvalid - na;
+        int incl = na;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL_MASK, incl, 31);
+        // survivors in point order, staged in the state buffer just read
+        int2 *stg = reinterpret_cast<int2 *>(stbuf + stage * WCH);
+        __syncwarp();
+        int pos = incl - na;
+#pragma unroll
+        for (int u = 0; u < WPA; ++u) {
+            if ((amask >> u) & 1u) {
+                stg[pos] = make_int2((int)(i0 + u - lo), ps[u].a);
+                ++pos;
+            }
+        }
+        __syncwarp();
+        stage = (stage + 1) % WSTAGES;
+        for (int base = 0; base < total; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < total;
+            const int2 ent = valid ? stg[e] : make_int2(0, 0);
+            const int key = valid ? (ent.y < 0 ? k : ent.y) : -1 - lane;
+            const unsigned grp = __match_any_sync(FULL_MASK, key);
+            const int rank = __popc(grp & ((1u << lane) - 1u));
+            int now = 0;
+            if (valid) {
+                const int c0 = bcnt[key];
+                bk[key * WBCAP + ((bhead[key] + c0 + rank) & (WBCAP - 1))] = ent.x;
+                now = c0 + __popc(grp);
+            }
+            __syncwarp();
+            if (valid && rank == 0) bcnt[key] = now;
+            __syncwarp();
+            unsigned fullm = __ballot_sync(FULL_MASK, valid && rank == 0 && now >= 32);
+            while (fullm) {
+                const int leader = __ffs(fullm) - 1;
+                fullm &= fullm - 1;
+                emit(__shfl_sync(FULL_MASK, key, leader), 32);
+            }
+        }
+        __syncwarp();
+    }
+    for (int cb = 0; cb <= k; ++cb) {
+        const int left = bcnt[cb];
+        if (left > 0) emit(cb, left);
+    }
+    cp_async_wait<0>();
+    const long long t = sp_warp_sum((long long)my_skipped);
+    if (lane == 0) {
+        p.rec_cnt[gw] = nrec;
+        atomicAdd(&p.ctr->skipped, (unsigned long long)t);
+    }
+}
+
+// ------------------------------------------------------------ Clauses 2-3
+
+namespace {
+
+// Adds (sign = +1) or subtracts (sign = -1) the staged rows of the lanes with
+// has = true into the warp's TwoSum accumulators, cluster cl of each lane;
+// the rows of a group are taken in lane order, lanes walking the dimensions.
+template <int DV>
+__device__ __forceinline__ void sp_accumulate(const float *rb, int rs, int cl, bool has, float sign, float *acc_hi,
+                                              float *acc_lo, int *cnt) {
+    const int lane = threadIdx.x & 31;
+    unsigned rem = __ballot_sync(FULL_MASK, has);
+    while (rem) {
+        const int c = __shfl_sync(FULL_MASK, cl, __ffs(rem) - 1);
+        const unsigned grp = __ballot_sync(FULL_MASK, has && cl == c);
+        rem &= ~grp;
+        if constexpr (DV <= 32) {
+            constexpr int G = 32 / DV; // members summed side by side
+            const int sub = lane / DV, j = lane % DV;
+            float h = 0.0f, l = 0.0f;
+            unsigned m = grp;
+            int idx = 0;
+            while (m) {
+                const int pl = __ffs(m) - 1;
+                m &= m - 1;
+                if (idx % G == sub) two_sum_reg(h, l, rb[pl * rs + j] * sign);
+                ++idx;
+            }
+#pragma unroll
+            for (int o = DV; o < 32; o <<= 1) {
+                const float h2 = __shfl_xor_sync(FULL_MASK, h, o);
+                const float l2 = __shfl_xor_sync(FULL_MASK, l, o);
+                two_sum_merge(h, l, h2, l2);
+            }
+            if (sub == 0) {
+                float H = acc_hi[c * DV + j], L = acc_lo[c * DV + j];
+                two_sum_merge(H, L, h, l);
+                acc_hi[c * DV + j] = H;
+                acc_lo[c * DV + j] = L;
+            }
+        } else {
+            constexpr int R = DV / 32;
+            float h[R], l[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { h[r] = 0.0f; l[r] = 0.0f; }
+            unsigned m = grp;
+            while (m) {
+                const int pl = __ffs(m) - 1;
+                m &= m - 1;
+#pragma unroll
+                for (int r = 0; r < R; ++r) two_sum_reg(h[r], l[r], rb[pl * rs + lane + 32 * r] * sign);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int e = c * DV + lane + 32 * r;
+                float H = acc_hi[e], L = acc_lo[e];
+                two_sum_merge(H, L, h[r], l[r]);
+                acc_hi[e] = H;
+                acc_lo[e] = L;
+            }
+        }
+        if (lane == 0) cnt[c] += (sign > 0.0f ? 1 : -1) * __popc(grp);
+    }
+}
+
+
+} // namespace
+
+// DV <= 32: up to 5 CTAs (20 warps) per SM; DV = 64: the row slots limit it.
+template <int DV>
+__global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterParams p, const int32_t *mode_dense,
+                                                                    int32_t *nslots, int32_t *fresh) {
+    if (*mode_dense != 0) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = p.k;
+    const int rs = p.sp_rs;
+    float *cent = reinterpret_cast<float *>(sm + p.off_cent);
+    float *halfD = reinterpret_cast<float *>(sm + p.off_halfD);
+    float *F_s = reinterpret_cast<float *>(sm + p.off_F);
+    for (int e = tid; e < k * DV; e += SPT) cent[e] = p.C32[e];
+    for (int e = tid; e < k * k; e += SPT) halfD[e] = p.halfD[e];
+    for (int c = tid; c < k; c += SPT) F_s[c] = p.F[c];
+    const int gw = blockIdx.x * SPW + w;
+    float *slots = reinterpret_cast<float *>(sm + p.sp_off_warp + w * p.sp_warp_stride); // 2 x 32 rows
+    int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32; // (point, new << 16 | old) of the points that changed
+    int nchg = 0;
+    __syncthreads();
+
+    const int32_t *rec = p.rec + (size_t)gw * p.rec_cap * SP_REC;
+    const int nrec = p.rec_cnt[gw];
+    // Record j's header and this lane's point index.
+    auto meta = [&](int j, int &cb, int &nb, int &idx) {
+        if (j < nrec) {
+            const int32_t *r = rec + (size_t)j * SP_REC;
+            cb = r[0];
+            nb = r[1];
+            idx = lane < nb ? r[4 + lane] : 0;
+        } else {
+            cb = 0;
+            nb = 0;
+            idx = 0;
+        }
+    };
+    // The rows of a record into slot `slot`: piece f (16 bytes) of the batch
+    // is row f / (DV/4), so one warp instruction copies whole rows side by
+    // side; then the copies are committed as one group.
+    auto fetch = [&](int slot, int nb, int idx) {
+        constexpr int CH = DV / 4;
+        float *dst = slots + (size_t)slot * 32 * rs;
+        for (int base = 0; base < nb * CH; base += 32) {
+            const int f = base + lane;
+            const int r = min(f / CH, 31);
+            const int ir = __shfl_sync(FULL_MASK, idx, r);
+            if (f < nb * CH) cp_async16(dst + r * rs + (f % CH) * 4, p.X + (int64_t)ir * DV + (f % CH) * 4);
+        }
+        cp_async_commit();
+    };
+
+    unsigned my_evals = 0, my_changed = 0;
+    int cb0, nb0, ix0, cb1, nb1, ix1;
+    meta(0, cb0, nb0, ix0);
+    fetch(0, nb0, ix0);
+    meta(1, cb1, nb1, ix1);
+    for (int j = 0; j < nrec; ++j) {
+        // rows of record j + 1 on their way; the header of j + 2 next
+        fetch((j + 1) & 1, nb1, ix1);
+        int cb2, nb2, ix2;
+        meta(j + 2, cb2, nb2, ix2);
+        cp_async_wait<1>();
+        __syncwarp();
+        const float *rb = slots + (size_t)(j & 1) * 32 * rs;
+        const int a = cb0 == k ? -1 : cb0;
+        const int nb = nb0;
+        int best = -1;
+        unsigned long long xk[DV / 2];
+        float bd = CUDART_INF_F, tst = 0.0f;
+        if (lane < nb) {
+#pragma unroll
+            for (int jj = 0; jj < DV; jj += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(rb + lane * rs + jj);
+                xk[jj / 2] = pack2(v.x, v.y);
+                xk[jj / 2 + 1] = pack2(v.z, v.w);
+            }
+            if (a < 0) {
+                best = 0;
+                for (int c = 0; c < k; ++c) {
+                    const float r = d2_reg<DV>(xk, cent + (size_t)c * DV);
+                    if (r < bd) { bd = r; best = c; }
+                }
+                my_evals += k;
+            } else {
+                // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
+                bd = d2_reg<DV>(xk, cent + (size_t)a * DV);
+                best = a;
+                ++my_evals;
+            }
+            tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
+        }
+        // Clause 2: every centroid c != a with u >= 1/2 d(c_a, c) survives.
+        // The union of the lanes' survivor sets is the set of the largest
+        // bound: lane b tests centroid cw + b against it and the warp walks
+        // the union in index order.  Every lane scores every centroid of the
+        // union: one that its own bound prunes is strictly farther than c_a
+        // in computed FP32 values, so it cannot change the argmin (only the
+        // lanes it survives count it as an evaluation).
+        if (a >= 0) {
+            const float *hrow = halfD + (size_t)a * k;
+            // tst >= 0 (sign bit cleared for -0): its bit pattern orders like the value
+            const float tmax = __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(tst) & 0x7fffffffu));
+            for (int cw = 0; cw < k; cw += 32) {
+                const int cl = cw + lane;
+                unsigned uni = __ballot_sync(FULL_MASK, cl < k && cl != a && !(tmax < hrow[min(cl, k - 1)]));
+                while (uni) {
+                    const int c = cw + __ffs(uni) - 1;
+                    uni &= uni - 1;
+                    if (lane < nb) {
+                        const float r = d2_reg<DV>(xk, cent + (size_t)c * DV);
+                        my_evals += tst < hrow[c] ? 0u : 1u;
+                        if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+                    }
+                }
+            }
+        }
+        bool changed = false;
+        if (lane < nb) {
+            PtState ns;
+            ns.a = best;
+            ns.ub = __fsub_ru(bound_up(bd, p.g_up, p.tiny), F_s[best]);
+            p.st[ix0] = ns;
+            changed = best != a;
+        }
+        // the points that changed cluster, in batch order, for k_mti_delta
+        // (an unassigned point has old cluster 0xFFFF: nothing to subtract)
+        const unsigned cm = __ballot_sync(FULL_MASK, changed);
+        if (changed)
+            chg[nchg + __popc(cm & ((1u << lane) - 1u))] =
+                make_int2(ix0, (int)(((unsigned)best << 16) | ((unsigned)a & 0xFFFFu)));
+        nchg += __popc(cm);
+        my_changed += __popc(cm);
+        __syncwarp(); // slot j & 1 is refilled by the next iteration's fetch
+        cb0 = cb1; nb0 = nb1; ix0 = ix1;
+        cb1 = cb2; nb1 = nb2; ix1 = ix2;
+    }
+    cp_async_wait<0>();
+    const long long t2 = sp_warp_sum((long long)my_evals);
+    if (lane == 0) {
+        p.chg_cnt[gw] = nchg;
+        atomicAdd(&p.ctr->changed, (unsigned long long)my_changed);
+        atomicAdd(&p.ctr->evals, (unsigned long long)t2);
+    }
+}
+
+// ------------------------------------------------------------ delta sums
+
+// Phase II by deltas: warp w takes the change list of scan warp w in order,
+// 32 entries at a time, brings their rows into shared memory (the next group's
+// rows in flight while it adds the current one), adds each row to its new
+// cluster and subtracts it from its old one in its TwoSum accumulators (in
+// shared memory); the CTA adds its warps' accumulators in warp order into its
+// partial slot.  Order and grouping depend only on the lists: deterministic.
+template <int DV>
+__global__ void __launch_bounds__(SPT) k_mti_delta(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
+                                                    int32_t *fresh) {
+    if (*mode_dense != 0) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = p.k;
+    const int rs = p.sp_rs;
+    if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
+    unsigned char *wr = sm + w * p.dl_warp_stride;
+    float *acc_hi = reinterpret_cast<float *>(wr);
+    float *acc_lo = acc_hi + (size_t)k * DV;
+    int *cnt = reinterpret_cast<int *>(acc_lo + (size_t)k * DV);
+    float *slots = reinterpret_cast<float *>(wr + p.dl_off_slots);
+    for (int e = lane; e < 2 * k * DV; e += 32) acc_hi[e] = 0.0f;
+    for (int c = lane; c < k; c += 32) cnt[c] = 0;
+    const int gw = blockIdx.x * SPW + w;
+    const int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32;
+    const int nchg = p.chg_cnt[gw];
+    const int ngrp = (nchg + 31) / 32;
+    auto entry = [&](int g, int &idx, int &cl) {
+        const int e = g * 32 + lane;
+        if (g < ngrp && e < nchg) {
+            const int2 v = chg[e];
+            idx = v.x;
+            cl = v.y;
+        } else {
+            idx = -1;
+            cl = 0;
+        }
+    };
+    auto fetch = [&](int slot, int idx) {
+        constexpr int CH = DV / 4;
+        float *dst = slots + (size_t)slot * 32 * rs;
+        const unsigned have = __ballot_sync(FULL_MASK, idx >= 0);
+        const int nb = __popc(have); // entries are a prefix of the group
+        for (int base = 0; base < nb * CH; base += 32) {
+            const int f = base + lane;
+            const int r = min(f / CH, 31);
+            const int ir = __shfl_sync(FULL_MASK, idx, r);
+            if (f < nb * CH) cp_async16(dst + r * rs + (f % CH) * 4, p.X + (int64_t)ir * DV + (f % CH) * 4);
+        }
+        cp_async_commit();
+    };
+    int i0, c0, i1, c1;
+    entry(0, i0, c0);
+    fetch(0, i0);
+    entry(1, i1, c1);
+    __syncwarp();
+    for (int g = 0; g < ngrp; ++g) {
+        fetch((g + 1) & 1, i1);
+        int i2, c2;
+        entry(g + 2, i2, c2);
+        cp_async_wait<1>();
+        __syncwarp();
+        const float *rb = slots + (size_t)(g & 1) * 32 * rs;
+        const bool has = i0 >= 0;
+        const int cnew = (int)((unsigned)c0 >> 16), cold = c0 & 0xFFFF;
+        sp_accumulate<DV>(rb, rs, cnew, has, 1.0f, acc_hi, acc_lo, cnt);
+        sp_accumulate<DV>(rb, rs, cold, has && cold != 0xFFFF, -1.0f, acc_hi, acc_lo, cnt);
+        __syncwarp(); // slot g & 1 is refilled by the next group's fetch
+        i0 = i1; c0 = c1;
+        i1 = i2; c1 = c2;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    const int kd = k * DV;
+    for (int e = tid; e < kd; e += SPT) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < SPW; ++q) {
+            const float *a = reinterpret_cast<const float *>(sm + q * p.dl_warp_stride);
+            sum += (double)a[e];
+            sum += (double)a[kd + e];
+        }
+        p.part_S[(size_t)e * p.part_stride + blockIdx.x] = sum;
+    }
+    for (int c = tid; c < k; c += SPT) {
+        long long sum = 0;
+#pragma unroll
+        for (int q = 0; q < SPW; ++q)
+            sum += reinterpret_cast<const int *>(sm + q * p.dl_warp_stride + (size_t)2 * kd * 4)[c];
+        p.part_cnt[(size_t)c * p.part_stride + blockIdx.x] = sum;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+cudaError_t mti_sel_attr(int wpb, size_t smem, int *bps) {
+    if (wpb != SPW) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_mti_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_mti_sel, SPT, smem);
+}
+cudaError_t launch_mti_sel(const IterParams &p, int grid, size_t smem, cudaStream_t s, const int32_t *md) {
+    k_mti_sel<<<grid, SPT, smem, s>>>(p, md);
+    return cudaGetLastError();
+}
+
+template <int DV>
+static cudaError_t mti_scan_attr_t(size_t smem, int *bps) {
+    cudaError_t e = cudaFuncSetAttribute(k_mti_scan<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_mti_scan<DV>, SPT, smem);
+}
+template <int DV>
+static cudaError_t mti_scan_launch_t(const IterParams &p, int grid, size_t smem, cudaStream_t s, const int32_t *md,
+                                     int32_t *ns, int32_t *fr) {
+    k_mti_scan<DV><<<grid, SPT, smem, s>>>(p, md, ns, fr);
+    return cudaGetLastError();
+}
+
+#define KNOR_DVSP_SWITCH(dv, FN, ...)                    \
+    switch (dv) {                                        \
+    case 8: return FN<8>(__VA_ARGS__);                   \
+    case 16: return FN<16>(__VA_ARGS__);                 \
+    case 32: return FN<32>(__VA_ARGS__);                 \
+    case 64: return FN<64>(__VA_ARGS__);                 \
+    default: return cudaErrorInvalidValue;               \
+    }
+
+template <int DV>
+static cudaError_t mti_delta_attr_t(size_t smem, int *bps) {
+    cudaError_t e = cudaFuncSetAttribute(k_mti_delta<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_mti_delta<DV>, SPT, smem);
+}
+template <int DV>
+static cudaError_t mti_delta_launch_t(const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                                      const int32_t *md, int32_t *ns, int32_t *fr) {
+    k_mti_delta<DV><<<grid, SPT, smem, s>>>(p, md, ns, fr);
+    return cudaGetLastError();
+}
+
+cudaError_t mti_delta_attr(int dv, size_t smem, int *bps) { KNOR_DVSP_SWITCH(dv, mti_delta_attr_t, smem, bps) }
+cudaError_t launch_mti_delta(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                             const int32_t *md, int32_t *ns, int32_t *fr) {
+    KNOR_DVSP_SWITCH(dv, mti_delta_launch_t, p, grid, smem, s, md, ns, fr)
+}
+
+cudaError_t mti_scan_attr(int dv, int wpb, size_t smem, int *bps) {
+    if (wpb != SPW) return cudaErrorInvalidValue;
+    KNOR_DVSP_SWITCH(dv, mti_scan_attr_t, smem, bps)
+}
+cudaError_t launch_mti_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s, const int32_t *md,
+                            int32_t *ns, int32_t *fr) {
+    KNOR_DVSP_SWITCH(dv, mti_scan_launch_t, p, grid, smem, s, md, ns, fr)
+}
+
+} // namespace knor

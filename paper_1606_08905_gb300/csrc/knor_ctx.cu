@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_set>
@@ -72,6 +73,11 @@ float f32_up(double v) { // smallest float >= v
 } // namespace knor
 
 namespace {
+
+int getenv_int(const char *name, int dflt) {
+    const char *v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
+}
 
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at{};
@@ -131,6 +137,10 @@ struct knor_ctx {
     alignas(64) unsigned char tmXc[128] = {};
     PrecParams pp2{};
     float *wacc = nullptr; // k_mti_w warp accumulators
+    int32_t *rec = nullptr, *rec_cnt = nullptr, *chg_cnt = nullptr; // split MTI scan: batch records
+    int2 *chg = nullptr;                                                // and change lists
+    IterParams ip_sel{};
+    size_t smem_sel = 0;
     float *xdn = nullptr, *rxdn = nullptr; // FP8: norms of x / sigma (else aliases of xn, rxn)
     float *sigma = nullptr;                // FP8: sigma_j, then 1 / sigma_j (d each)
     float *xn = nullptr, *cn = nullptr, *absmax = nullptr;
@@ -194,7 +204,7 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
-                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma,
+                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma, c->rec, c->rec_cnt, c->chg, c->chg_cnt,
                     c->xdn != c->xn ? c->xdn : nullptr, c->rxdn != c->rxn ? c->rxdn : nullptr};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -326,6 +336,62 @@ static size_t plan_layout_warp(const knor_ctx *c, bool mti, IterParams &p) {
     return total;
 }
 
+// Shared-memory layouts of the split MTI scan: k_mti_sel (s and F, then per
+// warp its buckets and state chunks) and k_mti_scan (centroids, k x k table,
+// F, then per warp two row slots and its member counts).  0 when the split
+// does not apply.
+static size_t plan_layout_sel(const knor_ctx *c, IterParams &p) {
+    const int k = c->k;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> int32_t {
+        const size_t o = off;
+        off = (off + bytes + 15) & ~(size_t)15;
+        return (int32_t)o;
+    };
+    p.off_s = take((size_t)k * 4);
+    p.off_F = take((size_t)k * 4);
+    p.w_base = take(0);
+    p.w_bucket = 0;
+    const size_t bucket = (((size_t)(k + 1) * (WBCAP + 2) * 4) + 15) & ~(size_t)15;
+    p.w_state = (int32_t)bucket;
+    p.w_stride = (int32_t)(bucket + (size_t)WSTAGES * WCH * sizeof(PtState));
+    p.sp_wpb = SP_WPB;
+    return off + (size_t)SP_WPB * p.w_stride;
+}
+static size_t plan_layout_scan(const knor_ctx *c, IterParams &p) {
+    const int d = c->d, k = c->k, dv = c->dv;
+    if (dv != 8 && dv != 16 && dv != 32 && dv != 64) return 0;
+    const size_t kd = (size_t)k * d;
+    if (kd * 4 > 32 * 1024 || (size_t)k * k * 4 > 48 * 1024) return 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> int32_t {
+        const size_t o = off;
+        off = (off + bytes + 15) & ~(size_t)15;
+        return (int32_t)o;
+    };
+    p.cent_smem = 1;
+    p.halfD_smem = 1;
+    p.off_cent = take(kd * 4);
+    p.off_halfD = take((size_t)k * k * 4);
+    p.off_F = take((size_t)k * 4);
+    // rows padded by 16 bytes: lane l reads its row at l * (4d + 16) bytes,
+    // so the 8 lanes of a 16-byte shared load hit distinct banks
+    p.sp_rs = d + 4;
+    p.sp_off_warp = take(0);
+    p.sp_off_cnt = 2 * 32 * p.sp_rs * 4;
+    p.sp_warp_stride = (int32_t)((p.sp_off_cnt + (size_t)k * 4 + 15) & ~(size_t)15);
+    p.sp_wpb = SP_WPB;
+    const size_t total = off + (size_t)SP_WPB * p.sp_warp_stride;
+    if (total > 112 * 1024) return 0; // keep at least two CTAs per SM
+    // k_mti_delta: per warp, TwoSum accumulators and counts, then two row slots
+    p.dl_off_slots = (int32_t)(((size_t)2 * kd * 4 + (size_t)k * 4 + 15) & ~(size_t)15);
+    p.dl_warp_stride = (int32_t)(p.dl_off_slots + (size_t)2 * 32 * p.sp_rs * 4);
+    if ((size_t)SP_WPB * p.dl_warp_stride > 200 * 1024) return 0;
+    p.warp_kernels = 3;
+    p.acc_global = 0;
+    return total;
+}
+
 static void fill_common(knor_ctx *c, IterParams &p) {
     p.X = c->X;
     p.n = c->n;
@@ -348,6 +414,7 @@ static void fill_common(knor_ctx *c, IterParams &p) {
     p.tau = std::ldexp(1.0f, -40);
     p.tiny = (float)std::ldexp((double)std::min(c->d, 1 << 20), -149);
     p.mti = c->opts.no_prune ? 0 : 1;
+    p.err = c->flags + F_ERR;
 }
 
 static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
@@ -361,6 +428,15 @@ static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
 
 static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
     int32_t *fl = c->flags;
+    if (c->ip_mti.warp_kernels == 3) {
+        cudaError_t e = launch_mti_sel(c->ip_sel, c->grid_mti, c->smem_sel, s, fl + F_MODE_DENSE);
+        if (e != cudaSuccess) return e;
+        e = launch_mti_scan(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
+                            fl + F_FRESH);
+        if (e != cudaSuccess) return e;
+        return launch_mti_delta(c->dv, c->ip_mti, c->grid_mti, (size_t)SP_WPB * c->ip_mti.dl_warp_stride, s,
+                                fl + F_MODE_DENSE, fl + F_NSLOTS, fl + F_FRESH);
+    }
     if (c->ip_mti.warp_kernels)
         return launch_mti_w(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                             fl + F_FRESH);
@@ -670,9 +746,23 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         const size_t sw = plan_layout_warp(c, false, pw);
         if (sw) { c->ip_dense = pw; c->smem_dense = sw; KCU(dense_w_attr(c->dv, sw, &bd)); }
         else { c->smem_dense = plan_layout(c, false, c->ip_dense); KCU(dense_attr(c->dv, c->smem_dense, &bd)); }
-        IterParams pm{};
-        const size_t sm = plan_layout_warp(c, true, pm);
-        if (sm) { c->ip_mti = pm; c->smem_mti = sm; KCU(mti_w_attr(c->dv, sm, &bm)); }
+        // MTI scan: the split kernels where they fit (KNOR_MTI_KERNEL = 1
+        // selects the one-kernel warp scan instead, for comparisons)
+        IterParams ps{}, pm{};
+        const int choice = getenv_int("KNOR_MTI_KERNEL", 0);
+        const size_t ssc = choice == 0 ? plan_layout_scan(c, ps) : 0;
+        const size_t sm = ssc ? 0 : plan_layout_warp(c, true, pm);
+        if (ssc) {
+            c->ip_mti = ps;
+            c->smem_mti = ssc;
+            KCU(mti_scan_attr(c->dv, SP_WPB, ssc, &bm));
+            c->smem_sel = plan_layout_sel(c, c->ip_sel);
+            int bs = 0, bdl = 0;
+            KCU(mti_sel_attr(SP_WPB, c->smem_sel, &bs));
+            KCU(mti_delta_attr(c->dv, (size_t)SP_WPB * ps.dl_warp_stride, &bdl));
+            if (bs < 1 || bdl < 1) bm = 0;
+        }
+        else if (sm) { c->ip_mti = pm; c->smem_mti = sm; KCU(mti_w_attr(c->dv, sm, &bm)); }
         else { c->smem_mti = plan_layout(c, true, c->ip_mti); KCU(mti_attr(c->dv, c->smem_mti, &bm)); }
     }
     if (bd < 1 || bm < 1) { c->err = "knor_create: kernel does not fit on an SM"; return bail(KNOR_ERR_CUDA); }
@@ -698,10 +788,30 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     KC(dalloc(c, &c->part_cnt, (size_t)k * c->part_stride));
     fill_common(c, c->ip_dense);
     fill_common(c, c->ip_mti);
-    if (c->ip_mti.warp_kernels) {
+    if (c->ip_mti.warp_kernels == 1) {
         // per-warp TwoSum accumulators of k_mti_w (global, warp-private)
         KC(dalloc(c, &c->wacc, (size_t)c->grid_mti * WPC * 2 * kd));
         c->ip_mti.wacc = c->wacc;
+    }
+    if (c->ip_mti.warp_kernels == 3) {
+        // batch records: per warp, one per 32 points of its range plus one
+        // partial bucket per cluster (and the unassigned bucket)
+        const int64_t nw = (int64_t)c->grid_mti * SP_WPB;
+        const int64_t units = (n + WPA - 1) / WPA;
+        const int64_t range = ((units + nw - 1) / nw) * WPA;
+        const int64_t cap = (range + 31) / 32 + k + 1;
+        KC(dalloc(c, &c->rec, (size_t)(nw * cap * SP_REC)));
+        KC(dalloc(c, &c->rec_cnt, (size_t)nw));
+        KC(dalloc(c, &c->chg, (size_t)(nw * cap * 32)));
+        KC(dalloc(c, &c->chg_cnt, (size_t)nw));
+        fill_common(c, c->ip_sel);
+        for (IterParams *q : {&c->ip_mti, &c->ip_sel}) {
+            q->rec = c->rec;
+            q->rec_cnt = c->rec_cnt;
+            q->rec_cap = cap;
+            q->chg = c->chg;
+            q->chg_cnt = c->chg_cnt;
+        }
     }
     c->ip_dense.part_stride = c->part_stride;
     c->ip_mti.part_stride = c->part_stride;
@@ -709,7 +819,9 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     {
         const std::string w = "<" + std::to_string(c->dv) + ">";
         c->kname[KNOR_KERNEL_DENSE] = (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
-        c->kname[KNOR_KERNEL_MTI] = (c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
+        c->kname[KNOR_KERNEL_MTI] =
+            c->ip_mti.warp_kernels == 3 ? "k_mti_sel + k_mti_scan" + w + " + k_mti_delta" + w
+                                        : (c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
         c->kname[KNOR_KERNEL_REDUCE] = "k_reduce";
         c->kname[KNOR_KERNEL_TABLE] = "k_table";
     }
@@ -861,10 +973,8 @@ static knor_status check_timeout(knor_ctx *c) {
 }
 
 static knor_status read_stats(knor_ctx *c, int count, knor_iter_stats *out) {
-    if (c->prec) {
-        knor_status st = check_timeout(c);
-        if (st != KNOR_OK) return st;
-    }
+    knor_status st = check_timeout(c);
+    if (st != KNOR_OK) return st;
     if (count <= 0 || !out) return KNOR_OK;
     KNOR_CUDA(c, cudaMemcpyAsync(c->h_stats, c->stats, sizeof(IterStats) * count, cudaMemcpyDeviceToHost, c->stream));
     KNOR_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -25,6 +25,14 @@ constexpr int WCH = 32 * WPA;
 constexpr int WBCAP = 64;
 constexpr int WSTAGES = 2;
 
+// Split MTI scan: ints per batch record (144 bytes, 16-byte aligned:
+// cluster, count, two unused, 32 point indices).
+constexpr int SP_REC = 36;
+#ifndef KNOR_SP_WPB
+#define KNOR_SP_WPB 4
+#endif
+constexpr int SP_WPB = KNOR_SP_WPB; // warps per CTA of both split kernels
+
 // Per-point MTI state, packed so that the bound test reads 8 bytes per point.
 //   a   assignment (-1 before the first iteration)
 //   ub  u - F[a] rounded up, where u >= d(x, c_a) was exact-plus-rounding when
@@ -87,7 +95,7 @@ struct IterParams {
     int32_t stages;        // row tiles in flight (dense kernel)
     // warp-autonomous kernels: warp w's private region starts at
     // w_base + w * w_stride; offsets below are within that region
-    int32_t warp_kernels;  // 1: k_dense_w / k_mti_w; 0: the CTA kernels
+    int32_t warp_kernels;  // 1: k_dense_w / k_mti_w; 3: the split MTI scan; 0: the CTA kernels
     int32_t w_base, w_stride;
     int32_t w_acc_hi, w_acc_lo, w_cnt, w_tile, w_bucket, w_state;
     // k_mti_w: when non-null, each warp's TwoSum accumulators (hi then lo,
@@ -95,6 +103,26 @@ struct IterParams {
     // instead of shared memory (few points change cluster in an MTI
     // iteration; the freed shared memory holds more warps per SM)
     float *wacc;
+    // split MTI scan: the row stride of a staged batch, in floats (d + 4)
+    int32_t sp_rs;
+    int32_t *err;          // set when a bounded wait gives up (KNOR_ERR_TIMEOUT)
+    // split MTI scan (k_mti_sel + k_mti_scan): per-warp lists of batch
+    // records (SP_REC ints each: cluster, count, 32 point indices, padding),
+    // rec_cap records per warp, rec_cnt[warp] records written; warps per CTA
+    // and the per-warp shared-memory region of the scan (two row slots, then
+    // the warp's member counts)
+    int32_t *rec;
+    int32_t *rec_cnt;
+    int64_t rec_cap;
+    int32_t sp_wpb;
+    int32_t sp_off_warp, sp_warp_stride, sp_off_cnt;
+    // change lists (point, new cluster << 16 | old cluster), 32 * rec_cap
+    // entries per warp, chg_cnt[warp] entries written; the delta kernel's
+    // per-warp shared-memory region (accumulators and counts, then two row
+    // slots at dl_off_slots)
+    int2 *chg;
+    int32_t *chg_cnt;
+    int32_t dl_warp_stride, dl_off_slots;
 };
 
 // Parameters of the reduction / finalize kernels.
@@ -182,6 +210,15 @@ cudaError_t launch_mti_w(int dv, const IterParams &p, int grid, size_t smem, cud
                          const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
 cudaError_t dense_w_attr(int dv, size_t smem, int *blocks_per_sm);
 cudaError_t mti_w_attr(int dv, size_t smem, int *blocks_per_sm);
+// split MTI scan: Clause 1 + batch records, then the scan of the records
+cudaError_t launch_mti_sel(const IterParams &p, int grid, size_t smem, cudaStream_t s, const int32_t *mode_dense);
+cudaError_t mti_sel_attr(int wpb, size_t smem, int *blocks_per_sm);
+cudaError_t launch_mti_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                            const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
+cudaError_t mti_scan_attr(int dv, int wpb, size_t smem, int *blocks_per_sm);
+cudaError_t launch_mti_delta(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                             const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
+cudaError_t mti_delta_attr(int dv, size_t smem, int *blocks_per_sm);
 cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32_t *fresh, cudaStream_t s);
 cudaError_t launch_table(const FinParams &f, int32_t *mode_dense, int need_table, int recompute_every,
                          int always_dense, cudaStream_t s);

@@ -81,6 +81,8 @@ _SIGS = {
     "knor_lloyd_step_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_probe_alu": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_float)]),
     "knor_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "knor_destroy": (None, [ctypes.c_void_p]),
     "knor_version": (ctypes.c_char_p, []),
@@ -442,6 +444,16 @@ def lloyd_step_noalloc(points, centroids, assign_out, sums_out, counts_out, stre
     p4, _ = _ptr(counts_out, np.int64)
     with torch.cuda.device(dev):
         _check(load().knor_lloyd_step_noalloc(p0, n, d, k, p1, p2, p3, p4, stream or None), None)
+
+
+def probe_alu(kind: str) -> tuple[float, float]:
+    """Measured FMA throughput of the current GPU (knor_probe_alu): kind
+    'fp32', 'fp32x2' (packed) or 'fp64'.  Returns (TFLOP/s, ms of the timed
+    kernel)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    _check(load().knor_probe_alu({"fp32": 0, "fp32x2": 1, "fp64": 2}[kind], ctypes.byref(tf), ctypes.byref(ms)),
+           None)
+    return float(tf.value), float(ms.value)
 
 
 def version() -> str:

@@ -57,8 +57,14 @@ def test_noalloc_rejects_sizes_beyond_the_scratch_array():
     with pytest.raises(knor.KnorError) as e:
         knor.lloyd_step_noalloc(X, C, a, S, N)
     assert e.value.status == knor.KNOR_ERR_ARG and "4096" in str(e.value)
-    with pytest.raises(knor.KnorError):  # host buffers are refused, not dereferenced
+    # host buffers are refused, not dereferenced: by the Python wrapper, and
+    # by the C entry point itself when it is called directly
+    with pytest.raises(ValueError):
         knor.lloyd_step_noalloc(X, C[:8].cpu(), a, S[:8], N[:8])
+    Ch = C[:8].cpu().contiguous()
+    st = knor.load().knor_lloyd_step_noalloc(X.data_ptr(), 100, 64, 8, Ch.data_ptr(), a.data_ptr(),
+                                             S.data_ptr(), N.data_ptr(), None)
+    assert st == knor.KNOR_ERR_ARG
 
 
 def test_noalloc_accepts_the_largest_size():
