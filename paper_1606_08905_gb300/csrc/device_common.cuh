@@ -141,6 +141,24 @@ __device__ __forceinline__ void d2_regN(const unsigned long long (&x2)[DV / 2], 
     for (int q = 0; q < NC; ++q) r[q] = fold2(acc[q]);
 }
 
+// d^2 to two centroids anywhere (independent chains, same values as d2_reg).
+template <int DV>
+__device__ __forceinline__ void d2_reg2(const unsigned long long (&x2)[DV / 2], const float *c0, const float *c1,
+                                        float &r0, float &r1) {
+    unsigned long long a0 = 0ULL, a1 = 0ULL;
+#pragma unroll
+    for (int j = 0; j < DV; j += 4) {
+        const float4 v0 = *reinterpret_cast<const float4 *>(c0 + j);
+        const float4 v1 = *reinterpret_cast<const float4 *>(c1 + j);
+        a0 = sqacc2(sub2(x2[j / 2], pack2(v0.x, v0.y)), a0);
+        a1 = sqacc2(sub2(x2[j / 2], pack2(v1.x, v1.y)), a1);
+        a0 = sqacc2(sub2(x2[j / 2 + 1], pack2(v0.z, v0.w)), a0);
+        a1 = sqacc2(sub2(x2[j / 2 + 1], pack2(v1.z, v1.w)), a1);
+    }
+    r0 = fold2(a0);
+    r1 = fold2(a1);
+}
+
 // d^2 to four centroids anywhere (independent chains, same values as d2_reg).
 template <int DV>
 __device__ __forceinline__ void d2_reg4(const unsigned long long (&x2)[DV / 2], const float *c0, const float *c1,

@@ -9,8 +9,8 @@
 //             the warp's own list, and the partial buckets follow at the end.
 //             Nothing but the 8-byte state of a point is read here.
 // k_mti_scan  Clauses 3 and 2 on the records: warp w scans list w in order.
-//             While it scores one batch, the rows of its next batch are
-//             already on their way into the warp's second shared-memory slot
+//             While it scores one batch, the rows of its next two batches
+//             are on their way into the warp's two shared-memory slots
 //             (cp.async), so the row gathers overlap the arithmetic.  The
 //             points of a batch share their cluster a, hence the row of the
 //             k x k table, and their Clause-2 candidate sets are nested, so
@@ -319,15 +319,15 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
     };
 
     unsigned my_evals = 0, my_changed = 0;
-    int cb0, nb0, ix0, cb1, nb1, ix1;
+    // Two batches in flight: the rows of batch j + 2 go into the slot of
+    // batch j as soon as batch j's rows are in registers.
+    int cb0, nb0, ix0, cb1, nb1, ix1, cb2, nb2, ix2;
     meta(0, cb0, nb0, ix0);
     fetch(0, nb0, ix0);
     meta(1, cb1, nb1, ix1);
+    fetch(1, nb1, ix1);
+    meta(2, cb2, nb2, ix2);
     for (int j = 0; j < nrec; ++j) {
-        // rows of record j + 1 on their way; the header of j + 2 next
-        fetch((j + 1) & 1, nb1, ix1);
-        int cb2, nb2, ix2;
-        meta(j + 2, cb2, nb2, ix2);
         cp_async_wait<1>();
         __syncwarp();
         const float *rb = slots + (size_t)(j & 1) * 32 * rs;
@@ -343,6 +343,12 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
                 xk[jj / 2] = pack2(v.x, v.y);
                 xk[jj / 2 + 1] = pack2(v.z, v.w);
             }
+        }
+        __syncwarp(); // every lane has its row: the slot takes batch j + 2
+        fetch(j & 1, nb2, ix2);
+        int cb3, nb3, ix3;
+        meta(j + 3, cb3, nb3, ix3);
+        if (lane < nb) {
             if (a < 0) {
                 best = 0;
                 for (int c = 0; c < k; ++c) {
@@ -372,10 +378,21 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
             for (int cw = 0; cw < k; cw += 32) {
                 const int cl = cw + lane;
                 unsigned uni = __ballot_sync(FULL_MASK, cl < k && cl != a && !(tmax < hrow[min(cl, k - 1)]));
+                // two members per step (independent chains), in index order
                 while (uni) {
                     const int c = cw + __ffs(uni) - 1;
                     uni &= uni - 1;
-                    if (lane < nb) {
+                    if (uni) {
+                        const int c2 = cw + __ffs(uni) - 1;
+                        uni &= uni - 1;
+                        if (lane < nb) {
+                            float r, r2;
+                            d2_reg2<DV>(xk, cent + (size_t)c * DV, cent + (size_t)c2 * DV, r, r2);
+                            my_evals += (tst < hrow[c] ? 0u : 1u) + (tst < hrow[c2] ? 0u : 1u);
+                            if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+                            if (r2 < bd || (r2 == bd && c2 < best)) { bd = r2; best = c2; }
+                        }
+                    } else if (lane < nb) {
                         const float r = d2_reg<DV>(xk, cent + (size_t)c * DV);
                         my_evals += tst < hrow[c] ? 0u : 1u;
                         if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
@@ -399,9 +416,9 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
                 make_int2(ix0, (int)(((unsigned)best << 16) | ((unsigned)a & 0xFFFFu)));
         nchg += __popc(cm);
         my_changed += __popc(cm);
-        __syncwarp(); // slot j & 1 is refilled by the next iteration's fetch
         cb0 = cb1; nb0 = nb1; ix0 = ix1;
         cb1 = cb2; nb1 = nb2; ix1 = ix2;
+        cb2 = cb3; nb2 = nb3; ix2 = ix3;
     }
     cp_async_wait<0>();
     const long long t2 = sp_warp_sum((long long)my_evals);
