@@ -17,6 +17,8 @@
 //             the warp walks one union.  New state; the points that changed
 //             cluster go to the warp's change list (point, new and old
 //             cluster).
+// k_dense_scan  the full scan (plain Lloyd, the first MTI iteration) over the
+//             same warp ranges, appending its changed points to the same lists.
 // k_mti_delta Phase II by deltas: warp w adds the rows of change list w to
 //             their new clusters and subtracts them from their old ones
 //             (TwoSum pairs in shared memory), rows again double-buffered.
@@ -203,67 +205,34 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
 
 namespace {
 
-// Adds (sign = +1) or subtracts (sign = -1) the staged rows of the lanes with
-// has = true into the warp's TwoSum accumulators, cluster cl of each lane;
-// the rows of a group are taken in lane order, lanes walking the dimensions.
+// Adds the staged rows of the lanes with has = true, in lane order, to their
+// new clusters and subtracts them from their old ones (cl: new << 16 | old,
+// old 0xFFFF for none), one row at a time with the lanes walking the
+// dimensions: every (cluster, dimension) accumulator takes its rows in a
+// fixed order.  Member counts move by shared-memory integer atomics.
 template <int DV>
-__device__ __forceinline__ void sp_accumulate(const float *rb, int rs, int cl, bool has, float sign, float *acc_hi,
-                                              float *acc_lo, int *cnt) {
+__device__ __forceinline__ void sp_accumulate_rows(const float *rb, int rs, int cl, bool has, float *acc_hi,
+                                                   float *acc_lo, int *cnt) {
     const int lane = threadIdx.x & 31;
-    unsigned rem = __ballot_sync(FULL_MASK, has);
-    while (rem) {
-        const int c = __shfl_sync(FULL_MASK, cl, __ffs(rem) - 1);
-        const unsigned grp = __ballot_sync(FULL_MASK, has && cl == c);
-        rem &= ~grp;
-        if constexpr (DV <= 32) {
-            constexpr int G = 32 / DV; // members summed side by side
-            const int sub = lane / DV, j = lane % DV;
-            float h = 0.0f, l = 0.0f;
-            unsigned m = grp;
-            int idx = 0;
-            while (m) {
-                const int pl = __ffs(m) - 1;
-                m &= m - 1;
-                if (idx % G == sub) two_sum_reg(h, l, rb[pl * rs + j] * sign);
-                ++idx;
-            }
+    const int cnew = (int)((unsigned)cl >> 16), cold = cl & 0xFFFF;
+    if (has) {
+        atomicAdd(&cnt[cnew], 1);
+        if (cold != 0xFFFF) atomicAdd(&cnt[cold], -1);
+    }
+    for (unsigned m = __ballot_sync(FULL_MASK, has); m; m &= m - 1) {
+        const int pl = __ffs(m) - 1;
+        const int c = __shfl_sync(FULL_MASK, cl, pl);
+        const int cn = (int)((unsigned)c >> 16), co = c & 0xFFFF;
 #pragma unroll
-            for (int o = DV; o < 32; o <<= 1) {
-                const float h2 = __shfl_xor_sync(FULL_MASK, h, o);
-                const float l2 = __shfl_xor_sync(FULL_MASK, l, o);
-                two_sum_merge(h, l, h2, l2);
-            }
-            if (sub == 0) {
-                float H = acc_hi[c * DV + j], L = acc_lo[c * DV + j];
-                two_sum_merge(H, L, h, l);
-                acc_hi[c * DV + j] = H;
-                acc_lo[c * DV + j] = L;
-            }
-        } else {
-            constexpr int R = DV / 32;
-            float h[R], l[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) { h[r] = 0.0f; l[r] = 0.0f; }
-            unsigned m = grp;
-            while (m) {
-                const int pl = __ffs(m) - 1;
-                m &= m - 1;
-#pragma unroll
-                for (int r = 0; r < R; ++r) two_sum_reg(h[r], l[r], rb[pl * rs + lane + 32 * r] * sign);
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int e = c * DV + lane + 32 * r;
-                float H = acc_hi[e], L = acc_lo[e];
-                two_sum_merge(H, L, h[r], l[r]);
-                acc_hi[e] = H;
-                acc_lo[e] = L;
+        for (int j = lane; j < (DV < 32 ? 32 : DV); j += 32) {
+            if (DV >= 32 || j < DV) {
+                const float x = rb[pl * rs + j];
+                two_sum_acc(&acc_hi[cn * DV + j], &acc_lo[cn * DV + j], x);
+                if (co != 0xFFFF) two_sum_acc(&acc_hi[co * DV + j], &acc_lo[co * DV + j], -x);
             }
         }
-        if (lane == 0) cnt[c] += (sign > 0.0f ? 1 : -1) * __popc(grp);
     }
 }
-
 
 } // namespace
 
@@ -429,6 +398,116 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
     }
 }
 
+// --------------------------------------------------------------- dense scan
+
+// Every point scans every centroid (plain Lloyd, the first MTI iteration):
+// warp w takes the same range as k_mti_sel's warp w, DS_P x 32 rows per tile
+// (double-buffered with cp.async), DS_P points per lane (lane l has rows l,
+// l + 32, ...), so each centroid read from shared memory serves DS_P
+// distances, two centroids per step; writes the new state and appends the
+// points that changed cluster to change list w, in point order, for
+// k_mti_delta.
+constexpr int DS_P = KNOR_DS_P;
+
+template <int DV>
+__global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const int32_t *mode_dense) {
+    if (*mode_dense == 0) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = p.k;
+    const int rs = p.sp_rs;
+    constexpr int TR = 32 * DS_P; // rows per tile
+    float *cent = reinterpret_cast<float *>(sm + p.off_cent);
+    float *F_s = reinterpret_cast<float *>(sm + p.off_F);
+    for (int e = tid; e < k * DV; e += SPT) cent[e] = p.C32[e];
+    for (int c = tid; c < k; c += SPT) F_s[c] = p.F[c];
+    float *tiles = reinterpret_cast<float *>(sm + p.sp_off_warp + w * p.sp_warp_stride); // 2 x TR rows
+    __syncthreads();
+    const int gw = blockIdx.x * SPW + w, nw = gridDim.x * SPW;
+    int64_t lo, hi;
+    warp_range(p.n, gw, nw, lo, hi);
+    const int64_t ntile = (hi - lo + TR - 1) / TR;
+    int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32;
+    int nchg = 0;
+    auto load_tile = [&](int slot, int64_t t) {
+        if (t < ntile) {
+            constexpr int CH = DV / 4;
+            const int64_t base = lo + t * TR;
+            const int rows = (int)min((int64_t)TR, hi - base);
+            float *dst = tiles + (size_t)slot * TR * rs;
+            const float *src = p.X + base * DV;
+            for (int f = lane; f < rows * CH; f += 32) cp_async16(dst + (f / CH) * rs + (f % CH) * 4, src + (size_t)f * 4);
+        }
+        cp_async_commit();
+    };
+    unsigned my_changed = 0;
+    load_tile(0, 0);
+    for (int64_t t = 0; t < ntile; ++t) {
+        load_tile((int)((t + 1) & 1), t + 1);
+        cp_async_wait<1>();
+        __syncwarp();
+        const int64_t base = lo + t * TR;
+        const int rows = (int)min((int64_t)TR, hi - base);
+        const float *tl = tiles + (size_t)(t & 1) * TR * rs;
+        // rows past the end compute on row 0 of the tile and are dropped
+        unsigned long long x2[DS_P][DV / 2];
+        float bd[DS_P];
+        int best[DS_P], olda[DS_P];
+#pragma unroll
+        for (int q = 0; q < DS_P; ++q) {
+            const int r = q * 32 + lane;
+            // the old assignment is loaded here, so its latency hides under the scan
+            olda[q] = r < rows ? p.st[base + r].a : -1;
+            load_x2<DV>(x2[q], tl + (r < rows ? r : 0) * rs);
+            bd[q] = CUDART_INF_F;
+            best[q] = 0;
+        }
+        int c = 0;
+        for (; c + 2 <= k; c += 2) {
+#pragma unroll
+            for (int q = 0; q < DS_P; ++q) {
+                float r0, r1;
+                d2_reg2<DV>(x2[q], cent + (size_t)c * DV, cent + (size_t)(c + 1) * DV, r0, r1);
+                if (r0 < bd[q]) { bd[q] = r0; best[q] = c; }
+                if (r1 < bd[q]) { bd[q] = r1; best[q] = c + 1; }
+            }
+        }
+        for (; c < k; ++c) {
+#pragma unroll
+            for (int q = 0; q < DS_P; ++q) {
+                const float r = d2_reg<DV>(x2[q], cent + (size_t)c * DV);
+                if (r < bd[q]) { bd[q] = r; best[q] = c; }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < DS_P; ++q) {
+            const int r = q * 32 + lane;
+            const int64_t i = base + r;
+            bool changed = false;
+            if (r < rows) {
+                PtState ns;
+                ns.a = best[q];
+                ns.ub = p.mti ? __fsub_ru(bound_up(bd[q], p.g_up, p.tiny), F_s[best[q]]) : 0.0f;
+                p.st[i] = ns;
+                changed = olda[q] != best[q];
+            }
+            const unsigned cm = __ballot_sync(FULL_MASK, changed);
+            if (changed)
+                chg[nchg + __popc(cm & ((1u << lane) - 1u))] =
+                    make_int2((int)i, (int)(((unsigned)best[q] << 16) | ((unsigned)olda[q] & 0xFFFFu)));
+            nchg += __popc(cm);
+            my_changed += __popc(cm);
+        }
+        __syncwarp(); // the tile's slot is refilled two steps on
+    }
+    cp_async_wait<0>();
+    if (lane == 0) {
+        p.chg_cnt[gw] = nchg;
+        atomicAdd(&p.ctr->changed, (unsigned long long)my_changed);
+        atomicAdd(&p.ctr->evals, (unsigned long long)((hi - lo) * (int64_t)k));
+    }
+}
+
 // ------------------------------------------------------------ delta sums
 
 // Phase II by deltas: warp w takes the change list of scan warp w in order,
@@ -440,7 +519,7 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
 template <int DV>
 __global__ void __launch_bounds__(SPT) k_mti_delta(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
                                                     int32_t *fresh) {
-    if (*mode_dense != 0) return;
+    if (*mode_dense != 0 && !p.dl_dense) return; // a dense scan that sums for itself ran
     extern __shared__ __align__(16) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int k = p.k;
@@ -493,10 +572,7 @@ __global__ void __launch_bounds__(SPT) k_mti_delta(const IterParams p, const int
         cp_async_wait<1>();
         __syncwarp();
         const float *rb = slots + (size_t)(g & 1) * 32 * rs;
-        const bool has = i0 >= 0;
-        const int cnew = (int)((unsigned)c0 >> 16), cold = c0 & 0xFFFF;
-        sp_accumulate<DV>(rb, rs, cnew, has, 1.0f, acc_hi, acc_lo, cnt);
-        sp_accumulate<DV>(rb, rs, cold, has && cold != 0xFFFF, -1.0f, acc_hi, acc_lo, cnt);
+        sp_accumulate_rows<DV>(rb, rs, c0, i0 >= 0, acc_hi, acc_lo, cnt);
         __syncwarp(); // slot g & 1 is refilled by the next group's fetch
         i0 = i1; c0 = c1;
         i1 = i2; c1 = c2;
@@ -569,6 +645,24 @@ static cudaError_t mti_delta_launch_t(const IterParams &p, int grid, size_t smem
                                       const int32_t *md, int32_t *ns, int32_t *fr) {
     k_mti_delta<DV><<<grid, SPT, smem, s>>>(p, md, ns, fr);
     return cudaGetLastError();
+}
+
+template <int DV>
+static cudaError_t dense_scan_attr_t(size_t smem, int *bps) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_scan<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_dense_scan<DV>, SPT, smem);
+}
+template <int DV>
+static cudaError_t dense_scan_launch_t(const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                                       const int32_t *md) {
+    k_dense_scan<DV><<<grid, SPT, smem, s>>>(p, md);
+    return cudaGetLastError();
+}
+cudaError_t dense_scan_attr(int dv, size_t smem, int *bps) { KNOR_DVSP_SWITCH(dv, dense_scan_attr_t, smem, bps) }
+cudaError_t launch_dense_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                              const int32_t *md) {
+    KNOR_DVSP_SWITCH(dv, dense_scan_launch_t, p, grid, smem, s, md)
 }
 
 cudaError_t mti_delta_attr(int dv, size_t smem, int *bps) { KNOR_DVSP_SWITCH(dv, mti_delta_attr_t, smem, bps) }

@@ -139,8 +139,10 @@ struct knor_ctx {
     float *wacc = nullptr; // k_mti_w warp accumulators
     int32_t *rec = nullptr, *rec_cnt = nullptr, *chg_cnt = nullptr; // split MTI scan: batch records
     int2 *chg = nullptr;                                                // and change lists
-    IterParams ip_sel{};
+    IterParams ip_sel{}, ip_delta{};
     size_t smem_sel = 0;
+    bool mti_split = false, dense_split = false; // the split kernels run the MTI / dense scans
+    int grid_split = 0;
     float *xdn = nullptr, *rxdn = nullptr; // FP8: norms of x / sigma (else aliases of xn, rxn)
     float *sigma = nullptr;                // FP8: sigma_j, then 1 / sigma_j (d each)
     float *xn = nullptr, *cn = nullptr, *absmax = nullptr;
@@ -419,6 +421,7 @@ static void fill_common(knor_ctx *c, IterParams &p) {
 
 static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
     int32_t *fl = c->flags;
+    if (c->dense_split) return launch_dense_scan(c->dv, c->ip_dense, c->grid_split, c->smem_dense, s, fl + F_MODE_DENSE);
     if (c->ip_dense.warp_kernels)
         return launch_dense_w(c->dv, c->ip_dense, c->grid_dense, c->smem_dense, s, fl + F_MODE_DENSE,
                               fl + F_NSLOTS, fl + F_FRESH);
@@ -428,20 +431,26 @@ static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
 
 static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
     int32_t *fl = c->flags;
-    if (c->ip_mti.warp_kernels == 3) {
-        cudaError_t e = launch_mti_sel(c->ip_sel, c->grid_mti, c->smem_sel, s, fl + F_MODE_DENSE);
+    if (c->mti_split) {
+        cudaError_t e = launch_mti_sel(c->ip_sel, c->grid_split, c->smem_sel, s, fl + F_MODE_DENSE);
         if (e != cudaSuccess) return e;
-        e = launch_mti_scan(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
-                            fl + F_FRESH);
-        if (e != cudaSuccess) return e;
-        return launch_mti_delta(c->dv, c->ip_mti, c->grid_mti, (size_t)SP_WPB * c->ip_mti.dl_warp_stride, s,
-                                fl + F_MODE_DENSE, fl + F_NSLOTS, fl + F_FRESH);
+        return launch_mti_scan(c->dv, c->ip_mti, c->grid_split, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
+                               fl + F_FRESH);
     }
     if (c->ip_mti.warp_kernels)
         return launch_mti_w(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                             fl + F_FRESH);
     return launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                       fl + F_FRESH);
+}
+
+// Phase II from the change lists of the split scans (a no-op in a dense
+// iteration whose scan summed for itself).
+static cudaError_t scan_delta(knor_ctx *c, cudaStream_t s) {
+    if (!c->mti_split && !c->dense_split) return cudaSuccess;
+    int32_t *fl = c->flags;
+    return launch_mti_delta(c->dv, c->ip_delta, c->grid_split, (size_t)SP_WPB * c->ip_delta.dl_warp_stride, s,
+                            fl + F_MODE_DENSE, fl + F_NSLOTS, fl + F_FRESH);
 }
 
 // The precision form's iteration: BF16 centroids, tensor-core scan with
@@ -496,6 +505,7 @@ static knor_status enqueue_iteration(knor_ctx *c, cudaStream_t s, unsigned long 
     }
     KNOR_CUDA(c, scan_dense(c, s));
     if (!c->opts.no_prune) KNOR_CUDA(c, scan_mti(c, s));
+    KNOR_CUDA(c, scan_delta(c, s));
     KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
     FinParams f = c->fp;
     f.snapshot = 1;
@@ -544,11 +554,13 @@ static knor_status profiled_iteration(knor_ctx *c) {
     if (dense) {
         KNOR_CUDA(c, cudaEventRecord(c->ev[0], s));
         KNOR_CUDA(c, scan_dense(c, s));
+        KNOR_CUDA(c, scan_delta(c, s));
         KNOR_CUDA(c, cudaEventRecord(c->ev[1], s));
         used[KNOR_KERNEL_DENSE] = true;
     } else {
         KNOR_CUDA(c, cudaEventRecord(c->ev[2], s));
         KNOR_CUDA(c, scan_mti(c, s));
+        KNOR_CUDA(c, scan_delta(c, s));
         KNOR_CUDA(c, cudaEventRecord(c->ev[3], s));
         used[KNOR_KERNEL_MTI] = true;
     }
@@ -742,31 +754,48 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     c->dv = supported_dv(d);
     int bd = 0, bm = 0;
     {
-        IterParams pw{};
-        const size_t sw = plan_layout_warp(c, false, pw);
-        if (sw) { c->ip_dense = pw; c->smem_dense = sw; KCU(dense_w_attr(c->dv, sw, &bd)); }
-        else { c->smem_dense = plan_layout(c, false, c->ip_dense); KCU(dense_attr(c->dv, c->smem_dense, &bd)); }
-        // MTI scan: the split kernels where they fit (KNOR_MTI_KERNEL = 1
-        // selects the one-kernel warp scan instead, for comparisons)
-        IterParams ps{}, pm{};
+        // The split kernels (per-warp ranges, change lists, k_mti_delta)
+        // where they fit: the MTI scan (unless KNOR_MTI_KERNEL = 1 selects the
+        // one-kernel warp scan, for comparisons) and the dense scan (unless
+        // full_recompute_every asks for sums rebuilt from every point).
+        IterParams ps{};
         const int choice = getenv_int("KNOR_MTI_KERNEL", 0);
-        const size_t ssc = choice == 0 ? plan_layout_scan(c, ps) : 0;
-        const size_t sm = ssc ? 0 : plan_layout_warp(c, true, pm);
+        const size_t ssc = !tc_form ? plan_layout_scan(c, ps) : 0;
+        int bsplit = 0;
         if (ssc) {
-            c->ip_mti = ps;
-            c->smem_mti = ssc;
-            KCU(mti_scan_attr(c->dv, SP_WPB, ssc, &bm));
-            c->smem_sel = plan_layout_sel(c, c->ip_sel);
             int bs = 0, bdl = 0;
+            KCU(mti_scan_attr(c->dv, SP_WPB, ssc, &bsplit));
+            c->smem_sel = plan_layout_sel(c, c->ip_sel);
             KCU(mti_sel_attr(SP_WPB, c->smem_sel, &bs));
             KCU(mti_delta_attr(c->dv, (size_t)SP_WPB * ps.dl_warp_stride, &bdl));
-            if (bs < 1 || bdl < 1) bm = 0;
+            if (bs < 1 || bdl < 1) bsplit = 0;
         }
+        c->mti_split = bsplit > 0 && choice == 0 && !o.no_prune;
+        c->dense_split = bsplit > 0 && o.full_recompute_every == 0;
+        IterParams pw{}, pm{};
+        if (c->dense_split) {
+            // the dense scan's warps stage DS_ROWS-row tiles, double-buffered
+            c->ip_dense = ps;
+            c->ip_dense.sp_warp_stride = 2 * DS_ROWS * ps.sp_rs * 4;
+            c->smem_dense = (size_t)ps.sp_off_warp + (size_t)SP_WPB * c->ip_dense.sp_warp_stride;
+            KCU(dense_scan_attr(c->dv, c->smem_dense, &bd));
+            if (bd < 1) c->dense_split = false;
+        }
+        if (!c->dense_split) {
+            const size_t sw = plan_layout_warp(c, false, pw);
+            if (sw) { c->ip_dense = pw; c->smem_dense = sw; KCU(dense_w_attr(c->dv, sw, &bd)); }
+            else { c->smem_dense = plan_layout(c, false, c->ip_dense); KCU(dense_attr(c->dv, c->smem_dense, &bd)); }
+        }
+        const size_t sm = c->mti_split ? 0 : plan_layout_warp(c, true, pm);
+        if (c->mti_split) { c->ip_mti = ps; c->smem_mti = ssc; bm = bsplit; }
         else if (sm) { c->ip_mti = pm; c->smem_mti = sm; KCU(mti_w_attr(c->dv, sm, &bm)); }
         else { c->smem_mti = plan_layout(c, true, c->ip_mti); KCU(mti_attr(c->dv, c->smem_mti, &bm)); }
+        c->grid_split = bsplit * c->num_sms;
     }
     if (bd < 1 || bm < 1) { c->err = "knor_create: kernel does not fit on an SM"; return bail(KNOR_ERR_CUDA); }
-    c->grid_dense = bd * c->num_sms;
+    // (the dense split scan runs on the split grid, in waves if fewer of its
+    // CTAs fit on an SM)
+    c->grid_dense = c->dense_split ? c->grid_split : bd * c->num_sms;
     c->grid_mti = bm * c->num_sms;
     // Both scans use the same accumulation mode: per-CTA partial slots, or,
     // when k x d sums do not fit in shared memory, one slot updated by FP64
@@ -776,6 +805,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         // the warp kernels always write per-CTA slots: use the CTA kernels for both
         c->ip_dense = IterParams{};
         c->ip_mti = IterParams{};
+        c->mti_split = c->dense_split = false;
         c->smem_dense = plan_layout(c, false, c->ip_dense);
         c->smem_mti = plan_layout(c, true, c->ip_mti);
         KCU(dense_attr(c->dv, c->smem_dense, &bd));
@@ -793,35 +823,42 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, &c->wacc, (size_t)c->grid_mti * WPC * 2 * kd));
         c->ip_mti.wacc = c->wacc;
     }
-    if (c->ip_mti.warp_kernels == 3) {
-        // batch records: per warp, one per 32 points of its range plus one
-        // partial bucket per cluster (and the unassigned bucket)
-        const int64_t nw = (int64_t)c->grid_mti * SP_WPB;
+    if (c->mti_split || c->dense_split) {
+        // per warp of the split grid: change lists with room for every point
+        // of its range, and (MTI) batch records, one per 32 points of the
+        // range plus one partial bucket per cluster and the unassigned one
+        const int64_t nw = (int64_t)c->grid_split * SP_WPB;
         const int64_t units = (n + WPA - 1) / WPA;
         const int64_t range = ((units + nw - 1) / nw) * WPA;
         const int64_t cap = (range + 31) / 32 + k + 1;
-        KC(dalloc(c, &c->rec, (size_t)(nw * cap * SP_REC)));
-        KC(dalloc(c, &c->rec_cnt, (size_t)nw));
+        if (c->mti_split) {
+            KC(dalloc(c, &c->rec, (size_t)(nw * cap * SP_REC)));
+            KC(dalloc(c, &c->rec_cnt, (size_t)nw));
+        }
         KC(dalloc(c, &c->chg, (size_t)(nw * cap * 32)));
         KC(dalloc(c, &c->chg_cnt, (size_t)nw));
         fill_common(c, c->ip_sel);
-        for (IterParams *q : {&c->ip_mti, &c->ip_sel}) {
+        c->ip_delta = c->mti_split ? c->ip_mti : c->ip_dense;
+        for (IterParams *q : {&c->ip_mti, &c->ip_sel, &c->ip_dense, &c->ip_delta}) {
             q->rec = c->rec;
             q->rec_cnt = c->rec_cnt;
             q->rec_cap = cap;
             q->chg = c->chg;
             q->chg_cnt = c->chg_cnt;
+            q->dl_dense = c->dense_split ? 1 : 0;
         }
     }
     c->ip_dense.part_stride = c->part_stride;
     c->ip_mti.part_stride = c->part_stride;
+    c->ip_delta.part_stride = c->part_stride;
     c->ip_dense.acc_global = c->ip_mti.acc_global = acc_global;
     {
         const std::string w = "<" + std::to_string(c->dv) + ">";
-        c->kname[KNOR_KERNEL_DENSE] = (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
+        c->kname[KNOR_KERNEL_DENSE] = c->dense_split ? "k_dense_scan" + w + " + k_mti_delta" + w
+                                                     : (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
         c->kname[KNOR_KERNEL_MTI] =
-            c->ip_mti.warp_kernels == 3 ? "k_mti_sel + k_mti_scan" + w + " + k_mti_delta" + w
-                                        : (c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
+            c->mti_split ? "k_mti_sel + k_mti_scan" + w + " + k_mti_delta" + w
+                         : (c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
         c->kname[KNOR_KERNEL_REDUCE] = "k_reduce";
         c->kname[KNOR_KERNEL_TABLE] = "k_table";
     }

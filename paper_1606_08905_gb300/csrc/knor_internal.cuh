@@ -32,6 +32,10 @@ constexpr int SP_REC = 36;
 #define KNOR_SP_WPB 4
 #endif
 constexpr int SP_WPB = KNOR_SP_WPB; // warps per CTA of both split kernels
+#ifndef KNOR_DS_P
+#define KNOR_DS_P 1
+#endif
+constexpr int DS_ROWS = 32 * KNOR_DS_P; // rows per tile of the split dense scan (KNOR_DS_P per lane)
 
 // Per-point MTI state, packed so that the bound test reads 8 bytes per point.
 //   a   assignment (-1 before the first iteration)
@@ -123,6 +127,7 @@ struct IterParams {
     int2 *chg;
     int32_t *chg_cnt;
     int32_t dl_warp_stride, dl_off_slots;
+    int32_t dl_dense;      // 1: dense iterations also sum by change lists (k_dense_scan)
 };
 
 // Parameters of the reduction / finalize kernels.
@@ -219,6 +224,9 @@ cudaError_t mti_scan_attr(int dv, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t launch_mti_delta(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
                              const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
 cudaError_t mti_delta_attr(int dv, size_t smem, int *blocks_per_sm);
+cudaError_t launch_dense_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                              const int32_t *mode_dense);
+cudaError_t dense_scan_attr(int dv, size_t smem, int *blocks_per_sm);
 cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32_t *fresh, cudaStream_t s);
 cudaError_t launch_table(const FinParams &f, int32_t *mode_dense, int need_table, int recompute_every,
                          int always_dense, cudaStream_t s);
