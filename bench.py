@@ -144,6 +144,8 @@ def measured_peaks():
 KERNEL_SOURCES = {  # CUDA sources that define each profiled kernel
     "k_mti_w": "kernels_warp.cu", "k_dense_w": "kernels_warp.cu", "k_mti": "kernels.cu", "k_dense": "kernels.cu",
     "k_tc_assign": "precision.cu", "k_bscan": "batch.cu", "k_bmti": "batch.cu",
+    "k_mti_sel": "kernels_split.cu", "k_mti_scan": "kernels_split.cu", "k_mti_delta": "kernels_split.cu",
+    "k_dense_scan": "kernels_split.cu",
 }
 
 
@@ -164,7 +166,11 @@ def csrc_sha256(kernel: str = "") -> str:
 def ncu_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes of `kernel` (scaled to this workload) from the
     committed ncu summary profiles/<kernel>_<workload>.md, if the kernel's
-    CUDA sources have not changed since the capture (else None)."""
+    CUDA sources have not changed since the capture (else None).  For a step
+    of several kernels ("a + b + c") the sum of theirs, if all are known."""
+    if " + " in kernel:
+        parts = [ncu_traffic(kk, workload) for kk in kernel.split(" + ")]
+        return None if any(v is None for v in parts) else float(sum(parts))
     base = re.sub(r"<.*", "", kernel)
     path = os.path.join(ROOT, "profiles", f"{base}_{workload}.md")
     if not os.path.exists(path):
@@ -542,7 +548,16 @@ def our_arm(args, wl, world, rank, local):
     pts = float(n) * sum(iters)
     ms_max, pts_all = aggregate(ms, pts, world)
     value = pts_all / (ms_max / 1000.0)
-    per_it = 9 if wl.get("precision", "fp32") != "fp32" else (4 if wl["prune"] else 3)
+    # kernels in one iteration's graph (each scan launch returns at once in the
+    # iterations that are not its own): precision form 9; split path: dense
+    # scan [+ Clause-1 selection + MTI scan] + delta sums + merge + table;
+    # else dense | MTI scan + merge + table
+    if wl.get("precision", "fp32") != "fp32":
+        per_it = 9
+    elif "k_mti_delta" in ctx.kernel_name("dense") or "k_mti_delta" in ctx.kernel_name("mti"):
+        per_it = 6 if wl["prune"] else 4
+    else:
+        per_it = 4 if wl["prune"] else 3
     launches = sum(3 + it * per_it for it in iters)
 
     # ---- per-kernel CUDA-event timing (profiling mode: kernel by kernel on the
@@ -551,12 +566,29 @@ def our_arm(args, wl, world, rank, local):
     ctx.profile(reset=True)
     prof_iters = []
     prof_recs = []
+    # per-kernel totals over the dense iterations (plain Lloyd, MTI iteration
+    # 1) and over the MTI iterations, read back after every iteration
+    prof_it = {"dense": {}, "mti": {}}
     for _ in range(max(1, min(args.steps, 3))):
         ctx.reset()
-        done, recs = ctx.run(T)
+        done = 0
+        while done < T:
+            r = ctx.iterate()
+            done += 1
+            prof_recs.append(r)
+            kind = "dense" if (r["iteration"] == 1 or not wl["prune"]) else "mti"
+            for kname_, (lk, mk) in ctx.profile(reset=True).items():
+                if lk:
+                    a0 = prof_it[kind].setdefault(kname_, [0, 0.0])
+                    a0[0] += lk
+                    a0[1] += mk
+            if r["changed"] == 0:
+                break
         prof_iters.append(done)
-        prof_recs.extend(recs)
-    prof = ctx.profile(reset=True)
+    prof = {kk: (0, 0.0) for kk in knor.KERNELS}
+    for kind in prof_it.values():
+        for kname_, (lk, mk) in kind.items():
+            prof[kname_] = (prof[kname_][0] + lk, prof[kname_][1] + mk)
     ctx.set_profiling(False)
     # algorithmic work per launch: dense scan n(4d + 16) bytes;
     # MTI scan 8n + active (4d + 8) bytes with active = n - clause1_skipped;
@@ -593,24 +625,54 @@ def our_arm(args, wl, world, rank, local):
         dense_bytes = sum(n * (4 * d + 16) for r in prof_recs if (r["iteration"] == 1 or not wl["prune"]))
         mti_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in prof_recs
                         if wl["prune"] and r["iteration"] > 1)
-        for name, byts in (("dense", dense_bytes), ("mti", mti_bytes)):
-            launches_k, ms_k = prof[name]
+        # FP32 arithmetic of the scans: one subtraction and one fused
+        # multiply-add per dimension and distance (the direct form), against
+        # the FMA issue rate measured on this GPU now (knor_probe_alu)
+        fma_tflops, _ = knor.probe_alu("fp32")
+        fma_ops_peak = fma_tflops * 1e12 / 2.0
+        dense_ops = sum(2.0 * d * k * n for r in prof_recs if (r["iteration"] == 1 or not wl["prune"]))
+        mti_ops = sum(2.0 * d * r["dist_evals"] for r in prof_recs if wl["prune"] and r["iteration"] > 1)
+        # one "step" of each kind: its scan plus, on the split path, the
+        # Clause-1 selection and the delta sums of the same iterations
+        def step(kind, names):
+            parts = {nm: prof_it[kind][nm] for nm in names if nm in prof_it[kind]}
+            launches_k = max((v[0] for v in parts.values()), default=0)
+            return launches_k, sum(v[1] for v in parts.values()), {
+                ctx.kernel_name(nm): {"launches": v[0], "ms_total": v[1]} for nm, v in parts.items()}
+        for name, byts, ops in (("dense", dense_bytes, dense_ops), ("mti", mti_bytes, mti_ops)):
+            launches_k, ms_k, parts = step(name, ("dense", "delta") if name == "dense" else ("select", "mti", "delta"))
             if launches_k == 0 or ms_k <= 0:
                 continue
             gbs = byts / (ms_k / 1000.0) / 1e9
+            opsps = ops / (ms_k / 1000.0)
             kernels[name] = {"launches": launches_k, "ms_total": ms_k, "ms_per_launch": ms_k / launches_k,
+                             "parts": parts,
                              "algorithmic_bytes_per_launch": byts / launches_k, "achieved_gbs": gbs,
-                             "frac_of_" + peak_src + "_hbm": gbs / peaks["hbm_gbs"]}
+                             "frac_of_" + peak_src + "_hbm": gbs / peaks["hbm_gbs"],
+                             "fp32_ops_per_launch": ops / launches_k,
+                             "alu": {"achieved_tops": opsps / 1e12, "peak_tops": fma_ops_peak / 1e12,
+                                     "peak_source": "FP32 FMA issue rate measured now (knor_probe_alu)",
+                                     "frac": opsps / fma_ops_peak}}
         total_prof_ms = sum(v[1] for v in prof.values())
         dom = max(kernels, key=lambda kk: kernels[kk]["ms_total"])
-        kname = ctx.kernel_name(dom)
         for kk in kernels:
-            kernels[kk]["kernel"] = ctx.kernel_name(kk)
-        roof = {"kernel": kname, "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"],
-                "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
-                "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(kname, args.workload) if not args.n else None,
-                "share_of_kernel_time": kernels[dom]["ms_total"] / total_prof_ms}
+            kernels[kk]["kernel"] = " + ".join(kernels[kk]["parts"])
+        kname = kernels[dom]["kernel"]
+        kd = kernels[dom]
+        hbm_frac = kd["achieved_gbs"] / peaks["hbm_gbs"]
+        if kd["alu"]["frac"] > hbm_frac:
+            # the binding roof is the FP32 pipe (large k: 2dk operations per
+            # 4d + 16 bytes), e.g. the plain scans and uniform data at k = 100
+            roof = {"kernel": kname, "bound": "alu", "achieved": kd["alu"]["achieved_tops"],
+                    "peak": kd["alu"]["peak_tops"], "peak_source": kd["alu"]["peak_source"],
+                    "unit": "Tops/s (FP32 sub + FMA per dimension and distance)", "frac": kd["alu"]["frac"],
+                    "traffic": None, "hbm_frac": hbm_frac}
+        else:
+            roof = {"kernel": kname, "bound": "hbm", "achieved": kd["achieved_gbs"],
+                    "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s", "frac": hbm_frac,
+                    "traffic": ncu_traffic(kname, args.workload) if not args.n else None,
+                    "alu_frac": kd["alu"]["frac"]}
+        roof["share_of_kernel_time"] = kd["ms_total"] / total_prof_ms
 
     # ---- plain FP32 Lloyd on the same points: speed, and identical assignments
     plain = None

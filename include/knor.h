@@ -170,7 +170,11 @@ typedef enum {
     KNOR_KERNEL_RECHECK = 4, /* precision form: the uncertified points -- gather, tensor-core
                                 candidate pass, exact FP32 re-score of the candidates */
     KNOR_KERNEL_SUMS = 5,   /* precision form: delta cluster sums of the changed points */
-    KNOR_KERNEL_COUNT = 6
+    KNOR_KERNEL_SELECT = 6, /* split MTI scan: Clause 1 and the per-cluster batch records
+                               (KNOR_KERNEL_MTI is then the scan of those records) */
+    KNOR_KERNEL_DELTA = 7,  /* split scans: cluster sums moved by the rows of the points
+                               that changed cluster */
+    KNOR_KERNEL_COUNT = 8
 } knor_kernel;
 typedef struct {
     int64_t launches[KNOR_KERNEL_COUNT];
@@ -219,6 +223,19 @@ knor_status knor_set_state(knor_ctx *ctx, const void *buf, size_t size);
 knor_status knor_lloyd_step_noalloc(const float *points, int64_t n, int32_t d, int32_t k,
                                     const float *centroids, int32_t *assign_out, double *sums_out,
                                     int64_t *counts_out, void *stream);
+
+/* Fault injection, for tests of the error paths (the paper has no
+ * counterpart).  They make a failure happen on the host; neither faults,
+ * traps nor blocks the GPU.
+ *   knor_test_fail_alloc(after): the device allocation made after `after`
+ *     more successful ones (0: the next one) fails as if the device were out
+ *     of memory (the call reports KNOR_ERR_OOM); once only.  after < 0
+ *     cancels a pending failure.  Process-wide.
+ *   knor_test_raise_error_flag(ctx): sets the context's device error flag,
+ *     the flag a bounded device-side wait sets when it gives up; the next
+ *     knor_iterate / knor_run then returns KNOR_ERR_TIMEOUT and clears it. */
+knor_status knor_test_fail_alloc(int32_t after);
+knor_status knor_test_raise_error_flag(knor_ctx *ctx);
 
 /* Measurement helper (the paper has no counterpart: it measures the roof that
  * the FP32-bound scans are judged against).  Times, with CUDA events on a

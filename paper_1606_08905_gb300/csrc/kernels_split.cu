@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
 template <int DV>
 __global__ void __launch_bounds__(SPT) k_mti_delta(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
                                                     int32_t *fresh) {
-    if (*mode_dense != 0 && !p.dl_dense) return; // a dense scan that sums for itself ran
+    if (*mode_dense != 0 ? !p.dl_dense : !p.dl_mti) return; // this iteration's scan summed for itself
     extern __shared__ __align__(16) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int k = p.k;

@@ -13,6 +13,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -185,9 +186,21 @@ static knor_status fail(const knor_ctx *c, knor_status st, const std::string &ms
     return st;
 }
 
+// Pending injected allocation failure (knor_test_fail_alloc): the number
+// of allocations still to succeed before one fails; -1: none.
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+
 template <class T>
 static knor_status dalloc(knor_ctx *c, T **p, size_t count) {
     if (count == 0) count = 1;
+    int64_t left = g_fail_alloc_after.load();
+    while (left >= 0 && !g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left == 0) {
+        *p = nullptr;
+        return fail(c, KNOR_ERR_OOM, "cudaMalloc(" + std::to_string(count * sizeof(T)) +
+                                         " bytes): injected failure (knor_test_fail_alloc)");
+    }
     cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -431,17 +444,20 @@ static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
 
 static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
     int32_t *fl = c->flags;
-    if (c->mti_split) {
-        cudaError_t e = launch_mti_sel(c->ip_sel, c->grid_split, c->smem_sel, s, fl + F_MODE_DENSE);
-        if (e != cudaSuccess) return e;
+    if (c->mti_split)
         return launch_mti_scan(c->dv, c->ip_mti, c->grid_split, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                                fl + F_FRESH);
-    }
     if (c->ip_mti.warp_kernels)
         return launch_mti_w(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                             fl + F_FRESH);
     return launch_mti(c->dv, c->ip_mti, c->grid_mti, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                       fl + F_FRESH);
+}
+
+// Clause 1 and the batch records of the split MTI scan.
+static cudaError_t scan_select(knor_ctx *c, cudaStream_t s) {
+    if (!c->mti_split) return cudaSuccess;
+    return launch_mti_sel(c->ip_sel, c->grid_split, c->smem_sel, s, c->flags + F_MODE_DENSE);
 }
 
 // Phase II from the change lists of the split scans (a no-op in a dense
@@ -504,7 +520,10 @@ static knor_status enqueue_iteration(knor_ctx *c, cudaStream_t s, unsigned long 
         KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
     }
     KNOR_CUDA(c, scan_dense(c, s));
-    if (!c->opts.no_prune) KNOR_CUDA(c, scan_mti(c, s));
+    if (!c->opts.no_prune) {
+        KNOR_CUDA(c, scan_select(c, s));
+        KNOR_CUDA(c, scan_mti(c, s));
+    }
     KNOR_CUDA(c, scan_delta(c, s));
     KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
     FinParams f = c->fp;
@@ -551,19 +570,23 @@ static knor_status profiled_iteration(knor_ctx *c) {
         KNOR_CUDA(c, cudaMemsetAsync(c->part_S, 0, sizeof(double) * (size_t)c->k * c->d, s));
         KNOR_CUDA(c, cudaMemsetAsync(c->part_cnt, 0, sizeof(long long) * (size_t)c->k, s));
     }
+    auto timed = [&](int kind, cudaError_t (*fn)(knor_ctx *, cudaStream_t)) -> knor_status {
+        KNOR_CUDA(c, cudaEventRecord(c->ev[2 * kind], s));
+        KNOR_CUDA(c, fn(c, s));
+        KNOR_CUDA(c, cudaEventRecord(c->ev[2 * kind + 1], s));
+        used[kind] = true;
+        return KNOR_OK;
+    };
+    knor_status ks = KNOR_OK;
     if (dense) {
-        KNOR_CUDA(c, cudaEventRecord(c->ev[0], s));
-        KNOR_CUDA(c, scan_dense(c, s));
-        KNOR_CUDA(c, scan_delta(c, s));
-        KNOR_CUDA(c, cudaEventRecord(c->ev[1], s));
-        used[KNOR_KERNEL_DENSE] = true;
+        ks = timed(KNOR_KERNEL_DENSE, scan_dense);
+        if (ks == KNOR_OK && c->dense_split) ks = timed(KNOR_KERNEL_DELTA, scan_delta);
     } else {
-        KNOR_CUDA(c, cudaEventRecord(c->ev[2], s));
-        KNOR_CUDA(c, scan_mti(c, s));
-        KNOR_CUDA(c, scan_delta(c, s));
-        KNOR_CUDA(c, cudaEventRecord(c->ev[3], s));
-        used[KNOR_KERNEL_MTI] = true;
+        if (c->mti_split) ks = timed(KNOR_KERNEL_SELECT, scan_select);
+        if (ks == KNOR_OK) ks = timed(KNOR_KERNEL_MTI, scan_mti);
+        if (ks == KNOR_OK && c->mti_split) ks = timed(KNOR_KERNEL_DELTA, scan_delta);
     }
+    if (ks != KNOR_OK) return ks;
     KNOR_CUDA(c, cudaEventRecord(c->ev[4], s));
     KNOR_CUDA(c, launch_reduce(c->fp, fl + F_NSLOTS, fl + F_FRESH, s));
     KNOR_CUDA(c, cudaEventRecord(c->ev[5], s));
@@ -846,6 +869,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
             q->chg = c->chg;
             q->chg_cnt = c->chg_cnt;
             q->dl_dense = c->dense_split ? 1 : 0;
+            q->dl_mti = c->mti_split ? 1 : 0;
         }
     }
     c->ip_dense.part_stride = c->part_stride;
@@ -854,11 +878,12 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     c->ip_dense.acc_global = c->ip_mti.acc_global = acc_global;
     {
         const std::string w = "<" + std::to_string(c->dv) + ">";
-        c->kname[KNOR_KERNEL_DENSE] = c->dense_split ? "k_dense_scan" + w + " + k_mti_delta" + w
-                                                     : (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
+        c->kname[KNOR_KERNEL_DENSE] =
+            c->dense_split ? "k_dense_scan" + w : (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
+        if (c->mti_split) c->kname[KNOR_KERNEL_SELECT] = "k_mti_sel";
+        if (c->mti_split || c->dense_split) c->kname[KNOR_KERNEL_DELTA] = "k_mti_delta" + w;
         c->kname[KNOR_KERNEL_MTI] =
-            c->mti_split ? "k_mti_sel + k_mti_scan" + w + " + k_mti_delta" + w
-                         : (c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
+            (c->mti_split ? "k_mti_scan" : c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
         c->kname[KNOR_KERNEL_REDUCE] = "k_reduce";
         c->kname[KNOR_KERNEL_TABLE] = "k_table";
     }
@@ -1067,6 +1092,20 @@ knor_status knor_run(knor_ctx *c, int32_t max_iters, int32_t *iters_done, knor_i
     c->host_total_iter += done;
     if (iters_done) *iters_done = done;
     return read_stats(c, done, per_iter);
+}
+
+knor_status knor_test_fail_alloc(int32_t after) {
+    g_fail_alloc_after.store(after < 0 ? -1 : (int64_t)after);
+    return KNOR_OK;
+}
+
+knor_status knor_test_raise_error_flag(knor_ctx *c) {
+    if (!c) return KNOR_ERR_ARG;
+    c->err.clear();
+    const int32_t one = 1;
+    KNOR_CUDA(c, cudaMemcpyAsync(c->flags + F_ERR, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream));
+    KNOR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KNOR_OK;
 }
 
 const char *knor_kernel_name(const knor_ctx *c, int32_t kernel) {

@@ -127,7 +127,8 @@ struct IterParams {
     int2 *chg;
     int32_t *chg_cnt;
     int32_t dl_warp_stride, dl_off_slots;
-    int32_t dl_dense;      // 1: dense iterations also sum by change lists (k_dense_scan)
+    int32_t dl_dense;      // 1: dense iterations sum by change lists (k_dense_scan)
+    int32_t dl_mti;        // 1: MTI iterations sum by change lists (k_mti_scan)
 };
 
 // Parameters of the reduction / finalize kernels.

@@ -44,10 +44,10 @@ class IterStats(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6)]
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8)]
 
 
-KERNELS = ("dense", "mti", "reduce", "table", "recheck", "sums")
+KERNELS = ("dense", "mti", "reduce", "table", "recheck", "sums", "select", "delta")
 
 
 class BatchInstance(ctypes.Structure):
@@ -81,6 +81,8 @@ _SIGS = {
     "knor_lloyd_step_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "knor_test_fail_alloc": (ctypes.c_int, [ctypes.c_int32]),
+    "knor_test_raise_error_flag": (ctypes.c_int, [ctypes.c_void_p]),
     "knor_probe_alu": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_float)]),
     "knor_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -194,6 +196,11 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+    def test_raise_error_flag(self):
+        """Fault injection (knor_test_raise_error_flag): the next iterate or
+        run reports KNOR_ERR_TIMEOUT, as after a device wait that gave up."""
+        _check(load().knor_test_raise_error_flag(self._ctx), self._ctx)
 
     # -- iteration
     def set_init_centroids(self, C):
@@ -444,6 +451,12 @@ def lloyd_step_noalloc(points, centroids, assign_out, sums_out, counts_out, stre
     p4, _ = _ptr(counts_out, np.int64)
     with torch.cuda.device(dev):
         _check(load().knor_lloyd_step_noalloc(p0, n, d, k, p1, p2, p3, p4, stream or None), None)
+
+
+def test_fail_alloc(after: int):
+    """Fault injection (knor_test_fail_alloc): the device allocation after
+    `after` more successful ones fails with KNOR_ERR_OOM; after < 0 cancels."""
+    _check(load().knor_test_fail_alloc(int(after)), None)
 
 
 def probe_alu(kind: str) -> tuple[float, float]:
