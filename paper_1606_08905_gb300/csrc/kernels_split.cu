@@ -3,10 +3,10 @@
 // k_mti_sel   Clause 1 ("Minimal Triangle Inequality (MTI) Pruning") on the
 //             packed state of every point.  Each warp owns a contiguous range
 //             of points, streams its state, and puts the points that Clause 1
-//             cannot skip into per-cluster buckets in shared memory (rings of
-//             WBCAP local indices); a bucket that reaches 32 points is written
-//             out as one batch record (cluster, count, 32 point indices) to
-//             the warp's own list, and the partial buckets follow at the end.
+//             cannot skip into per-cluster buckets in shared memory (32 local
+//             indices each); a bucket that fills is written out at once as
+//             one batch record (cluster, count, 32 point indices) to the
+//             warp's own list, and the partial buckets follow at the end.
 //             Nothing but the 8-byte state of a point is read here.
 // k_mti_scan  Clauses 3 and 2 on the records: warp w scans list w in order.
 //             While it scores one batch, the rows of its next two batches
@@ -19,9 +19,9 @@
 //             cluster).
 // k_dense_scan  the full scan (plain Lloyd, the first MTI iteration) over the
 //             same warp ranges, appending its changed points to the same lists.
-// k_mti_delta Phase II by deltas: warp w adds the rows of change list w to
-//             their new clusters and subtracts them from their old ones
-//             (TwoSum pairs in shared memory), rows again double-buffered.
+// k_mti_delta Phase II by deltas: the rows of the change lists are added to
+//             their new clusters and subtracted from their old ones (TwoSum
+//             pairs in shared memory), each list split over a few warps.
 //
 // Record and change lists are a pure function of the state, and each is
 // processed by one warp in order, so the sums (each CTA adds its warps'
@@ -61,11 +61,10 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
     float *F_s = reinterpret_cast<float *>(sm + p.off_F);
     for (int c = tid; c < k; c += SPT) { s_s[c] = p.s[c]; F_s[c] = p.F[c]; }
     unsigned char *wr = sm + p.w_base + w * p.w_stride;
-    int *bk = reinterpret_cast<int *>(wr + p.w_bucket); // (k + 1) rings of WBCAP local indices
-    int *bhead = bk + (k + 1) * WBCAP;
-    int *bcnt = bhead + (k + 1);
+    int *bk = reinterpret_cast<int *>(wr + p.w_bucket); // (k + 1) buckets of 32 local indices
+    int *bcnt = bk + (k + 1) * 32;
     PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
-    for (int c = lane; c <= k; c += 32) { bhead[c] = 0; bcnt[c] = 0; }
+    for (int c = lane; c <= k; c += 32) bcnt[c] = 0;
     __syncthreads();
     const int gw = blockIdx.x * SPW + w, nw = gridDim.x * SPW;
     int64_t lo, hi;
@@ -86,18 +85,16 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
         }
         cp_async_commit();
     };
-    // Writes the first nb (<= 32) points of bucket cb as the next record.
+    // Writes the nb (<= 32) points of bucket cb as the next record (the
+    // caller then resets the bucket's count).
     auto emit = [&](int cb, int nb) {
         int32_t *r = rec + (size_t)nrec * SP_REC;
-        if (lane < nb) r[4 + lane] = (int32_t)(lo + bk[cb * WBCAP + ((bhead[cb] + lane) & (WBCAP - 1))]);
-        __syncwarp(); // every lane has read bhead before lane 0 moves it
+        if (lane < nb) r[4 + lane] = (int32_t)(lo + bk[cb * 32 + lane]);
         if (lane == 0) {
             r[0] = cb;
             r[1] = nb;
-            bhead[cb] = (bhead[cb] + nb) & (WBCAP - 1);
-            bcnt[cb] -= nb;
         }
-        __syncwarp();
+        __syncwarp(); // every lane has read the bucket before it is refilled
         ++nrec;
     };
 
@@ -171,14 +168,12 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
             const int key = valid ? (ent.y < 0 ? k : ent.y) : -1 - lane;
             const unsigned grp = __match_any_sync(FULL_MASK, key);
             const int rank = __popc(grp & ((1u << lane) - 1u));
-            int now = 0;
-            if (valid) {
-                const int c0 = bcnt[key];
-                bk[key * WBCAP + ((bhead[key] + c0 + rank) & (WBCAP - 1))] = ent.x;
-                now = c0 + __popc(grp);
-            }
-            __syncwarp();
-            if (valid && rank == 0) bcnt[key] = now;
+            // the entries that fit go in; a bucket that fills is emitted at
+            // once and the rest of its group starts it afresh (point order is
+            // kept: first in, first out)
+            const int c0 = valid ? bcnt[key] : 0;
+            const int now = c0 + __popc(grp);
+            if (valid && c0 + rank < 32) bk[key * 32 + c0 + rank] = ent.x;
             __syncwarp();
             unsigned fullm = __ballot_sync(FULL_MASK, valid && rank == 0 && now >= 32);
             while (fullm) {
@@ -186,6 +181,9 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
                 fullm &= fullm - 1;
                 emit(__shfl_sync(FULL_MASK, key, leader), 32);
             }
+            if (valid && c0 + rank >= 32) bk[key * 32 + c0 + rank - 32] = ent.x;
+            if (valid && rank == 0) bcnt[key] = now >= 32 ? now - 32 : now;
+            __syncwarp();
         }
         __syncwarp();
     }
@@ -510,91 +508,84 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
 
 // ------------------------------------------------------------ delta sums
 
-// Phase II by deltas: warp w takes the change list of scan warp w in order,
-// 32 entries at a time, brings their rows into shared memory (the next group's
-// rows in flight while it adds the current one), adds each row to its new
-// cluster and subtracts it from its old one in its TwoSum accumulators (in
-// shared memory); the CTA adds its warps' accumulators in warp order into its
-// partial slot.  Order and grouping depend only on the lists: deterministic.
+// Phase II by deltas: CTA b takes the change lists of scan CTA b, each
+// split into p.dl_split consecutive parts with one warp per part (warp w:
+// list w / dl_split, part w % dl_split).  A warp takes its entries 32 at a
+// time, loads their rows straight into registers (32 row loads in flight per
+// lane, lanes walking the dimensions), then adds each row to its new cluster
+// and subtracts it from its old one in its TwoSum accumulators (shared
+// memory), in list order; the CTA adds its warps' accumulators in warp order
+// into its partial slot.  Order and grouping depend only on the lists and
+// the fixed split: deterministic.
 template <int DV>
-__global__ void __launch_bounds__(SPT) k_mti_delta(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
+__global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
                                                     int32_t *fresh) {
     if (*mode_dense != 0 ? !p.dl_dense : !p.dl_mti) return; // this iteration's scan summed for itself
     extern __shared__ __align__(16) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int nthr = blockDim.x;
     const int k = p.k;
-    const int rs = p.sp_rs;
+    constexpr int R = DV < 32 ? 1 : DV / 32; // dimensions per lane
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
-    unsigned char *wr = sm + w * p.dl_warp_stride;
-    float *acc_hi = reinterpret_cast<float *>(wr);
+    float *acc_hi = reinterpret_cast<float *>(sm + w * p.dl_warp_stride);
     float *acc_lo = acc_hi + (size_t)k * DV;
     int *cnt = reinterpret_cast<int *>(acc_lo + (size_t)k * DV);
-    float *slots = reinterpret_cast<float *>(wr + p.dl_off_slots);
     for (int e = lane; e < 2 * k * DV; e += 32) acc_hi[e] = 0.0f;
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
-    const int gw = blockIdx.x * SPW + w;
-    const int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32;
-    const int nchg = p.chg_cnt[gw];
-    const int ngrp = (nchg + 31) / 32;
-    auto entry = [&](int g, int &idx, int &cl) {
-        const int e = g * 32 + lane;
-        if (g < ngrp && e < nchg) {
-            const int2 v = chg[e];
+    __syncwarp();
+    const int list = blockIdx.x * SPW + w / p.dl_split, part = w % p.dl_split;
+    const int2 *chg = p.chg + (size_t)list * p.rec_cap * 32;
+    const int nchg = p.chg_cnt[list];
+    const int e0 = (int)((int64_t)nchg * part / p.dl_split), e1 = (int)((int64_t)nchg * (part + 1) / p.dl_split);
+    for (int g0 = e0; g0 < e1; g0 += 32) {
+        const int nb = min(32, e1 - g0);
+        int idx = 0, cl = 0;
+        if (lane < nb) {
+            const int2 v = chg[g0 + lane];
             idx = v.x;
             cl = v.y;
-        } else {
-            idx = -1;
-            cl = 0;
+            atomicAdd(&cnt[(unsigned)cl >> 16], 1);
+            if ((cl & 0xFFFF) != 0xFFFF) atomicAdd(&cnt[cl & 0xFFFF], -1);
         }
-    };
-    auto fetch = [&](int slot, int idx) {
-        constexpr int CH = DV / 4;
-        float *dst = slots + (size_t)slot * 32 * rs;
-        const unsigned have = __ballot_sync(FULL_MASK, idx >= 0);
-        const int nb = __popc(have); // entries are a prefix of the group
-        for (int base = 0; base < nb * CH; base += 32) {
-            const int f = base + lane;
-            const int r = min(f / CH, 31);
-            const int ir = __shfl_sync(FULL_MASK, idx, r);
-            if (f < nb * CH) cp_async16(dst + r * rs + (f % CH) * 4, p.X + (int64_t)ir * DV + (f % CH) * 4);
-        }
-        cp_async_commit();
-    };
-    int i0, c0, i1, c1;
-    entry(0, i0, c0);
-    fetch(0, i0);
-    entry(1, i1, c1);
-    __syncwarp();
-    for (int g = 0; g < ngrp; ++g) {
-        fetch((g + 1) & 1, i1);
-        int i2, c2;
-        entry(g + 2, i2, c2);
-        cp_async_wait<1>();
-        __syncwarp();
-        const float *rb = slots + (size_t)(g & 1) * 32 * rs;
-        sp_accumulate_rows<DV>(rb, rs, c0, i0 >= 0, acc_hi, acc_lo, cnt);
-        __syncwarp(); // slot g & 1 is refilled by the next group's fetch
-        i0 = i1; c0 = c1;
-        i1 = i2; c1 = c2;
-    }
-    cp_async_wait<0>();
-    __syncthreads();
-    const int kd = k * DV;
-    for (int e = tid; e < kd; e += SPT) {
-        double sum = 0.0;
+        float x[32][R];
 #pragma unroll
-        for (int q = 0; q < SPW; ++q) {
+        for (int q = 0; q < 32; ++q) {
+            const int iq = __shfl_sync(FULL_MASK, idx, q);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int j = lane + 32 * r;
+                x[q][r] = (q < nb && j < DV) ? __ldg(p.X + (int64_t)iq * DV + j) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (q >= nb) break;
+            const int c = __shfl_sync(FULL_MASK, cl, q);
+            const int cn = (int)((unsigned)c >> 16), co = c & 0xFFFF;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int j = lane + 32 * r;
+                if (j < DV) {
+                    two_sum_acc(&acc_hi[cn * DV + j], &acc_lo[cn * DV + j], x[q][r]);
+                    if (co != 0xFFFF) two_sum_acc(&acc_hi[co * DV + j], &acc_lo[co * DV + j], -x[q][r]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int kd = k * DV, nw = nthr >> 5;
+    for (int e = tid; e < kd; e += nthr) {
+        double sum = 0.0;
+        for (int q = 0; q < nw; ++q) {
             const float *a = reinterpret_cast<const float *>(sm + q * p.dl_warp_stride);
             sum += (double)a[e];
             sum += (double)a[kd + e];
         }
         p.part_S[(size_t)e * p.part_stride + blockIdx.x] = sum;
     }
-    for (int c = tid; c < k; c += SPT) {
+    for (int c = tid; c < k; c += nthr) {
         long long sum = 0;
-#pragma unroll
-        for (int q = 0; q < SPW; ++q)
-            sum += reinterpret_cast<const int *>(sm + q * p.dl_warp_stride + (size_t)2 * kd * 4)[c];
+        for (int q = 0; q < nw; ++q) sum += reinterpret_cast<const int *>(sm + q * p.dl_warp_stride + (size_t)2 * kd * 4)[c];
         p.part_cnt[(size_t)c * p.part_stride + blockIdx.x] = sum;
     }
 }
@@ -635,15 +626,15 @@ static cudaError_t mti_scan_launch_t(const IterParams &p, int grid, size_t smem,
     }
 
 template <int DV>
-static cudaError_t mti_delta_attr_t(size_t smem, int *bps) {
+static cudaError_t mti_delta_attr_t(size_t smem, int split, int *bps) {
     cudaError_t e = cudaFuncSetAttribute(k_mti_delta<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_mti_delta<DV>, SPT, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_mti_delta<DV>, SPT * split, smem);
 }
 template <int DV>
 static cudaError_t mti_delta_launch_t(const IterParams &p, int grid, size_t smem, cudaStream_t s,
                                       const int32_t *md, int32_t *ns, int32_t *fr) {
-    k_mti_delta<DV><<<grid, SPT, smem, s>>>(p, md, ns, fr);
+    k_mti_delta<DV><<<grid, SPT * p.dl_split, smem, s>>>(p, md, ns, fr);
     return cudaGetLastError();
 }
 
@@ -665,7 +656,9 @@ cudaError_t launch_dense_scan(int dv, const IterParams &p, int grid, size_t smem
     KNOR_DVSP_SWITCH(dv, dense_scan_launch_t, p, grid, smem, s, md)
 }
 
-cudaError_t mti_delta_attr(int dv, size_t smem, int *bps) { KNOR_DVSP_SWITCH(dv, mti_delta_attr_t, smem, bps) }
+cudaError_t mti_delta_attr(int dv, size_t smem, int split, int *bps) {
+    KNOR_DVSP_SWITCH(dv, mti_delta_attr_t, smem, split, bps)
+}
 cudaError_t launch_mti_delta(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
                              const int32_t *md, int32_t *ns, int32_t *fr) {
     KNOR_DVSP_SWITCH(dv, mti_delta_launch_t, p, grid, smem, s, md, ns, fr)

@@ -367,7 +367,7 @@ static size_t plan_layout_sel(const knor_ctx *c, IterParams &p) {
     p.off_F = take((size_t)k * 4);
     p.w_base = take(0);
     p.w_bucket = 0;
-    const size_t bucket = (((size_t)(k + 1) * (WBCAP + 2) * 4) + 15) & ~(size_t)15;
+    const size_t bucket = (((size_t)(k + 1) * (32 + 1) * 4) + 15) & ~(size_t)15; // 32 slots and a count
     p.w_state = (int32_t)bucket;
     p.w_stride = (int32_t)(bucket + (size_t)WSTAGES * WCH * sizeof(PtState));
     p.sp_wpb = SP_WPB;
@@ -398,10 +398,12 @@ static size_t plan_layout_scan(const knor_ctx *c, IterParams &p) {
     p.sp_wpb = SP_WPB;
     const size_t total = off + (size_t)SP_WPB * p.sp_warp_stride;
     if (total > 112 * 1024) return 0; // keep at least two CTAs per SM
-    // k_mti_delta: per warp, TwoSum accumulators and counts, then two row slots
-    p.dl_off_slots = (int32_t)(((size_t)2 * kd * 4 + (size_t)k * 4 + 15) & ~(size_t)15);
-    p.dl_warp_stride = (int32_t)(p.dl_off_slots + (size_t)2 * 32 * p.sp_rs * 4);
-    if ((size_t)SP_WPB * p.dl_warp_stride > 200 * 1024) return 0;
+    // k_mti_delta: per warp, TwoSum accumulators and counts; each change list
+    // split over up to 4 warps while a CTA stays within 96 KB
+    p.dl_warp_stride = (int32_t)(((size_t)2 * kd * 4 + (size_t)k * 4 + 15) & ~(size_t)15);
+    p.dl_split = 4;
+    while (p.dl_split > 1 && (size_t)SP_WPB * p.dl_split * p.dl_warp_stride > 96 * 1024) p.dl_split /= 2;
+    if ((size_t)SP_WPB * p.dl_split * p.dl_warp_stride > 200 * 1024) return 0;
     p.warp_kernels = 3;
     p.acc_global = 0;
     return total;
@@ -465,7 +467,8 @@ static cudaError_t scan_select(knor_ctx *c, cudaStream_t s) {
 static cudaError_t scan_delta(knor_ctx *c, cudaStream_t s) {
     if (!c->mti_split && !c->dense_split) return cudaSuccess;
     int32_t *fl = c->flags;
-    return launch_mti_delta(c->dv, c->ip_delta, c->grid_split, (size_t)SP_WPB * c->ip_delta.dl_warp_stride, s,
+    return launch_mti_delta(c->dv, c->ip_delta, c->grid_split,
+                            (size_t)SP_WPB * c->ip_delta.dl_split * c->ip_delta.dl_warp_stride, s,
                             fl + F_MODE_DENSE, fl + F_NSLOTS, fl + F_FRESH);
 }
 
@@ -790,7 +793,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
             KCU(mti_scan_attr(c->dv, SP_WPB, ssc, &bsplit));
             c->smem_sel = plan_layout_sel(c, c->ip_sel);
             KCU(mti_sel_attr(SP_WPB, c->smem_sel, &bs));
-            KCU(mti_delta_attr(c->dv, (size_t)SP_WPB * ps.dl_warp_stride, &bdl));
+            KCU(mti_delta_attr(c->dv, (size_t)SP_WPB * ps.dl_split * ps.dl_warp_stride, ps.dl_split, &bdl));
             if (bs < 1 || bdl < 1) bsplit = 0;
         }
         c->mti_split = bsplit > 0 && choice == 0 && !o.no_prune;

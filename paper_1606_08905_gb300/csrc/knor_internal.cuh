@@ -122,11 +122,11 @@ struct IterParams {
     int32_t sp_off_warp, sp_warp_stride, sp_off_cnt;
     // change lists (point, new cluster << 16 | old cluster), 32 * rec_cap
     // entries per warp, chg_cnt[warp] entries written; the delta kernel's
-    // per-warp shared-memory region (accumulators and counts, then two row
-    // slots at dl_off_slots)
+    // per-warp shared-memory region (accumulators and counts) and the number
+    // of its warps that share one list
     int2 *chg;
     int32_t *chg_cnt;
-    int32_t dl_warp_stride, dl_off_slots;
+    int32_t dl_warp_stride, dl_split; // k_mti_delta: per-warp region, warps per change list
     int32_t dl_dense;      // 1: dense iterations sum by change lists (k_dense_scan)
     int32_t dl_mti;        // 1: MTI iterations sum by change lists (k_mti_scan)
 };
@@ -224,7 +224,7 @@ cudaError_t launch_mti_scan(int dv, const IterParams &p, int grid, size_t smem, 
 cudaError_t mti_scan_attr(int dv, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t launch_mti_delta(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
                              const int32_t *mode_dense, int32_t *nslots, int32_t *fresh);
-cudaError_t mti_delta_attr(int dv, size_t smem, int *blocks_per_sm);
+cudaError_t mti_delta_attr(int dv, size_t smem, int split, int *blocks_per_sm);
 cudaError_t launch_dense_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
                               const int32_t *mode_dense);
 cudaError_t dense_scan_attr(int dv, size_t smem, int *blocks_per_sm);
