@@ -413,10 +413,10 @@ def batch_arm(args, wl, world, rank, local):
             ppit = bp.work()[0]
             q1.record(ps)
             torch.cuda.synchronize()
-            same = all(np.array_equal(bp.assignments(i), b.assignments(i)) for i in range(0, wl["m"], 17))
+            same = all(np.array_equal(bp.assignments(i), b.assignments(i)) for i in range(wl["m"]))
             pv = ppit / (q0.elapsed_time(q1) / 1000.0)
             plain = {"value": pv, "unit": "point-iterations/s", "speedup": (value / world) / pv,
-                     "identical_assignments_every_17th_instance": bool(same)}
+                     "identical_assignments_all_instances": bool(same)}
 
     # e2e through the C ABI from pinned host memory: create, run, read back
     e2e = None
@@ -645,6 +645,11 @@ def our_arm(args, wl, world, rank, local):
                 continue
             gbs = byts / (ms_k / 1000.0) / 1e9
             opsps = ops / (ms_k / 1000.0)
+            if name == "dense" and ctx.kernel_name("dense") in parts:
+                # the scan on its own against the FP32 pipe (its sums are the
+                # delta part)
+                sp_ = parts[ctx.kernel_name("dense")]
+                sp_["alu_frac"] = ops / (sp_["ms_total"] / 1000.0) / fma_ops_peak
             kernels[name] = {"launches": launches_k, "ms_total": ms_k, "ms_per_launch": ms_k / launches_k,
                              "parts": parts,
                              "algorithmic_bytes_per_launch": byts / launches_k, "achieved_gbs": gbs,
