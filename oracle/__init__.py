@@ -78,7 +78,7 @@ def _load():
         lib.oracle_mti_iter.restype = c.c_int64
         lib.oracle_run.argtypes = [_f32p, c.c_int64, c.c_int32, c.c_int32, _f64p, c.c_int32,
                                    c.c_int, _f64p, _i32p, c.c_void_p, c.c_void_p, c.c_void_p,
-                                   c.c_void_p, c.c_void_p, c.c_int]
+                                   c.c_void_p, c.c_void_p, c.c_void_p, c.c_int]
         lib.oracle_run.restype = c.c_int
         lib.oracle_assign_f32.argtypes = [_f32p, c.c_int64, c.c_int32, c.c_int32, _f32p, _i32p,
                                           c.c_int]
@@ -206,10 +206,13 @@ class RunResult:
         self.__dict__.update(kw)
 
 
-def run(X, C0, max_iters: int, prune: bool, history: bool = False, nthreads: int = 0) -> RunResult:
+def run(X, C0, max_iters: int, prune, history: bool = False, nthreads: int = 0) -> RunResult:
     """Lloyd's algorithm from C0 (k x d) until no assignment changes or
-    max_iters.  With history=True also returns a_hist (iters x n) and C_hist
-    ((iters+1) x k x d, C^0 first)."""
+    max_iters.  prune: False (every distance), True (MTI) or "elkan" (MTI
+    plus per-centroid lower bounds; also checks the bounds every iteration,
+    result.violations).  With history=True also returns a_hist (iters x n)
+    and C_hist ((iters+1) x k x d, C^0 first)."""
+    mode = 2 if prune == "elkan" else (1 if prune else 0)
     X = _X(X)
     n, d = X.shape
     C0 = np.ascontiguousarray(C0, dtype=np.float64)
@@ -221,12 +224,13 @@ def run(X, C0, max_iters: int, prune: bool, history: bool = False, nthreads: int
     ev = np.zeros(max_iters, np.int64)
     ah = np.zeros((max_iters, n), np.int32) if history else None
     Ch = np.zeros((max_iters + 1, k, d), np.float64) if history else None
-    it = _load().oracle_run(X, n, d, k, C0, max_iters, 1 if prune else 0, C, a,
+    vi = np.zeros(max_iters, np.int64)
+    it = _load().oracle_run(X, n, d, k, C0, max_iters, mode, C, a,
                             ah.ctypes.data if history else None,
                             Ch.ctypes.data if history else None,
-                            ch.ctypes.data, sk.ctypes.data, ev.ctypes.data, nthreads)
+                            ch.ctypes.data, sk.ctypes.data, ev.ctypes.data, vi.ctypes.data, nthreads)
     return RunResult(iters=int(it), C=C, a=a, changed=ch[:it].copy(), skipped=sk[:it].copy(),
-                     evals=ev[:it].copy(),
+                     evals=ev[:it].copy(), violations=vi[:it].copy(),
                      a_hist=ah[:it].copy() if history else None,
                      C_hist=Ch[:it + 1].copy() if history else None)
 

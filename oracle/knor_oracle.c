@@ -133,6 +133,18 @@ static double oracle_dist2(const float *x, const double *c, int32_t d) {
     return s;
 }
 
+/* The squared distance over every dimension (used only to check the bounds,
+ * so that a planted mistake in oracle_dist2 cannot hide itself). */
+static double oracle_dist2_exactish(const float *x, const double *c, int32_t d) {
+    double s = 0.0;
+    int32_t i;
+    for (i = 0; i < d; ++i) {
+        double t = (double)x[i] - c[i];
+        s += t * t;
+    }
+    return s;
+}
+
 static double oracle_dist2_cc(const double *a, const double *b, int32_t d) {
     double s = 0.0;
     int32_t i;
@@ -398,23 +410,134 @@ int64_t oracle_mti_iter(const float *X, int64_t n, int32_t d, int32_t k, const d
 }
 
 /* ------------------------------------------------------------------ */
+/* Elkan's algorithm: MTI plus per-centroid lower bounds.               */
+/* ------------------------------------------------------------------ */
+
+/* A lower bound on a - b for a >= 0, b >= 0 (0 when negative). */
+static double oracle_sub_down(double a, double b) {
+    double v = (a - b) * (1.0 - 8.0 * ORACLE_EPS64);
+    return v > 0.0 ? v : 0.0;
+}
+
+/* One iteration of Elkan's algorithm (Elkan 2003, the source the paper cites
+ * for its pruning; the paper's MTI keeps Elkan's first three tests and
+ * leaves out the fourth, whose n x k lower bounds it finds too costly, and
+ * does not measure it).  Besides MTI's upper bound u(x) >= d(x, c_a) every
+ * point keeps lower bounds l(x, c) <= d(x, c), one per centroid, set when
+ * the distance is computed and lowered by the centroid's drift each
+ * iteration (triangle inequality).  A centroid is ruled out when u is below
+ * 1/2 d(c_a, c) (MTI's Clause 2) or below l(x, c) (the fourth test); Clause 1
+ * and the tightening of u (Clause 3) are MTI's.
+ *   l        n*k lower bounds (row per point), updated in place
+ *   a, u     as for oracle_mti_iter
+ *   viol_out NULL, or receives the number of bounds found wrong before
+ *            the tests use them: some l(x, c) above d(x, c), or u below
+ *            d(x, c_a) (exact distances in FP64, with a rounding margin);
+ *            always 0 for correct bounds.
+ * Returns the number of points whose assignment changed. */
+int64_t oracle_elkan_iter(const float *X, int64_t n, int32_t d, int32_t k, const double *C,
+                          const double *halfD, const double *s, const double *f, int32_t *a,
+                          double *u, double *l, int64_t *skipped_out, int64_t *evals_out,
+                          int64_t *viol_out, int nthreads) {
+    double g = oracle_gamma(d);
+    double kappa = 2.0 * g;
+    double tau = 1e-280;
+    int64_t changed = 0, skipped = 0, evals = 0, viol = 0;
+    int64_t i;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static) reduction(+ : changed, skipped, evals, viol)
+#endif
+    for (i = 0; i < n; ++i) {
+        const float *x = X + (size_t)i * d;
+        double *li = l + (size_t)i * k;
+        int32_t ai = a[i], c, best;
+        double ui, bd;
+        int tight = 0;
+        if (ai < 0) {
+            /* No assignment yet: every distance, and every lower bound. */
+            best = 0;
+            bd = INFINITY;
+            for (c = 0; c < k; ++c) {
+                double v = oracle_dist2(x, C + (size_t)c * d, d);
+                li[c] = oracle_dist_down(v, g);
+                if (v < bd) { bd = v; best = c; }
+            }
+            evals += k;
+            a[i] = best;
+            u[i] = oracle_dist_up(bd, g);
+            changed += 1;
+            continue;
+        }
+        ui = oracle_add_up(u[i], f[ai]);
+#ifndef ORACLE_PLANT_ELKAN_NO_LB_DRIFT /* lower bounds ignore centroid drift */
+        for (c = 0; c < k; ++c) li[c] = oracle_sub_down(li[c], f[c]);
+#endif
+        if (viol_out) {
+            for (c = 0; c < k; ++c) {
+                double e = sqrt(oracle_dist2_exactish(x, C + (size_t)c * d, d));
+                if (li[c] > e * (1.0 + 4.0 * g) + 1e-300) viol += 1;
+                if (c == ai && ui < e * (1.0 - 4.0 * g)) viol += 1;
+            }
+        }
+        /* Clause 1: nothing else is read. */
+        if (ui * (1.0 + kappa) + tau < s[ai]) {
+            u[i] = ui;
+            skipped += 1;
+            continue;
+        }
+        best = ai;
+        bd = 0.0;
+        for (c = 0; c < k; ++c) {
+            double v, thr;
+            if (c == ai) continue;
+            /* Clause 2 (1/2 d(c_a, c)) and the fourth test (l(x, c)). */
+            thr = halfD[(size_t)ai * k + c] > li[c] ? halfD[(size_t)ai * k + c] : li[c];
+            if (ui * (1.0 + kappa) + tau < thr) continue;
+            if (!tight) {
+                /* Clause 3: tighten u to the exact d(v, c_a) and retest. */
+                bd = oracle_dist2(x, C + (size_t)ai * d, d);
+                evals += 1;
+                ui = oracle_dist_up(bd, g);
+                li[ai] = oracle_dist_down(bd, g);
+                tight = 1;
+                if (ui * (1.0 + kappa) + tau < thr) continue;
+            }
+            v = oracle_dist2(x, C + (size_t)c * d, d);
+            evals += 1;
+            li[c] = oracle_dist_down(v, g);
+            if (v < bd || (v == bd && c < best)) { bd = v; best = c; }
+        }
+        if (best != ai) changed += 1;
+        a[i] = best;
+        u[i] = tight ? oracle_dist_up(bd, g) : ui;
+    }
+    if (skipped_out) *skipped_out = skipped;
+    if (evals_out) *evals_out = evals;
+    if (viol_out) *viol_out = viol;
+    return changed;
+}
+
+/* ------------------------------------------------------------------ */
 /* A whole run.                                                         */
 /* ------------------------------------------------------------------ */
 
 /* Lloyd's algorithm from C0 for at most max_iters iterations, stopping after
  * the first iteration in which no assignment changes (reading R6).
- *   prune       0: unpruned scans; 1: MTI.
+ *   prune       0: unpruned scans; 1: MTI; 2: Elkan (MTI plus lower bounds).
  *   C_out       k*d final centroids.
  *   a_out       n final assignments.
  *   a_hist      NULL or max_iters*n: assignments after each iteration.
  *   C_hist      NULL or (max_iters+1)*k*d: C^0 then the centroids after each
  *               iteration.
  *   changed/skipped/evals  NULL or max_iters per-iteration counters.
+ *   viol_out    NULL or max_iters: Elkan's bound check (see oracle_elkan_iter);
+ *               0 for the other modes.
  * Returns the number of iterations executed. */
 int oracle_run(const float *X, int64_t n, int32_t d, int32_t k, const double *C0,
                int32_t max_iters, int prune, double *C_out, int32_t *a_out,
                int32_t *a_hist, double *C_hist, int64_t *changed_out, int64_t *skipped_out,
-               int64_t *evals_out, int nthreads) {
+               int64_t *evals_out, int64_t *viol_out, int nthreads) {
     size_t kd = (size_t)k * d;
     double *C = (double *)malloc(kd * sizeof(double));
     double *Cp = (double *)malloc(kd * sizeof(double));
@@ -425,14 +548,19 @@ int oracle_run(const float *X, int64_t n, int32_t d, int32_t k, const double *C0
     int32_t *a = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     int32_t *an = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     double *u = (double *)malloc((size_t)n * sizeof(double));
+    double *l = prune == 2 ? (double *)malloc((size_t)n * k * sizeof(double)) : NULL;
     int32_t t, iters = 0;
     int64_t i;
     memcpy(C, C0, kd * sizeof(double));
     if (C_hist) memcpy(C_hist, C0, kd * sizeof(double));
     for (i = 0; i < n; ++i) { a[i] = -1; u[i] = INFINITY; }
     for (t = 0; t < max_iters; ++t) {
-        int64_t changed = 0, skipped = 0, evals = 0;
-        if (prune) {
+        int64_t changed = 0, skipped = 0, evals = 0, viol = 0;
+        if (prune == 2) {
+            oracle_mti_tables(C, t > 0 ? Cp : NULL, d, k, halfD, s, f);
+            changed = oracle_elkan_iter(X, n, d, k, C, halfD, s, f, a, u, l, &skipped, &evals,
+                                        viol_out ? &viol : NULL, nthreads);
+        } else if (prune) {
             oracle_mti_tables(C, t > 0 ? Cp : NULL, d, k, halfD, s, f);
             changed = oracle_mti_iter(X, n, d, k, C, halfD, s, f, a, u, &skipped, &evals,
                                       nthreads);
@@ -452,13 +580,14 @@ int oracle_run(const float *X, int64_t n, int32_t d, int32_t k, const double *C0
         if (changed_out) changed_out[t] = changed;
         if (skipped_out) skipped_out[t] = skipped;
         if (evals_out) evals_out[t] = evals;
+        if (viol_out) viol_out[t] = viol;
         iters = t + 1;
         if (changed == 0) break;
     }
     memcpy(C_out, C, kd * sizeof(double));
     memcpy(a_out, a, (size_t)n * sizeof(int32_t));
     free(C); free(Cp); free(Cn); free(halfD); free(s); free(f);
-    free(a); free(an); free(u);
+    free(a); free(an); free(u); free(l);
     return iters;
 }
 

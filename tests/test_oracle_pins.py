@@ -389,3 +389,38 @@ def test_means_hand_values():
     assert list(cnt) == [3, 2, 0]
 
 
+
+
+# ---------------------------------------------------------------- Elkan ----
+
+@pytest.mark.parametrize("name,seed,n,d,k", [("spd", 31, 3000, 8, 7), ("aniso", 32, 2500, 16, 12),
+                                              ("uniform", 33, 2000, 4, 9)])
+def test_elkan_equals_unpruned_and_prunes_more_than_mti(name, seed, n, d, k):
+    """Pin: Elkan's algorithm (MTI's tests plus per-centroid lower bounds)
+    reaches exactly the unpruned result at every iteration.  Also checked
+    (a property of these inputs, not a theorem: Elkan's upper bound is only
+    tightened when a centroid survives the tests, so its Clause 1 can skip
+    fewer points than MTI's): it computes no more distances than MTI in any
+    iteration, and fewer over the run."""
+    X = synth.make({"spd": "spd", "aniso": "aniso", "uniform": "uniform"}[name], n, d, k, seed).numpy()
+    C0 = oracle.forgy_centroids(X, k, 42)
+    e = oracle.run(X, C0, 60, prune="elkan", history=True)
+    m = oracle.run(X, C0, 60, prune=True, history=True)
+    u = oracle.run(X, C0, 60, prune=False, history=True)
+    assert e.iters == u.iters == m.iters
+    assert np.array_equal(e.a_hist, u.a_hist)
+    assert np.array_equal(e.C_hist, u.C_hist)
+    assert np.all(e.evals <= m.evals)
+    assert e.evals[1:].sum() < m.evals[1:].sum()
+
+
+def test_elkan_bounds_hold_every_iteration():
+    """Pin (triangle inequality): before each Elkan iteration uses them, every
+    lower bound l(x, c) is at most the exact d(x, c) and every upper bound is
+    at least the exact distance to the assigned centroid (the oracle checks
+    them against FP64 distances over all dimensions)."""
+    for seed, (n, d, k) in ((41, (3000, 8, 10)), (42, (1500, 32, 6))):
+        X = synth.spd_mixture(n, d, k, seed).numpy()
+        r = oracle.run(X, oracle.forgy_centroids(X, k, 42), 40, prune="elkan")
+        assert r.iters > 3
+        assert np.all(r.violations == 0), r.violations
