@@ -78,8 +78,19 @@ typedef struct {
     int32_t full_recompute_every; /* 0: never; m > 0: rebuild the cluster sums
                                      from all points every m-th iteration */
     int32_t debug_invariants;     /* 1: after each MTI iteration, check on the
-                                     GPU that every bound u >= d(x, c_a) and count
+                                     GPU that every bound u >= d(x, c_a) (with
+                                     elkan, also every lower bound) and count
                                      violations into knor_iter_stats.violations */
+    int32_t elkan;                /* 1: Elkan's algorithm instead of MTI -- MTI's
+                                     tests plus a lower bound l(x, c) per point and
+                                     centroid (the fourth test, which the paper's
+                                     MTI leaves out: c is ruled out when u <
+                                     l(x, c)); an ablation that keeps an n x k FP32
+                                     matrix (4nk bytes).  Needs FP32 distances,
+                                     pruning, full_recompute_every = 0, d in {8,
+                                     16, 32, 64}, k <= 110 and k*d <= 8192;
+                                     KNOR_ERR_ARG otherwise.  Assignments equal
+                                     MTI's and plain Lloyd's. */
 } knor_opts;
 
 /* Per-iteration counters. */

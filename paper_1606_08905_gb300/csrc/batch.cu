@@ -1255,8 +1255,8 @@ knor_status knor_batch_create(int32_t m, const float *const *points, const int64
     }
     knor_opts o{};
     if (opts) o = *opts;
-    if (o.precision != KNOR_PREC_FP32 || o.full_recompute_every != 0) {
-        set_global_error("knor_batch_create: the batched form supports FP32 distances and delta sums only");
+    if (o.precision != KNOR_PREC_FP32 || o.full_recompute_every != 0 || o.elkan != 0) {
+        set_global_error("knor_batch_create: the batched form supports FP32 distances, delta sums and MTI only");
         return KNOR_ERR_ARG;
     }
     for (int32_t i = 0; i < m; ++i) {

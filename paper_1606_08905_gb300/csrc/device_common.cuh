@@ -203,6 +203,12 @@ __device__ __forceinline__ float bound_up(float d2, float g_up, float tiny) {
     return __fsqrt_ru(__fmaf_ru(d2, g_up, tiny));
 }
 
+// Lower bound on the exact distance whose square was computed as d2 (the
+// other side of bound_up): the exact square is at least (d2 - tiny) g^-1.
+__device__ __forceinline__ float bound_down(float d2, float ginv_dn, float tiny) {
+    return __fsqrt_rd(__fmul_rd(fmaxf(__fsub_rd(d2, tiny), 0.0f), ginv_dn));
+}
+
 // Error-free transformation of hi + x (Knuth's TwoSum): hi gets the rounded
 // sum, lo collects the exact rounding error, so hi + lo carries the running
 // sum to about FP32^2 precision.

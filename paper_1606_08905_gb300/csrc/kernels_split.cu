@@ -19,6 +19,8 @@
 //             cluster).
 // k_dense_scan  the full scan (plain Lloyd, the first MTI iteration) over the
 //             same warp ranges, appending its changed points to the same lists.
+// k_elkan_scan  Elkan's algorithm (MTI plus per-centroid lower bounds), the
+//             ablation the paper leaves out, on the same ranges and lists.
 // k_mti_delta Phase II by deltas: the rows of the change lists are added to
 //             their new clusters and subtracted from their old ones (TwoSum
 //             pairs in shared memory), each list split over a few warps.
@@ -460,6 +462,12 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
             bd[q] = CUDART_INF_F;
             best[q] = 0;
         }
+        // Elkan's lower bounds, when kept: every distance of a full scan sets one
+        auto keep = [&](int q, int c, float r) {
+            const int rr = q * 32 + lane;
+            if (p.lb != nullptr && rr < rows)
+                p.lb[(size_t)c * p.n + base + rr] = __fadd_rd(bound_down(r, p.ginv_dn, p.tiny), F_s[c]);
+        };
         int c = 0;
         for (; c + 2 <= k; c += 2) {
 #pragma unroll
@@ -468,6 +476,8 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
                 d2_reg2<DV>(x2[q], cent + (size_t)c * DV, cent + (size_t)(c + 1) * DV, r0, r1);
                 if (r0 < bd[q]) { bd[q] = r0; best[q] = c; }
                 if (r1 < bd[q]) { bd[q] = r1; best[q] = c + 1; }
+                keep(q, c, r0);
+                keep(q, c + 1, r1);
             }
         }
         for (; c < k; ++c) {
@@ -475,6 +485,7 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
             for (int q = 0; q < DS_P; ++q) {
                 const float r = d2_reg<DV>(x2[q], cent + (size_t)c * DV);
                 if (r < bd[q]) { bd[q] = r; best[q] = c; }
+                keep(q, c, r);
             }
         }
 #pragma unroll
@@ -504,6 +515,133 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
         atomicAdd(&p.ctr->changed, (unsigned long long)my_changed);
         atomicAdd(&p.ctr->evals, (unsigned long long)((hi - lo) * (int64_t)k));
     }
+}
+
+// ------------------------------------------------------------ Elkan's scan
+
+// Elkan's algorithm as an ablation of MTI: the same Clause 1 on the same
+// upper bound, then for every other centroid c the fourth test besides
+// Clause 2 -- c is ruled out when u is below max(1/2 d(c_a, c), l(x, c)),
+// with l(x, c) = lb[c][x] - F(c) rounded down -- tightening u (Clause 3) the
+// first time a centroid survives; every computed distance refreshes its
+// lower bound.  One point per lane, 32-point tiles of warp w's range (the
+// split grid's ranges), so the lower-bound loads of a warp are coalesced;
+// the points that changed cluster go to change list w for k_mti_delta.
+template <int DV>
+__global__ void __launch_bounds__(SPT) k_elkan_scan(const IterParams p, const int32_t *mode_dense) {
+    if (*mode_dense != 0) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = p.k;
+    float *cent = reinterpret_cast<float *>(sm + p.off_cent);
+    float *halfD = reinterpret_cast<float *>(sm + p.off_halfD);
+    float *s_s = reinterpret_cast<float *>(sm + p.off_s);
+    float *F_s = reinterpret_cast<float *>(sm + p.off_F);
+    for (int e = tid; e < k * DV; e += SPT) cent[e] = p.C32[e];
+    for (int e = tid; e < k * k; e += SPT) halfD[e] = p.halfD[e];
+    for (int c = tid; c < k; c += SPT) { s_s[c] = p.s[c]; F_s[c] = p.F[c]; }
+    __syncthreads();
+    const int gw = blockIdx.x * SPW + w, nw = gridDim.x * SPW;
+    int64_t lo, hi;
+    warp_range(p.n, gw, nw, lo, hi);
+    int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32;
+    int nchg = 0;
+    unsigned my_skipped = 0, my_evals = 0, my_changed = 0;
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t i = base + lane;
+        bool changed = false;
+        int a = -1, best = -1;
+        if (i < hi) {
+            const PtState ps = p.st[i];
+            a = ps.a;
+            bool active = true;
+            float u = 0.0f, tst = 0.0f;
+            if (a >= 0) {
+                u = __fadd_ru(ps.ub, F_s[a]); // u^t = ub + F^t(a)
+                tst = __fmaf_ru(u, p.onepk, p.tau);
+                active = !(tst < s_s[a]); // Clause 1
+            }
+            if (!active) {
+                ++my_skipped;
+            } else {
+                unsigned long long xk[DV / 2];
+                if constexpr (DV % 8 == 0) ldg_x2_w32<DV>(xk, p.X + i * DV);
+                else ldg_x2<DV>(xk, p.X + i * DV);
+                float bd = CUDART_INF_F;
+                bool tight = false;
+                if (a < 0) { // no assignment yet: every distance, every bound
+                    best = 0;
+                    for (int c = 0; c < k; ++c) {
+                        const float r = d2_reg<DV>(xk, cent + (size_t)c * DV);
+                        p.lb[(size_t)c * p.n + i] = __fadd_rd(bound_down(r, p.ginv_dn, p.tiny), F_s[c]);
+                        if (r < bd) { bd = r; best = c; }
+                    }
+                    my_evals += k;
+                    tight = true;
+                } else {
+                    best = a;
+                    for (int c = 0; c < k; ++c) {
+                        if (c == a) continue;
+                        const float l = __fsub_rd(p.lb[(size_t)c * p.n + i], F_s[c]);
+                        const float thr = fmaxf(halfD[(size_t)a * k + c], l);
+                        if (tst < thr) continue; // Clause 2 or the fourth test
+                        if (!tight) {
+                            // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
+                            bd = d2_reg<DV>(xk, cent + (size_t)a * DV);
+                            ++my_evals;
+                            p.lb[(size_t)a * p.n + i] = __fadd_rd(bound_down(bd, p.ginv_dn, p.tiny), F_s[a]);
+                            tst = __fmaf_ru(bound_up(bd, p.g_up, p.tiny), p.onepk, p.tau);
+                            tight = true;
+                            if (tst < thr) continue;
+                        }
+                        const float r = d2_reg<DV>(xk, cent + (size_t)c * DV);
+                        ++my_evals;
+                        p.lb[(size_t)c * p.n + i] = __fadd_rd(bound_down(r, p.ginv_dn, p.tiny), F_s[c]);
+                        if (r < bd || (r == bd && c < best)) { bd = r; best = c; }
+                    }
+                }
+                if (tight) { // otherwise u stays as it was (no write)
+                    PtState ns;
+                    ns.a = best;
+                    ns.ub = __fsub_ru(bound_up(bd, p.g_up, p.tiny), F_s[best]);
+                    p.st[i] = ns;
+                }
+                changed = best != a;
+            }
+        }
+        const unsigned cm = __ballot_sync(FULL_MASK, changed);
+        if (changed)
+            chg[nchg + __popc(cm & ((1u << lane) - 1u))] =
+                make_int2((int)i, (int)(((unsigned)best << 16) | ((unsigned)a & 0xFFFFu)));
+        nchg += __popc(cm);
+        my_changed += __popc(cm);
+    }
+    const long long t1 = sp_warp_sum((long long)my_skipped);
+    const long long t2 = sp_warp_sum((long long)my_evals);
+    if (lane == 0) {
+        p.chg_cnt[gw] = nchg;
+        atomicAdd(&p.ctr->changed, (unsigned long long)my_changed);
+        atomicAdd(&p.ctr->skipped, (unsigned long long)t1);
+        atomicAdd(&p.ctr->evals, (unsigned long long)t2);
+    }
+}
+
+// Debug check of Elkan's lower bounds after an iteration: a bound above an
+// upper bound on the exact distance (from the FP32 distance and its error
+// bound) is counted as a violation of the run's current record.
+template <int DV>
+__global__ void k_elkan_check(const IterParams p, IterStats *stats, const int32_t *run_iter) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    unsigned long long xk[DV / 2];
+    ldg_x2<DV>(xk, p.X + i * DV);
+    unsigned bad = 0;
+    for (int c = 0; c < p.k; ++c) {
+        const float r = d2_reg<DV>(xk, p.C32 + (size_t)c * DV);
+        const float l = __fsub_rd(p.lb[(size_t)c * p.n + i], p.F[c]);
+        if (l > bound_up(r, p.g_up, p.tiny)) ++bad;
+    }
+    if (bad) atomicAdd(reinterpret_cast<unsigned long long *>(&stats[*run_iter - 1].violations), bad);
 }
 
 // ------------------------------------------------------------ delta sums
@@ -654,6 +792,34 @@ cudaError_t dense_scan_attr(int dv, size_t smem, int *bps) { KNOR_DVSP_SWITCH(dv
 cudaError_t launch_dense_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
                               const int32_t *md) {
     KNOR_DVSP_SWITCH(dv, dense_scan_launch_t, p, grid, smem, s, md)
+}
+
+template <int DV>
+static cudaError_t elkan_scan_attr_t(size_t smem, int *bps) {
+    cudaError_t e = cudaFuncSetAttribute(k_elkan_scan<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_elkan_scan<DV>, SPT, smem);
+}
+template <int DV>
+static cudaError_t elkan_scan_launch_t(const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                                       const int32_t *md) {
+    k_elkan_scan<DV><<<grid, SPT, smem, s>>>(p, md);
+    return cudaGetLastError();
+}
+template <int DV>
+static cudaError_t elkan_check_launch_t(const IterParams &p, IterStats *stats, const int32_t *run_iter,
+                                        cudaStream_t s) {
+    k_elkan_check<DV><<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p, stats, run_iter);
+    return cudaGetLastError();
+}
+cudaError_t elkan_scan_attr(int dv, size_t smem, int *bps) { KNOR_DVSP_SWITCH(dv, elkan_scan_attr_t, smem, bps) }
+cudaError_t launch_elkan_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                              const int32_t *md) {
+    KNOR_DVSP_SWITCH(dv, elkan_scan_launch_t, p, grid, smem, s, md)
+}
+cudaError_t launch_elkan_check(int dv, const IterParams &p, IterStats *stats, const int32_t *run_iter,
+                               cudaStream_t s) {
+    KNOR_DVSP_SWITCH(dv, elkan_check_launch_t, p, stats, run_iter, s)
 }
 
 cudaError_t mti_delta_attr(int dv, size_t smem, int split, int *bps) {

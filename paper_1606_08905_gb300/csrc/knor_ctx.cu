@@ -93,7 +93,7 @@ struct StateHeader {
     uint32_t magic, version;
     int64_t n;
     int32_t d, k;
-    int32_t no_prune, precision, recompute, total_iter, mode_dense, pad;
+    int32_t no_prune, precision, recompute, total_iter, mode_dense, pad; // pad: the elkan option
 };
 
 } // namespace
@@ -140,6 +140,7 @@ struct knor_ctx {
     float *wacc = nullptr; // k_mti_w warp accumulators
     int32_t *rec = nullptr, *rec_cnt = nullptr, *chg_cnt = nullptr; // split MTI scan: batch records
     int2 *chg = nullptr;                                                // and change lists
+    float *lb = nullptr;                                                // Elkan's lower bounds
     IterParams ip_sel{}, ip_delta{};
     size_t smem_sel = 0;
     bool mti_split = false, dense_split = false; // the split kernels run the MTI / dense scans
@@ -219,7 +220,7 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
-                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma, c->rec, c->rec_cnt, c->chg, c->chg_cnt,
+                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma, c->rec, c->rec_cnt, c->chg, c->chg_cnt, c->lb,
                     c->xdn != c->xn ? c->xdn : nullptr, c->rxdn != c->rxn ? c->rxdn : nullptr};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -389,6 +390,7 @@ static size_t plan_layout_scan(const knor_ctx *c, IterParams &p) {
     p.off_cent = take(kd * 4);
     p.off_halfD = take((size_t)k * k * 4);
     p.off_F = take((size_t)k * 4);
+    p.off_s = take((size_t)k * 4);
     // rows padded by 16 bytes: lane l reads its row at l * (4d + 16) bytes,
     // so the 8 lanes of a 16-byte shared load hit distinct banks
     p.sp_rs = d + 4;
@@ -446,6 +448,8 @@ static cudaError_t scan_dense(knor_ctx *c, cudaStream_t s) {
 
 static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
     int32_t *fl = c->flags;
+    if (c->mti_split && c->opts.elkan)
+        return launch_elkan_scan(c->dv, c->ip_mti, c->grid_split, c->smem_mti, s, fl + F_MODE_DENSE);
     if (c->mti_split)
         return launch_mti_scan(c->dv, c->ip_mti, c->grid_split, c->smem_mti, s, fl + F_MODE_DENSE, fl + F_NSLOTS,
                                fl + F_FRESH);
@@ -458,7 +462,7 @@ static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
 
 // Clause 1 and the batch records of the split MTI scan.
 static cudaError_t scan_select(knor_ctx *c, cudaStream_t s) {
-    if (!c->mti_split) return cudaSuccess;
+    if (!c->mti_split || c->opts.elkan) return cudaSuccess;
     return launch_mti_sel(c->ip_sel, c->grid_split, c->smem_sel, s, c->flags + F_MODE_DENSE);
 }
 
@@ -536,6 +540,8 @@ static knor_status enqueue_iteration(knor_ctx *c, cudaStream_t s, unsigned long 
                               c->opts.no_prune ? 1 : 0, s));
     if (c->opts.debug_invariants && !c->opts.no_prune)
         KNOR_CUDA(c, launch_check_bounds(c->X, c->n, c->d, c->st, c->C32, c->F, c->stats, fl + F_RUN_ITER, s));
+    if (c->opts.debug_invariants && c->opts.elkan)
+        KNOR_CUDA(c, launch_elkan_check(c->dv, c->ip_mti, c->stats, fl + F_RUN_ITER, s));
     return KNOR_OK;
 }
 
@@ -585,7 +591,7 @@ static knor_status profiled_iteration(knor_ctx *c) {
         ks = timed(KNOR_KERNEL_DENSE, scan_dense);
         if (ks == KNOR_OK && c->dense_split) ks = timed(KNOR_KERNEL_DELTA, scan_delta);
     } else {
-        if (c->mti_split) ks = timed(KNOR_KERNEL_SELECT, scan_select);
+        if (c->mti_split && !c->opts.elkan) ks = timed(KNOR_KERNEL_SELECT, scan_select);
         if (ks == KNOR_OK) ks = timed(KNOR_KERNEL_MTI, scan_mti);
         if (ks == KNOR_OK && c->mti_split) ks = timed(KNOR_KERNEL_DELTA, scan_delta);
     }
@@ -602,6 +608,8 @@ static knor_status profiled_iteration(knor_ctx *c) {
     used[KNOR_KERNEL_REDUCE] = used[KNOR_KERNEL_TABLE] = true;
     if (c->opts.debug_invariants && !c->opts.no_prune)
         KNOR_CUDA(c, launch_check_bounds(c->X, c->n, c->d, c->st, c->C32, c->F, c->stats, fl + F_RUN_ITER, s));
+    if (c->opts.debug_invariants && c->opts.elkan)
+        KNOR_CUDA(c, launch_elkan_check(c->dv, c->ip_mti, c->stats, fl + F_RUN_ITER, s));
     KNOR_CUDA(c, cudaStreamSynchronize(s));
     for (int kk = 0; kk < KNOR_KERNEL_COUNT; ++kk) {
         if (!used[kk]) continue;
@@ -732,6 +740,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         return KNOR_ERR_ARG;
     }
     if (o.full_recompute_every < 0) { g_create_err = "knor_create: full_recompute_every < 0"; return KNOR_ERR_ARG; }
+    if (o.elkan && (o.no_prune || tc_form || o.full_recompute_every != 0)) {
+        g_create_err = "knor_create: elkan needs pruning, FP32 distances and full_recompute_every = 0";
+        return KNOR_ERR_ARG;
+    }
 
     knor_ctx *c = new knor_ctx();
     c->n = n; c->d = d; c->k = k; c->opts = o; c->init = init; c->seed = seed;
@@ -785,7 +797,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         // one-kernel warp scan, for comparisons) and the dense scan (unless
         // full_recompute_every asks for sums rebuilt from every point).
         IterParams ps{};
-        const int choice = getenv_int("KNOR_MTI_KERNEL", 0);
+        const int choice = o.elkan ? 0 : getenv_int("KNOR_MTI_KERNEL", 0);
         const size_t ssc = !tc_form ? plan_layout_scan(c, ps) : 0;
         int bsplit = 0;
         if (ssc) {
@@ -798,6 +810,14 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         }
         c->mti_split = bsplit > 0 && choice == 0 && !o.no_prune;
         c->dense_split = bsplit > 0 && o.full_recompute_every == 0;
+        if (o.elkan) {
+            int be = 0;
+            if (bsplit > 0) KCU(elkan_scan_attr(c->dv, ssc, &be));
+            if (be < bsplit) {
+                c->err = "knor_create: elkan needs d in {8, 16, 32, 64}, k <= 110 and k*d <= 8192";
+                return bail(KNOR_ERR_ARG);
+            }
+        }
         IterParams pw{}, pm{};
         if (c->dense_split) {
             // the dense scan's warps stage DS_ROWS-row tiles, double-buffered
@@ -864,6 +884,16 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         KC(dalloc(c, &c->chg, (size_t)(nw * cap * 32)));
         KC(dalloc(c, &c->chg_cnt, (size_t)nw));
         fill_common(c, c->ip_sel);
+        if (o.elkan) {
+            // Elkan's lower bounds, n x k, cluster-major
+            KC(dalloc(c, &c->lb, (size_t)n * k));
+            const float ginv = (float)(1.0 - (d + 2) * std::ldexp(1.0, -24));
+            const float ginv_dn = (double)ginv > 1.0 - (d + 2) * std::ldexp(1.0, -24) ? std::nextafter(ginv, 0.0f) : ginv;
+            for (IterParams *q : {&c->ip_mti, &c->ip_dense}) {
+                q->lb = c->lb;
+                q->ginv_dn = ginv_dn;
+            }
+        }
         c->ip_delta = c->mti_split ? c->ip_mti : c->ip_dense;
         for (IterParams *q : {&c->ip_mti, &c->ip_sel, &c->ip_dense, &c->ip_delta}) {
             q->rec = c->rec;
@@ -883,10 +913,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         const std::string w = "<" + std::to_string(c->dv) + ">";
         c->kname[KNOR_KERNEL_DENSE] =
             c->dense_split ? "k_dense_scan" + w : (c->ip_dense.warp_kernels ? "k_dense_w" : "k_dense") + w;
-        if (c->mti_split) c->kname[KNOR_KERNEL_SELECT] = "k_mti_sel";
+        if (c->mti_split && !o.elkan) c->kname[KNOR_KERNEL_SELECT] = "k_mti_sel";
         if (c->mti_split || c->dense_split) c->kname[KNOR_KERNEL_DELTA] = "k_mti_delta" + w;
         c->kname[KNOR_KERNEL_MTI] =
-            (c->mti_split ? "k_mti_scan" : c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
+            (c->mti_split ? (o.elkan ? "k_elkan_scan" : "k_mti_scan") : c->ip_mti.warp_kernels ? "k_mti_w" : "k_mti") + w;
         c->kname[KNOR_KERNEL_REDUCE] = "k_reduce";
         c->kname[KNOR_KERNEL_TABLE] = "k_table";
     }
@@ -1197,7 +1227,8 @@ knor_status knor_get_iteration(const knor_ctx *cc, int32_t *out) {
 static size_t state_size(const knor_ctx *c) {
     const size_t kd = (size_t)c->k * c->d, k = (size_t)c->k;
     return sizeof(StateHeader) + 3 * kd * sizeof(double) + k * sizeof(long long) + kd * sizeof(float) +
-           k * sizeof(float) + k * k * sizeof(float) + k * sizeof(float) + (size_t)c->n * sizeof(PtState);
+           k * sizeof(float) + k * k * sizeof(float) + k * sizeof(float) + (size_t)c->n * sizeof(PtState) +
+           (c->lb ? (size_t)c->n * k * sizeof(float) : 0);
 }
 
 knor_status knor_get_state(const knor_ctx *cc, void *buf, size_t *size) {
@@ -1210,15 +1241,17 @@ knor_status knor_get_state(const knor_ctx *cc, void *buf, size_t *size) {
     int32_t fl[F_COUNT];
     KNOR_CUDA(c, cudaMemcpy(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost));
     StateHeader h{kStateMagic, kStateVersion, c->n, c->d, c->k, c->opts.no_prune, c->opts.precision,
-                  c->opts.full_recompute_every, fl[F_TOTAL_ITER], fl[F_MODE_DENSE], 0};
+                  c->opts.full_recompute_every, fl[F_TOTAL_ITER], fl[F_MODE_DENSE], c->opts.elkan};
     char *p = static_cast<char *>(buf);
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     const size_t kd = (size_t)c->k * c->d, k = (size_t)c->k;
     struct Part { const void *src; size_t bytes; } parts[] = {
         {c->C0, kd * 8}, {c->C64, kd * 8}, {c->S, kd * 8}, {c->cnt, k * 8}, {c->C32, kd * 4}, {c->F, k * 4},
-        {c->halfD, k * k * 4}, {c->s, k * 4}, {c->st, (size_t)c->n * sizeof(PtState)}};
+        {c->halfD, k * k * 4}, {c->s, k * 4}, {c->st, (size_t)c->n * sizeof(PtState)},
+        {c->lb, c->lb ? (size_t)c->n * k * 4 : 0}};
     for (auto &pt : parts) {
+        if (!pt.bytes) continue;
         KNOR_CUDA(c, cudaMemcpyAsync(p, pt.src, pt.bytes, cudaMemcpyDeviceToHost, c->stream));
         p += pt.bytes;
     }
@@ -1235,14 +1268,16 @@ knor_status knor_set_state(knor_ctx *c, const void *buf, size_t size) {
     std::memcpy(&h, buf, sizeof(h));
     if (h.magic != kStateMagic || h.version != kStateVersion || h.n != c->n || h.d != c->d || h.k != c->k ||
         h.no_prune != c->opts.no_prune || h.precision != c->opts.precision ||
-        h.recompute != c->opts.full_recompute_every)
+        h.recompute != c->opts.full_recompute_every || h.pad != c->opts.elkan)
         return fail(c, KNOR_ERR_ARG, "knor_set_state: state is from a context with other sizes or options");
     const char *p = static_cast<const char *>(buf) + sizeof(h);
     const size_t kd = (size_t)c->k * c->d, k = (size_t)c->k;
     struct Part { void *dst; size_t bytes; } parts[] = {
         {c->C0, kd * 8}, {c->C64, kd * 8}, {c->S, kd * 8}, {c->cnt, k * 8}, {c->C32, kd * 4}, {c->F, k * 4},
-        {c->halfD, k * k * 4}, {c->s, k * 4}, {c->st, (size_t)c->n * sizeof(PtState)}};
+        {c->halfD, k * k * 4}, {c->s, k * 4}, {c->st, (size_t)c->n * sizeof(PtState)},
+        {c->lb, c->lb ? (size_t)c->n * k * 4 : 0}};
     for (auto &pt : parts) {
+        if (!pt.bytes) continue;
         KNOR_CUDA(c, cudaMemcpyAsync(pt.dst, p, pt.bytes, cudaMemcpyHostToDevice, c->stream));
         p += pt.bytes;
     }

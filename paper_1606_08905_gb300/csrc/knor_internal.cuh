@@ -129,6 +129,12 @@ struct IterParams {
     int32_t dl_warp_stride, dl_split; // k_mti_delta: per-warp region, warps per change list
     int32_t dl_dense;      // 1: dense iterations sum by change lists (k_dense_scan)
     int32_t dl_mti;        // 1: MTI iterations sum by change lists (k_mti_scan)
+    // Elkan's lower bounds (ablation of MTI): n x k FP32, cluster-major
+    // (lb[c n + i]); each stored as l + F(c) rounded down, where l <= d(x_i, c)
+    // when stored and F is the cumulative drift, so that lb - F^t(c) bounds
+    // d(x_i, c^t) from below; null when not kept
+    float *lb;
+    float ginv_dn;         // <= (1 - (d+2) 2^-24): turns a computed d^2 into a lower bound
 };
 
 // Parameters of the reduction / finalize kernels.
@@ -228,6 +234,12 @@ cudaError_t mti_delta_attr(int dv, size_t smem, int split, int *blocks_per_sm);
 cudaError_t launch_dense_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
                               const int32_t *mode_dense);
 cudaError_t dense_scan_attr(int dv, size_t smem, int *blocks_per_sm);
+// Elkan's scan (MTI plus lower bounds) on the split grid, and its bound check
+cudaError_t launch_elkan_scan(int dv, const IterParams &p, int grid, size_t smem, cudaStream_t s,
+                              const int32_t *mode_dense);
+cudaError_t elkan_scan_attr(int dv, size_t smem, int *blocks_per_sm);
+cudaError_t launch_elkan_check(int dv, const IterParams &p, IterStats *stats, const int32_t *run_iter,
+                               cudaStream_t s);
 cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32_t *fresh, cudaStream_t s);
 cudaError_t launch_table(const FinParams &f, int32_t *mode_dense, int need_table, int recompute_every,
                          int always_dense, cudaStream_t s);
