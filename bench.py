@@ -207,7 +207,7 @@ def cpu_sample_rows(wl, seconds, X=None, threads=1):
     else:
         from paper_1606_08905_gb300 import synth
         Xp = synth.make(wl["kind"], probe, wl["d"], wl["k"], wl["data_seed"], device="cpu").numpy()
-    p, dt, _ = cpu_oracle_run(Xp, wl["k"], wl["max_iters"], wl["prune"], threads)
+    p, dt, _ = cpu_oracle_run(Xp, wl["k"], wl["max_iters"], ("elkan" if wl.get("elkan") else wl["prune"]), threads)
     rate = p / max(dt, 1e-3)
     return int(max(20_000, min(wl["n"], rate * seconds / wl["max_iters"])))
 
@@ -239,10 +239,10 @@ def reference_arm(args, wl, world, rank):
     ns = cpu_sample_rows(wl, per_step, None, threads)
     Xs = synth.make(wl["kind"], ns, wl["d"], wl["k"], wl["data_seed"], device="cpu").numpy()
     for _ in range(args.warmup):
-        cpu_oracle_run(Xs, wl["k"], wl["max_iters"], wl["prune"], threads)
+        cpu_oracle_run(Xs, wl["k"], wl["max_iters"], ("elkan" if wl.get("elkan") else wl["prune"]), threads)
     pts, secs, its = 0, 0.0, []
     for _ in range(args.steps):
-        p, dt, it = cpu_oracle_run(Xs, wl["k"], wl["max_iters"], wl["prune"], threads)
+        p, dt, it = cpu_oracle_run(Xs, wl["k"], wl["max_iters"], ("elkan" if wl.get("elkan") else wl["prune"]), threads)
         pts += p
         secs += dt
         its.append(it)
@@ -472,6 +472,8 @@ def batch_arm(args, wl, world, rank, local):
                 "iterations_per_step": iters, "roofline": roof, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "vs_plain_fp32": plain,
                 "gpu_launches": launches, "clocks": clk}
+        if vs_mti is not None:
+            line["elkan_vs_mti"] = vs_mti
         print(json.dumps(line), flush=True)
 
 
@@ -498,7 +500,8 @@ def config_of(wl, name, world):
     return {"workload": name if wl["n"] == synth_n(name) else f"{name} (n overridden)", "n": wl["n"],
             "distance": (wl["precision"].upper() + " tensor cores + exact FP32 recheck"
                          if wl.get("precision", "fp32") != "fp32" else "FP32"), "d": wl["d"], "k": wl["k"], "max_iters": wl["max_iters"],
-            "pruning": "MTI" if wl["prune"] else "none", "init": "Forgy, seed 42",
+            "pruning": ("Elkan (MTI + lower bounds)" if wl.get("elkan") else "MTI") if wl["prune"] else "none",
+            "init": "Forgy, seed 42",
             "data_seed": wl["data_seed"], "points_dtype": "f32",
             "l2": l2_note(wl["n"] * wl["d"] * 4),
             "parallelism": f"replicas x{world}"}
@@ -518,7 +521,8 @@ def our_arm(args, wl, world, rank, local):
     X = make_points(wl, "cuda")
     torch.cuda.synchronize()
     prec = wl.get("precision", "fp32")
-    ctx = knor.Context(X, k, seed=42, prune=wl["prune"], precision=prec)
+    elkan = bool(wl.get("elkan", False))
+    ctx = knor.Context(X, k, seed=42, prune=wl["prune"], precision=prec, elkan=elkan)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     def barrier():
@@ -555,7 +559,7 @@ def our_arm(args, wl, world, rank, local):
     if wl.get("precision", "fp32") != "fp32":
         per_it = 9
     elif "k_mti_delta" in ctx.kernel_name("dense") or "k_mti_delta" in ctx.kernel_name("mti"):
-        per_it = 6 if wl["prune"] else 4
+        per_it = (5 if elkan else 6) if wl["prune"] else 4
     else:
         per_it = 4 if wl["prune"] else 3
     launches = sum(3 + it * per_it for it in iters)
@@ -625,9 +629,17 @@ def our_arm(args, wl, world, rank, local):
         dense_bytes = sum(n * (4 * d + 16) for r in prof_recs if (r["iteration"] == 1 or not wl["prune"]))
         mti_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in prof_recs
                         if wl["prune"] and r["iteration"] > 1)
+        if elkan:
+            # Elkan also reads the k lower bounds of every point Clause 1 does
+            # not skip and writes one per distance it computes; its first
+            # (full) scan writes all n k of them
+            dense_bytes += sum(4 * n * k for r in prof_recs if r["iteration"] == 1)
+            mti_bytes += sum((n - r["clause1_skipped"]) * 4 * k + 4 * r["dist_evals"] for r in prof_recs
+                             if r["iteration"] > 1)
         # FP32 arithmetic of the scans: one subtraction and one fused
         # multiply-add per dimension and distance (the direct form), against
         # the FMA issue rate measured on this GPU now (knor_probe_alu)
+        kernels_bytes = {}
         fma_tflops, _ = knor.probe_alu("fp32")
         fma_ops_peak = fma_tflops * 1e12 / 2.0
         dense_ops = sum(2.0 * d * k * n for r in prof_recs if (r["iteration"] == 1 or not wl["prune"]))
@@ -641,6 +653,9 @@ def our_arm(args, wl, world, rank, local):
                 ctx.kernel_name(nm): {"launches": v[0], "ms_total": v[1]} for nm, v in parts.items()}
         for name, byts, ops in (("dense", dense_bytes, dense_ops), ("mti", mti_bytes, mti_ops)):
             launches_k, ms_k, parts = step(name, ("dense", "delta") if name == "dense" else ("select", "mti", "delta"))
+            if launches_k == 0 or ms_k <= 0:
+                continue
+            kernels_bytes[name] = byts
             if launches_k == 0 or ms_k <= 0:
                 continue
             gbs = byts / (ms_k / 1000.0) / 1e9
@@ -678,6 +693,42 @@ def our_arm(args, wl, world, rank, local):
                     "traffic": ncu_traffic(kname, args.workload) if not args.n else None,
                     "alu_frac": kd["alu"]["frac"]}
         roof["share_of_kernel_time"] = kd["ms_total"] / total_prof_ms
+
+    # ---- Elkan's ablation: MTI on the same points, the same measurements
+    vs_mti = None
+    if elkan:
+        ctx.reset()
+        _, e_recs = ctx.run(T)
+        a_e = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.assignments(a_e)
+        with knor.Context(X, k, seed=42, prune=True) as mc:
+            ms_ = torch.cuda.ExternalStream(mc.stream)
+            mc.run(T)
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(ms_)
+            msteps, mits = max(1, min(args.steps, 3)), 0
+            for _ in range(msteps):
+                mc.reset()
+                done_m, m_recs = mc.run(T)
+                mits += done_m
+            q1.record(ms_)
+            torch.cuda.synchronize()
+            a_m = torch.empty(n, dtype=torch.int32, device="cuda")
+            mc.assignments(a_m)
+            m_bytes = sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8) for r in m_recs[1:])
+            vs_mti = {"mti_value": n * mits / (q0.elapsed_time(q1) / 1000.0), "unit": "point-iterations/s",
+                      "elkan_value_over_mti": value / (n * mits / (q0.elapsed_time(q1) / 1000.0)),
+                      "identical_assignments": bool(torch.equal(a_e, a_m)),
+                      "iterations": [len(e_recs), len(m_recs)],
+                      "dist_evals_after_iteration_1": [sum(r["dist_evals"] for r in e_recs[1:]),
+                                                        sum(r["dist_evals"] for r in m_recs[1:])],
+                      "clause1_skipped_after_iteration_1": [sum(r["clause1_skipped"] for r in e_recs[1:]),
+                                                             sum(r["clause1_skipped"] for r in m_recs[1:])],
+                      "algorithmic_bytes_after_iteration_1": [
+                          sum(8 * n + (n - r["clause1_skipped"]) * (4 * d + 8 + 4 * k) + 4 * r["dist_evals"]
+                              for r in e_recs[1:]), m_bytes],
+                      "order": "[elkan, mti]"}
 
     # ---- plain FP32 Lloyd on the same points: speed, and identical assignments
     plain = None
@@ -721,7 +772,7 @@ def our_arm(args, wl, world, rank, local):
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(es):
-            with knor.Context(Xh, k, seed=42, prune=wl["prune"], precision=prec) as c2:
+            with knor.Context(Xh, k, seed=42, prune=wl["prune"], precision=prec, elkan=elkan) as c2:
                 done, _ = c2.run(T)
                 c2.assignments(ah)
                 c2.centroids(Ch)
@@ -739,10 +790,11 @@ def our_arm(args, wl, world, rank, local):
         threads = os.cpu_count() or 1
         ns = cpu_sample_rows(wl, args.cpu_seconds, X, threads)
         Xs = X[:ns].cpu().numpy()
-        p, dt, it = cpu_oracle_run(Xs, k, T, wl["prune"], threads)
+        mode = "elkan" if elkan else wl["prune"]
+        p, dt, it = cpu_oracle_run(Xs, k, T, mode, threads)
         cpu = {"value": p / dt, "unit": "point-iterations/s", "cores": threads, "kind": "oracle",
                "sample": f"first {ns} of the {n} points, one full run ({it} iterations, "
-                         f"{'MTI' if wl['prune'] else 'plain'}, FP64), {dt:.1f} s"}
+                         f"{'Elkan' if elkan else 'MTI' if wl['prune'] else 'plain'}, FP64), {dt:.1f} s"}
 
     if rank == 0:
         line = {"metric": "point-iterations/sec", "value": value, "unit": "point-iterations/s",

@@ -206,12 +206,14 @@ class RunResult:
         self.__dict__.update(kw)
 
 
-def run(X, C0, max_iters: int, prune, history: bool = False, nthreads: int = 0) -> RunResult:
+def run(X, C0, max_iters: int, prune, history: bool = False, nthreads: int = 0,
+        check_bounds: bool = False) -> RunResult:
     """Lloyd's algorithm from C0 (k x d) until no assignment changes or
     max_iters.  prune: False (every distance), True (MTI) or "elkan" (MTI
-    plus per-centroid lower bounds; also checks the bounds every iteration,
-    result.violations).  With history=True also returns a_hist (iters x n)
-    and C_hist ((iters+1) x k x d, C^0 first)."""
+    plus per-centroid lower bounds; with check_bounds=True the bounds are
+    checked against exact distances every iteration, result.violations).
+    With history=True also returns a_hist (iters x n) and C_hist
+    ((iters+1) x k x d, C^0 first)."""
     mode = 2 if prune == "elkan" else (1 if prune else 0)
     X = _X(X)
     n, d = X.shape
@@ -228,7 +230,8 @@ def run(X, C0, max_iters: int, prune, history: bool = False, nthreads: int = 0) 
     it = _load().oracle_run(X, n, d, k, C0, max_iters, mode, C, a,
                             ah.ctypes.data if history else None,
                             Ch.ctypes.data if history else None,
-                            ch.ctypes.data, sk.ctypes.data, ev.ctypes.data, vi.ctypes.data, nthreads)
+                            ch.ctypes.data, sk.ctypes.data, ev.ctypes.data,
+                            vi.ctypes.data if check_bounds else None, nthreads)
     return RunResult(iters=int(it), C=C, a=a, changed=ch[:it].copy(), skipped=sk[:it].copy(),
                      evals=ev[:it].copy(), violations=vi[:it].copy(),
                      a_hist=ah[:it].copy() if history else None,

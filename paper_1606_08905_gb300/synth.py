@@ -187,6 +187,12 @@ WORKLOADS = {
                                       data_seed=1005, max_iters=20, prune=True),
     "scale_1b_d16_k100_mixture": dict(kind="spd_scaled", n=1_000_000_000, d=16, k=100,
                                       data_seed=1006, max_iters=20, prune=True),
+    # Elkan's lower bounds (the ablation of MTI) on the 100k x 8, k = 10
+    # workload's points and on a 16M-point slice of the 66M x 32, k = 20 one
+    "elkan_100k_d8_k10": dict(kind="isotropic", n=100_000, d=8, k=10, data_seed=1001,
+                              max_iters=20, prune=True, elkan=True),
+    "elkan_16m_d32_k20": dict(kind="spd", n=16_000_000, d=32, k=20, data_seed=1002,
+                              max_iters=50, prune=True, elkan=True),
 }
 INIT_SEED = 42
 WORKLOADS["batched_512"]["n"] = sum(s.n for s in batched_specs(512, 1004))

@@ -63,7 +63,7 @@ def test_elkan_counters_match_oracle(name, make, k):
     with knor.Context(torch.as_tensor(X).cuda(), k, seed=42, elkan=True) as c:
         done, recs = c.run(40)
         C0 = X[c.init_indices()].astype(np.float64)
-    ref = oracle.run(X, C0, 40, prune="elkan")
+    ref = oracle.run(X, C0, 40, prune="elkan", check_bounds=True)
     assert np.all(ref.violations == 0)
     slack = 0.002 * n + 10
     for t in range(min(done, ref.iters)):

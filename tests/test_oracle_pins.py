@@ -421,6 +421,6 @@ def test_elkan_bounds_hold_every_iteration():
     them against FP64 distances over all dimensions)."""
     for seed, (n, d, k) in ((41, (3000, 8, 10)), (42, (1500, 32, 6))):
         X = synth.spd_mixture(n, d, k, seed).numpy()
-        r = oracle.run(X, oracle.forgy_centroids(X, k, 42), 40, prune="elkan")
+        r = oracle.run(X, oracle.forgy_centroids(X, k, 42), 40, prune="elkan", check_bounds=True)
         assert r.iters > 3
         assert np.all(r.violations == 0), r.violations
