@@ -813,7 +813,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         if (o.elkan) {
             int be = 0;
             if (bsplit > 0) KCU(elkan_scan_attr(c->dv, ssc, &be));
-            if (be < bsplit) {
+            if (bsplit < 1 || be < bsplit) {
                 c->err = "knor_create: elkan needs d in {8, 16, 32, 64}, k <= 110 and k*d <= 8192";
                 return bail(KNOR_ERR_ARG);
             }
