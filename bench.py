@@ -472,8 +472,6 @@ def batch_arm(args, wl, world, rank, local):
                 "iterations_per_step": iters, "roofline": roof, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "vs_plain_fp32": plain,
                 "gpu_launches": launches, "clocks": clk}
-        if vs_mti is not None:
-            line["elkan_vs_mti"] = vs_mti
         print(json.dumps(line), flush=True)
 
 
@@ -808,6 +806,8 @@ def our_arm(args, wl, world, rank, local):
                 "roofline": roof, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "vs_plain_fp32": plain,
                 "gpu_launches": launches, "clocks": clk}
+        if vs_mti is not None:
+            line["elkan_vs_mti"] = vs_mti
         print(json.dumps(line), flush=True)
 
 
