@@ -347,7 +347,25 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
             for (int cw = 0; cw < k; cw += 32) {
                 const int cl = cw + lane;
                 unsigned uni = __ballot_sync(FULL_MASK, cl < k && cl != a && !(tmax < hrow[min(cl, k - 1)]));
-                // two members per step (independent chains), in index order
+                // four or two members per step (independent chains), in index order
+                while (__popc(uni) >= 4) {
+                    int cc[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        cc[q] = cw + __ffs(uni) - 1;
+                        uni &= uni - 1;
+                    }
+                    if (lane < nb) {
+                        float r[4];
+                        d2_reg4<DV>(xk, cent + (size_t)cc[0] * DV, cent + (size_t)cc[1] * DV,
+                                    cent + (size_t)cc[2] * DV, cent + (size_t)cc[3] * DV, r);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            my_evals += tst < hrow[cc[q]] ? 0u : 1u;
+                            if (r[q] < bd || (r[q] == bd && cc[q] < best)) { bd = r[q]; best = cc[q]; }
+                        }
+                    }
+                }
                 while (uni) {
                     const int c = cw + __ffs(uni) - 1;
                     uni &= uni - 1;
