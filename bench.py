@@ -502,6 +502,8 @@ def config_of(wl, name, world):
             "init": "Forgy, seed 42",
             "data_seed": wl["data_seed"], "points_dtype": "f32",
             "l2": l2_note(wl["n"] * wl["d"] * 4),
+            "points": "pinned host memory, read in place over NVLink-C2C" if wl.get("points_in_host")
+                      else "HBM",
             "parallelism": f"replicas x{world}"}
 
 
@@ -520,7 +522,10 @@ def our_arm(args, wl, world, rank, local):
     torch.cuda.synchronize()
     prec = wl.get("precision", "fp32")
     elkan = bool(wl.get("elkan", False))
-    ctx = knor.Context(X, k, seed=42, prune=wl["prune"], precision=prec, elkan=elkan)
+    on_host = bool(wl.get("points_in_host", False))
+    if on_host:  # the points stay in pinned host memory; the GPU reads them in place
+        X = X.cpu().pin_memory()
+    ctx = knor.Context(X, k, seed=42, prune=wl["prune"], precision=prec, elkan=elkan, points_in_host=on_host)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     def barrier():
@@ -735,7 +740,7 @@ def our_arm(args, wl, world, rank, local):
         ctx.run(T)
         a_mti = torch.empty(n, dtype=torch.int32, device="cuda")
         ctx.assignments(a_mti)
-        with knor.Context(X, k, seed=42, prune=False) as pc:
+        with knor.Context(X, k, seed=42, prune=False, points_in_host=on_host) as pc:
             pc.reset()
             pc.run(T)
             pstream = torch.cuda.ExternalStream(pc.stream)
@@ -770,7 +775,8 @@ def our_arm(args, wl, world, rank, local):
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(es):
-            with knor.Context(Xh, k, seed=42, prune=wl["prune"], precision=prec, elkan=elkan) as c2:
+            with knor.Context(Xh, k, seed=42, prune=wl["prune"], precision=prec, elkan=elkan,
+                              points_in_host=on_host) as c2:
                 done, _ = c2.run(T)
                 c2.assignments(ah)
                 c2.centroids(Ch)

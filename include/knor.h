@@ -17,8 +17,9 @@
  *     stays valid and destroyable, and knor_last_error() describes the error.
  *   - Pointers marked "host or device" may point to host memory (pageable or
  *     pinned) or to device memory of the context's GPU; the library tells
- *     them apart with cudaPointerGetAttributes.  Inputs are copied; the caller
- *     keeps ownership of every buffer it passes.  Outputs go to caller-owned
+ *     them apart with cudaPointerGetAttributes.  Inputs are copied (except the
+ *     points under knor_opts.points_in_host); the caller keeps ownership of
+ *     every buffer it passes.  Outputs go to caller-owned
  *     buffers and are complete when the call returns.
  *   - All arrays are dense and row-major.  Points are FP32; centroids are
  *     returned as FP64 (the master copy) or FP32 (the copy the scan used).
@@ -91,6 +92,18 @@ typedef struct {
                                      16, 32, 64}, k <= 110 and k*d <= 8192;
                                      KNOR_ERR_ARG otherwise.  Assignments equal
                                      MTI's and plain Lloyd's. */
+    int32_t points_in_host;       /* 1: the points stay where the caller has them,
+                                     in host memory (pinned or pageable; a pageable
+                                     buffer is registered with the CUDA driver for
+                                     the context's lifetime): no n x d copy in HBM,
+                                     the scans read rows over the host link (NVLink-
+                                     C2C on Grace), so the rows Clause 1 skips are
+                                     never transferred -- the in-memory analogue of
+                                     the paper's semi-external mode.  The caller
+                                     keeps the buffer alive and unchanged until
+                                     knor_destroy.  Needs FP32 distances, a 16-byte
+                                     aligned host buffer; KNOR_ERR_ARG otherwise
+                                     (or if points is device memory). */
 } knor_opts;
 
 /* Per-iteration counters. */

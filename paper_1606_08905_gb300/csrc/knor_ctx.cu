@@ -141,6 +141,8 @@ struct knor_ctx {
     int32_t *rec = nullptr, *rec_cnt = nullptr, *chg_cnt = nullptr; // split MTI scan: batch records
     int2 *chg = nullptr;                                                // and change lists
     float *lb = nullptr;                                                // Elkan's lower bounds
+    bool X_on_host = false;          // points_in_host: X is the device address of the caller's buffer
+    float *host_registered = nullptr; // ... registered by knor_create (pageable memory)
     IterParams ip_sel{}, ip_delta{};
     size_t smem_sel = 0;
     bool mti_split = false, dense_split = false; // the split kernels run the MTI / dense scans
@@ -217,7 +219,8 @@ static void free_all(knor_ctx *c) {
     c->ev.clear();
     if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
     if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
-    void *bufs[] = {c->X,      c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
+    if (c->host_registered) cudaHostUnregister(c->host_registered);
+    void *bufs[] = {c->X_on_host ? nullptr : c->X, c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
                     c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma, c->rec, c->rec_cnt, c->chg, c->chg_cnt, c->lb,
@@ -740,6 +743,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         return KNOR_ERR_ARG;
     }
     if (o.full_recompute_every < 0) { g_create_err = "knor_create: full_recompute_every < 0"; return KNOR_ERR_ARG; }
+    if (o.points_in_host && (tc_form || is_device_ptr(points) || (reinterpret_cast<uintptr_t>(points) & 15) != 0)) {
+        g_create_err = "knor_create: points_in_host needs FP32 distances and a 16-byte aligned host buffer";
+        return KNOR_ERR_ARG;
+    }
     if (o.elkan && (o.no_prune || tc_form || o.full_recompute_every != 0)) {
         g_create_err = "knor_create: elkan needs pruning, FP32 distances and full_recompute_every = 0";
         return KNOR_ERR_ARG;
@@ -759,9 +766,26 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     KCU(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
     KCU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     const size_t nd = (size_t)n * d, kd = (size_t)k * d;
-    KC(dalloc(c, &c->X, nd));
-    KCU(cudaMemcpyAsync(c->X, points, nd * sizeof(float),
-                        is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (o.points_in_host) {
+        // read in place: pinned memory is mapped already; pageable memory is
+        // registered (mapped) for the context's lifetime
+        cudaPointerAttributes at{};
+        const bool pinned = cudaPointerGetAttributes(&at, points) == cudaSuccess && at.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        if (!pinned) {
+            KCU(cudaHostRegister(const_cast<float *>(points), nd * sizeof(float),
+                                 cudaHostRegisterMapped));
+            c->host_registered = const_cast<float *>(points);
+        }
+        void *dp = nullptr;
+        KCU(cudaHostGetDevicePointer(&dp, const_cast<float *>(points), 0));
+        c->X = static_cast<float *>(dp);
+        c->X_on_host = true;
+    } else {
+        KC(dalloc(c, &c->X, nd));
+        KCU(cudaMemcpyAsync(c->X, points, nd * sizeof(float),
+                            is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    }
     KC(dalloc(c, &c->d_bad, 1));
     KCU(cudaMemsetAsync(c->d_bad, 0, sizeof(unsigned long long), c->stream));
     KCU(launch_validate(c->X, (int64_t)nd, c->d_bad, c->stream));

@@ -31,7 +31,7 @@ class KnorError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("no_prune", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("full_recompute_every", ctypes.c_int32), ("debug_invariants", ctypes.c_int32),
-                ("elkan", ctypes.c_int32)]
+                ("elkan", ctypes.c_int32), ("points_in_host", ctypes.c_int32)]
 
 
 class IterStats(ctypes.Structure):
@@ -162,7 +162,7 @@ class Context:
 
     def __init__(self, points, k: int, init: str = "forgy", seed: int = 0, prune: bool = True,
                  precision: str = "fp32", full_recompute_every: int = 0,
-                 debug_invariants: bool = False, elkan: bool = False):
+                 debug_invariants: bool = False, elkan: bool = False, points_in_host: bool = False):
         lib = load()
         shape = tuple(points.shape)
         if len(shape) != 2:
@@ -171,11 +171,14 @@ class Context:
         self.k = int(k)
         ptr, keep = _ptr(points, np.float32)
         opts = Opts(0 if prune else 1, PRECISIONS[precision], int(full_recompute_every),
-                    1 if debug_invariants else 0, 1 if elkan else 0)
+                    1 if debug_invariants else 0, 1 if elkan else 0, 1 if points_in_host else 0)
         out = ctypes.c_void_p()
         st = lib.knor_create(ptr, self.n, self.d, self.k,
                              KNOR_INIT_FORGY if init == "forgy" else KNOR_INIT_EXPLICIT,
                              int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opts), ctypes.byref(out))
+        # with points_in_host the library reads the caller's buffer for the
+        # context's lifetime: keep it referenced
+        self._points = keep if points_in_host else None
         del keep
         _check(st, None)
         self._ctx = out.value

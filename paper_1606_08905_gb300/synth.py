@@ -189,6 +189,10 @@ WORKLOADS = {
                                       data_seed=1006, max_iters=20, prune=True),
     # Elkan's lower bounds (the ablation of MTI) on the 100k x 8, k = 10
     # workload's points and on a 16M-point slice of the 66M x 32, k = 20 one
+    # the 66M x 32, k = 20 workload with the points left in pinned host
+    # memory (read in place over the host link; Clause 1 saves the transfers)
+    "host_66m_d32_k20": dict(kind="spd", n=66_000_000, d=32, k=20, data_seed=1002,
+                             max_iters=50, prune=True, points_in_host=True),
     "elkan_100k_d8_k10": dict(kind="isotropic", n=100_000, d=8, k=10, data_seed=1001,
                               max_iters=20, prune=True, elkan=True),
     "elkan_16m_d32_k20": dict(kind="spd", n=16_000_000, d=32, k=20, data_seed=1002,
