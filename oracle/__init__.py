@@ -60,6 +60,8 @@ def _load():
         lib.oracle_splitmix64_next.argtypes = [c.POINTER(c.c_uint64)]
         lib.oracle_splitmix64_next.restype = c.c_uint64
         lib.oracle_forgy_indices.argtypes = [c.c_int64, c.c_int32, c.c_uint64, _i64p]
+        lib.oracle_kmeanspp_indices.argtypes = [_f32p, c.c_int64, c.c_int32, c.c_int32, c.c_uint64, _i64p]
+        lib.oracle_kmeanspp_indices.restype = c.c_int
         lib.oracle_forgy_indices.restype = c.c_int
         lib.oracle_assign.argtypes = [_f32p, c.c_int64, c.c_int32, c.c_int32, _f64p,
                                       _i32p, _f64p, _f64p, _f64p, c.c_int]
@@ -120,6 +122,17 @@ def forgy_centroids(X, k: int, seed: int) -> np.ndarray:
     X = _X(X)
     idx = forgy_indices(X.shape[0], k, seed)
     return X[idx].astype(np.float64)
+
+
+def kmeanspp_indices(X, k: int, seed: int) -> np.ndarray:
+    """k-means++ seeding (D^2 sampling, reproducible readings in
+    knor_oracle.c): the k row indices in the order drawn."""
+    X = _X(X)
+    n, d = X.shape
+    out = np.zeros(k, np.int64)
+    if _load().oracle_kmeanspp_indices(X, n, d, k, seed & 0xFFFFFFFFFFFFFFFF, out) != 0:
+        raise ValueError("kmeanspp_indices: need 1 <= k <= n")
+    return out
 
 
 def assign(X, C, nthreads: int = 0):

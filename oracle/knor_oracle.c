@@ -117,6 +117,87 @@ int oracle_forgy_indices(int64_t n, int32_t k, uint64_t seed, int64_t *idx_out) 
     return 0;
 }
 
+/* The library's FP32 squared distance, restated (see oracle_assign_f32 for
+ * the order): two chains over even and odd coordinates, fmaf, then e + o. */
+static float oracle_dist2_f32(const float *x, const float *c, int32_t d) {
+    float e = 0.0f, o = 0.0f;
+    int32_t q;
+    for (q = 0; q < d; ++q) {
+        float t = x[q] - c[q];
+        if (q % 2 == 0) e = fmaf(t, t, e);
+        else o = fmaf(t, t, o);
+    }
+    return e + o;
+}
+
+/* k-means++ seeding (Arthur and Vassilvitskii, SODA 2007; the paper lists it
+ * among the variants to come): the first centroid is a uniformly drawn point,
+ * every further one a point drawn with probability proportional to its
+ * squared distance D^2 to the nearest centroid chosen so far.  Readings that
+ * make a draw reproducible bit for bit:
+ *   - D^2 is the FP32 squared distance above (the one every scan uses),
+ *     between the FP32 rows of the point and of the chosen points;
+ *   - the weights are D^2 quantised onto a power-of-two grid fixed per round:
+ *     w(x) = floor(D^2(x) 2^E) with E = 32 - e, e the smallest integer with
+ *     max D^2 < 2^e, so every weight is an exact integer below 2^32 and the
+ *     total an exact 64-bit integer;
+ *   - each draw is the next SplitMix64(seed) output r reduced by the
+ *     multiply-shift: the first index floor(r n / 2^64), then t = floor(r T /
+ *     2^64) with T the total weight, and the chosen point is the first whose
+ *     running weight sum exceeds t (a point of weight 0 is never chosen);
+ *   - if every weight is 0 (all points sit on chosen centroids) the next index
+ *     is drawn uniformly like the first.
+ * idx_out receives the k indices in the order drawn.  Returns 0, or -1 for
+ * bad arguments. */
+int oracle_kmeanspp_indices(const float *X, int64_t n, int32_t d, int32_t k, uint64_t seed,
+                            int64_t *idx_out) {
+    uint64_t state = seed;
+    float *D2;
+    uint64_t *w;
+    int32_t j;
+    int64_t i;
+    if (n <= 0 || k <= 0 || d <= 0 || (int64_t)k > n) return -1;
+    D2 = (float *)malloc((size_t)n * sizeof(float));
+    w = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    idx_out[0] = (int64_t)oracle_below(&state, (uint64_t)n);
+    for (i = 0; i < n; ++i) D2[i] = INFINITY;
+    for (j = 1; j < k; ++j) {
+        const float *c = X + (size_t)idx_out[j - 1] * d;
+        float m = 0.0f;
+        uint64_t T = 0, t, run = 0;
+        int e = 0;
+        for (i = 0; i < n; ++i) {
+            float v = oracle_dist2_f32(X + (size_t)i * d, c, d);
+            if (v < D2[i]) D2[i] = v;
+            if (D2[i] > m) m = D2[i];
+        }
+        if (m > 0.0f) {
+            (void)frexpf(m, &e); /* m = f 2^e, f in [0.5, 1): m < 2^e */
+            for (i = 0; i < n; ++i) {
+#ifdef ORACLE_PLANT_KPP_LINEAR /* weights in proportion to D instead of D^2 */
+                w[i] = (uint64_t)floor(ldexp(sqrt((double)D2[i]) / sqrt((double)m), 32));
+#else
+                w[i] = (uint64_t)floor(ldexp((double)D2[i], 32 - e));
+#endif
+                T += w[i];
+            }
+        }
+        if (T == 0) {
+            idx_out[j] = (int64_t)oracle_below(&state, (uint64_t)n);
+            continue;
+        }
+        t = oracle_below(&state, T);
+        for (i = 0; i < n; ++i) {
+            run += w[i];
+            if (run > t) break;
+        }
+        idx_out[j] = i;
+    }
+    free(D2);
+    free(w);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Distances ("Nomenclature").                                          */
 /* ------------------------------------------------------------------ */

@@ -424,3 +424,60 @@ def test_elkan_bounds_hold_every_iteration():
         r = oracle.run(X, oracle.forgy_centroids(X, k, 42), 40, prune="elkan", check_bounds=True)
         assert r.iters > 3
         assert np.all(r.violations == 0), r.violations
+
+
+# ------------------------------------------------------------ k-means++ ----
+
+def test_kmeanspp_hand_worked_indices():
+    """Pin: k-means++ indices on the points 0, 1, 3 worked by hand from the
+    published SplitMix64 outputs (tests/golden/kmeanspp_hand.txt)."""
+    X = np.array([[0.0], [1.0], [3.0]], np.float32)
+    with open(os.path.join(GOLDEN, "kmeanspp_hand.txt")) as fh:
+        rows = [ln.split() for ln in fh if ln.startswith("case ")]
+    assert len(rows) == 2
+    for row in rows:
+        seed = int(row[1])
+        bars = [i for i, v in enumerate(row) if v == "|"]
+        k2 = [int(v) for v in row[bars[0] + 1:bars[1]]]
+        k3 = [int(v) for v in row[bars[1] + 1:]]
+        assert list(oracle.kmeanspp_indices(X, 2, seed)) == k2
+        assert list(oracle.kmeanspp_indices(X, 3, seed)) == k3
+
+
+def test_kmeanspp_draws_in_proportion_to_squared_distance():
+    """Pin (the definition): on the points 0, 1, 3 the first index is uniform
+    and the second, given the first, is drawn with probability D^2 / sum D^2
+    (the weights here are exact on the quantisation grid: squares of small
+    integers).  Chi-square over 30000 seeds, 3 + 3 x 1 degrees of freedom."""
+    X = np.array([[0.0], [1.0], [3.0]], np.float32)
+    xs = np.array([0.0, 1.0, 3.0])
+    trials = 30000
+    first = np.zeros(3)
+    pair = np.zeros((3, 3))
+    for s in range(trials):
+        i, j = oracle.kmeanspp_indices(X, 2, s + 1000)
+        first[i] += 1
+        pair[i, j] += 1
+    chi2 = (((first - trials / 3) ** 2) / (trials / 3)).sum()
+    for i in range(3):
+        d2 = (xs - xs[i]) ** 2
+        p = d2 / d2.sum()
+        m = p > 0
+        assert pair[i, ~m].sum() == 0  # the chosen point itself has weight 0
+        exp = first[i] * p[m]
+        chi2 += (((pair[i, m] - exp) ** 2) / exp).sum()
+    assert chi2 < 24.3  # 5 dof, p = 0.0002
+
+
+def test_kmeanspp_covers_every_distinct_location():
+    """Pin: with exactly k distinct locations (each repeated many times) the
+    seeding picks one point at each, because points on chosen centroids weigh
+    nothing; with k = n distinct points it picks every point once."""
+    rng = np.random.default_rng(3)
+    locs = rng.normal(size=(7, 5)).astype(np.float32) * 10
+    X = locs[rng.integers(0, 7, 3000)]
+    for seed in range(5):
+        idx = oracle.kmeanspp_indices(X, 7, seed)
+        assert len({tuple(X[i]) for i in idx}) == 7
+    Y = rng.normal(size=(40, 3)).astype(np.float32)
+    assert sorted(oracle.kmeanspp_indices(Y, 40, 11).tolist()) == list(range(40))

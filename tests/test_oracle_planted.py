@@ -23,6 +23,7 @@ CASES = [
     ("ORACLE_PLANT_EMPTY_ZERO", "test_empty_cluster_keeps_centroid"),
     ("ORACLE_PLANT_NO_DRIFT", "test_pruned_equals_unpruned_every_iteration or test_mti_invariants"),
     ("ORACLE_PLANT_ELKAN_NO_LB_DRIFT", "test_elkan"),
+    ("ORACLE_PLANT_KPP_LINEAR", "test_kmeanspp"),
 ]
 
 
