@@ -51,8 +51,9 @@ typedef enum {
 } knor_status;
 
 typedef enum {
-    KNOR_INIT_FORGY = 0,   /* k distinct rows chosen from the seed (below) */
-    KNOR_INIT_EXPLICIT = 1 /* caller supplies C^0 with knor_set_init_centroids */
+    KNOR_INIT_FORGY = 0,    /* k distinct rows chosen from the seed (below) */
+    KNOR_INIT_EXPLICIT = 1, /* caller supplies C^0 with knor_set_init_centroids */
+    KNOR_INIT_KMEANSPP = 2  /* k-means++ seeding from the seed (below) */
 } knor_init;
 
 typedef enum {
@@ -129,6 +130,16 @@ typedef struct {
  *     (for j = n-k .. n-1: t = floor(r * (j+1) / 2^64) with r the next
  *     SplitMix64 output of state `seed`; keep t unless already kept, else j).
  *     The paper states no initialisation; this one is reproducible.
+ *   init = KNOR_INIT_KMEANSPP: k-means++ (Arthur and Vassilvitskii 2007; the
+ *     paper names it among the variants to come), reproducible bit for bit:
+ *     with r_1, r_2, ... the SplitMix64 outputs of state `seed` and
+ *     below(r, m) = floor(r * m / 2^64), the first index is below(r_1, n);
+ *     then D^2(x) = min over the chosen points p of the FP32 squared distance
+ *     of the scans (even/odd fma chains) between the rows x and p; with e the
+ *     smallest integer such that max D^2 < 2^e, the weights are
+ *     w(x) = floor(D^2(x) * 2^(32 - e)) and T their sum; the next index is the
+ *     first point whose running weight sum exceeds below(r_j, T), or
+ *     below(r_j, n) when T = 0.  C^0 = the rows in drawn order.
  *   init = KNOR_INIT_EXPLICIT: C^0 must be set with knor_set_init_centroids
  *     before the first iteration (KNOR_ERR_STATE otherwise).
  * Errors: KNOR_ERR_ARG if points or out is NULL, n < 1, d < 1, k < 1, k > n,
@@ -168,8 +179,8 @@ knor_status knor_get_assignments(const knor_ctx *ctx, int32_t *out_n);
 knor_status knor_get_centroids(const knor_ctx *ctx, double *out_kxd);
 knor_status knor_get_centroids_f32(const knor_ctx *ctx, float *out_kxd);
 
-/* The Forgy row indices (k int64, host buffer).  KNOR_ERR_STATE for
- * KNOR_INIT_EXPLICIT contexts. */
+/* The Forgy or k-means++ row indices (k int64, host buffer), in drawn order.
+ * KNOR_ERR_STATE for KNOR_INIT_EXPLICIT contexts. */
 knor_status knor_get_init_indices(const knor_ctx *ctx, int64_t *out_k);
 
 /* Iterations completed since the last reset. */

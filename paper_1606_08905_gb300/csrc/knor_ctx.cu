@@ -65,6 +65,75 @@ std::vector<int64_t> forgy_indices(int64_t n, int32_t k, uint64_t seed) {
     return out;
 }
 
+// k-means++ row indices (the rule of knor.h's KNOR_INIT_KMEANSPP): D^2 and
+// the weights on the GPU, the draws and exact integer sums on the host.
+static cudaError_t kmeanspp_indices(const float *X, int64_t n, int32_t d, int32_t k, uint64_t seed, int dv,
+                                    int num_sms, cudaStream_t s, std::vector<int64_t> &out) {
+    out.clear();
+    uint64_t state = seed;
+    auto below = [&](uint64_t m) {
+        const uint64_t r = splitmix64(state);
+        return (uint64_t)(((unsigned __int128)r * (unsigned __int128)m) >> 64);
+    };
+    out.push_back((int64_t)below((uint64_t)n));
+    if (k == 1) return cudaSuccess;
+    const int grid = 8 * num_sms;
+    float *D2 = nullptr;
+    unsigned *maxbits = nullptr;
+    unsigned long long *sums = nullptr;
+    int64_t *found = nullptr;
+    cudaError_t e = cudaMalloc((void **)&D2, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&maxbits, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sums, sizeof(unsigned long long) * grid);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&found, sizeof(int64_t));
+    std::vector<unsigned long long> hs((size_t)grid);
+    for (int32_t j = 1; j < k && e == cudaSuccess; ++j) {
+        unsigned mb = 0;
+        e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess)
+            e = kpp_update(dv, X, n, d, X + (size_t)out.back() * d, D2, j == 1 ? 1 : 0, maxbits, grid, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&mb, maxbits, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        float m;
+        std::memcpy(&m, &mb, sizeof(m));
+        unsigned long long T = 0;
+        double scale = 0.0;
+        if (m > 0.0f) {
+            int ex = 0;
+            std::frexp(m, &ex); // m = f 2^ex, f in [0.5, 1): m < 2^ex
+            scale = std::ldexp(1.0, 32 - ex);
+            e = kpp_sums(D2, n, scale, sums, grid, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hs.data(), sums, sizeof(unsigned long long) * grid, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            for (unsigned long long v : hs) T += v;
+        }
+        if (T == 0) {
+            out.push_back((int64_t)below((uint64_t)n));
+            continue;
+        }
+        unsigned long long t = below(T), before = 0;
+        int b = 0;
+        while (b < grid - 1 && before + hs[(size_t)b] <= t) before += hs[(size_t)b++];
+        // CTA b's range, as block_range on the device splits [0, n)
+        const int64_t lo = (int64_t)((unsigned __int128)n * b / grid);
+        const int64_t hi = (int64_t)((unsigned __int128)n * (b + 1) / grid);
+        int64_t idx = -1;
+        e = kpp_find(D2, lo, hi, scale, t - before, found, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&idx, found, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && (idx < lo || idx >= hi)) e = cudaErrorUnknown; // cannot happen: the sums say so
+        out.push_back(idx);
+    }
+    cudaFree(D2);
+    cudaFree(maxbits);
+    cudaFree(sums);
+    cudaFree(found);
+    return e;
+}
+
 float f32_up(double v) { // smallest float >= v
     float f = (float)v;
     if ((double)f < v) f = std::nextafter(f, INFINITY);
@@ -729,7 +798,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     if ((double)n * (double)d > std::ldexp(1.0, 40)) { g_create_err = "knor_create: n*d above 2^40"; return KNOR_ERR_ARG; }
     if (n > (int64_t)1 << 31) { g_create_err = "knor_create: n above 2^31"; return KNOR_ERR_ARG; }
     if ((double)k * (double)d > (double)(1 << 28)) { g_create_err = "knor_create: k*d above 2^28"; return KNOR_ERR_ARG; }
-    if (init != KNOR_INIT_FORGY && init != KNOR_INIT_EXPLICIT) { g_create_err = "knor_create: bad init"; return KNOR_ERR_ARG; }
+    if (init != KNOR_INIT_FORGY && init != KNOR_INIT_EXPLICIT && init != KNOR_INIT_KMEANSPP) {
+        g_create_err = "knor_create: bad init";
+        return KNOR_ERR_ARG;
+    }
     knor_opts o{};
     if (opts) o = *opts;
     if (o.precision != KNOR_PREC_FP32 && o.precision != KNOR_PREC_BF16 && o.precision != KNOR_PREC_FP16 &&
@@ -1040,8 +1112,9 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         c->kname[KNOR_KERNEL_SUMS] = "k_delta_sums";
     }
     // C^0
-    if (init == KNOR_INIT_FORGY) {
-        c->init_idx = forgy_indices(n, k, seed);
+    if (init == KNOR_INIT_FORGY || init == KNOR_INIT_KMEANSPP) {
+        if (init == KNOR_INIT_FORGY) c->init_idx = forgy_indices(n, k, seed);
+        else KCU(kmeanspp_indices(c->X, n, d, k, seed, c->dv, c->num_sms, c->stream, c->init_idx));
         KC(dalloc(c, &c->d_idx, (size_t)k));
         KCU(cudaMemcpyAsync(c->d_idx, c->init_idx.data(), sizeof(int64_t) * k, cudaMemcpyHostToDevice, c->stream));
         KCU(launch_gather_rows(c->X, d, c->d_idx, k, c->C0, c->stream));
@@ -1233,7 +1306,7 @@ knor_status knor_get_init_indices(const knor_ctx *c, int64_t *out_k) {
     if (!c) return KNOR_ERR_ARG;
     c->err.clear();
     if (!out_k) return fail(c, KNOR_ERR_ARG, "knor_get_init_indices: NULL output");
-    if (c->init != KNOR_INIT_FORGY) return fail(c, KNOR_ERR_STATE, "knor_get_init_indices: context uses explicit init");
+    if (c->init == KNOR_INIT_EXPLICIT) return fail(c, KNOR_ERR_STATE, "knor_get_init_indices: context uses explicit init");
     std::memcpy(out_k, c->init_idx.data(), sizeof(int64_t) * c->k);
     return KNOR_OK;
 }

@@ -254,6 +254,14 @@ cudaError_t launch_check_bounds(const float *X, int64_t n, int32_t d, const PtSt
                                 const int32_t *run_iter, cudaStream_t s);
 int supported_dv(int d); // template width used for d (0 = generic)
 void set_global_error(const char *msg); // message for knor_last_error(NULL)
+// k-means++ seeding (kmeanspp.cu): one round's D^2 update (with the round's
+// largest D^2 as float bits), the weight sums over the fixed CTA ranges, and
+// the search of one range for the drawn point
+cudaError_t kpp_update(int dv, const float *X, int64_t n, int32_t d, const float *c, float *D2, int first,
+                       unsigned *maxbits, int grid, cudaStream_t s);
+cudaError_t kpp_sums(const float *D2, int64_t n, double scale, unsigned long long *sums, int grid, cudaStream_t s);
+cudaError_t kpp_find(const float *D2, int64_t lo, int64_t hi, double scale, unsigned long long t, int64_t *out,
+                     cudaStream_t s);
 // Forgy initialisation: k distinct indices of [0, n) (Floyd's sampling on
 // SplitMix64(seed)), in the order drawn (knor_ctx.cu).
 std::vector<int64_t> forgy_indices(int64_t n, int32_t k, uint64_t seed);

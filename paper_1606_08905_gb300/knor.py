@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_PKG, "libknor.so")
 _lib = None
 
 KNOR_OK, KNOR_ERR_ARG, KNOR_ERR_OOM, KNOR_ERR_CUDA, KNOR_ERR_TIMEOUT, KNOR_ERR_STATE = 0, -1, -2, -3, -4, -5
-KNOR_INIT_FORGY, KNOR_INIT_EXPLICIT = 0, 1
+KNOR_INIT_FORGY, KNOR_INIT_EXPLICIT, KNOR_INIT_KMEANSPP = 0, 1, 2
+INITS = {"forgy": KNOR_INIT_FORGY, "explicit": KNOR_INIT_EXPLICIT, "kmeans++": KNOR_INIT_KMEANSPP}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
 
 
@@ -174,7 +175,7 @@ class Context:
                     1 if debug_invariants else 0, 1 if elkan else 0, 1 if points_in_host else 0)
         out = ctypes.c_void_p()
         st = lib.knor_create(ptr, self.n, self.d, self.k,
-                             KNOR_INIT_FORGY if init == "forgy" else KNOR_INIT_EXPLICIT,
+                             INITS[init],
                              int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(opts), ctypes.byref(out))
         # with points_in_host the library reads the caller's buffer for the
         # context's lifetime: keep it referenced

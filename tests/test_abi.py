@@ -67,3 +67,11 @@ def test_batch_create_rejects_bad_instances_without_touching_the_gpu(lib):
     assert lib.knor_batch_create(0, ptrs, None, None, None, 1, None, ctypes.byref(out)) == knor.KNOR_ERR_ARG
     assert lib.knor_batch_iterate(None, None) == knor.KNOR_ERR_ARG
     lib.knor_batch_destroy(None)  # no-op
+
+
+def test_create_rejects_an_unknown_init_without_touching_the_gpu(lib):
+    X = np.zeros((10, 4), np.float32)
+    out = ctypes.c_void_p()
+    for bad in (3, -1):
+        st = lib.knor_create(X.ctypes.data, 10, 4, 2, bad, 1, None, ctypes.byref(out))
+        assert st == knor.KNOR_ERR_ARG and "init" in lib.knor_last_error(None).decode()
