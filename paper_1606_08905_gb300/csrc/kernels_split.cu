@@ -669,9 +669,8 @@ __global__ void k_elkan_check(const IterParams p, IterStats *stats, const int32_
 // list w / dl_split, part w % dl_split).  A warp takes its entries 32 at a
 // time, loads their rows straight into registers (32 row loads in flight per
 // lane, lanes walking the dimensions), then adds each row to its new cluster
-// and subtracts it from its old one in its accumulators (shared memory: TwoSum
-// FP32 pairs, or FP64 for rows of 16 floats or fewer), in list order; the CTA
-// adds its warps' accumulators in warp order
+// and subtracts it from its old one in its TwoSum accumulators (shared
+// memory), in list order; the CTA adds its warps' accumulators in warp order
 // into its partial slot.  Order and grouping depend only on the lists and
 // the fixed split: deterministic.
 template <int DV>
@@ -684,13 +683,8 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     const int k = p.k;
     constexpr int R = DV < 32 ? 1 : DV / 32; // dimensions per lane
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
-    // accumulators: TwoSum FP32 pairs (hi, lo) for DV >= 32; for narrower rows
-    // (half a warp or less per row, longer add chains per lane) FP64, which
-    // costs one add per element on the FP64 pipe; the same bytes either way
-    constexpr bool F64 = DV <= 16;
     float *acc_hi = reinterpret_cast<float *>(sm + w * p.dl_warp_stride);
     float *acc_lo = acc_hi + (size_t)k * DV;
-    double *acc64 = reinterpret_cast<double *>(acc_hi);
     int *cnt = reinterpret_cast<int *>(acc_lo + (size_t)k * DV);
     for (int e = lane; e < 2 * k * DV; e += 32) acc_hi[e] = 0.0f;
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
@@ -728,13 +722,8 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
             for (int r = 0; r < R; ++r) {
                 const int j = lane + 32 * r;
                 if (j < DV) {
-                    if constexpr (F64) {
-                        acc64[cn * DV + j] += (double)x[q][r];
-                        if (co != 0xFFFF) acc64[co * DV + j] -= (double)x[q][r];
-                    } else {
-                        two_sum_acc(&acc_hi[cn * DV + j], &acc_lo[cn * DV + j], x[q][r]);
-                        if (co != 0xFFFF) two_sum_acc(&acc_hi[co * DV + j], &acc_lo[co * DV + j], -x[q][r]);
-                    }
+                    two_sum_acc(&acc_hi[cn * DV + j], &acc_lo[cn * DV + j], x[q][r]);
+                    if (co != 0xFFFF) two_sum_acc(&acc_hi[co * DV + j], &acc_lo[co * DV + j], -x[q][r]);
                 }
             }
         }
@@ -744,13 +733,9 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     for (int e = tid; e < kd; e += nthr) {
         double sum = 0.0;
         for (int q = 0; q < nw; ++q) {
-            if constexpr (F64) {
-                sum += reinterpret_cast<const double *>(sm + q * p.dl_warp_stride)[e];
-            } else {
-                const float *a = reinterpret_cast<const float *>(sm + q * p.dl_warp_stride);
-                sum += (double)a[e];
-                sum += (double)a[kd + e];
-            }
+            const float *a = reinterpret_cast<const float *>(sm + q * p.dl_warp_stride);
+            sum += (double)a[e];
+            sum += (double)a[kd + e];
         }
         p.part_S[(size_t)e * p.part_stride + blockIdx.x] = sum;
     }
