@@ -561,7 +561,7 @@ def our_arm(args, wl, world, rank, local):
     # else dense | MTI scan + merge + table
     if wl.get("precision", "fp32") != "fp32":
         per_it = 9
-    elif "k_mti_delta" in ctx.kernel_name("dense") or "k_mti_delta" in ctx.kernel_name("mti"):
+    elif ctx.kernel_name("delta"):  # the split path: a delta-sum launch every iteration
         per_it = (5 if elkan else 6) if wl["prune"] else 4
     else:
         per_it = 4 if wl["prune"] else 3

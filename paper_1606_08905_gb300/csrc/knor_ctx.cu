@@ -915,13 +915,30 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
             }
         }
         IterParams pw{}, pm{};
+        int split_mult = bsplit;
         if (c->dense_split) {
-            // the dense scan's warps stage DS_ROWS-row tiles, double-buffered
+            // the dense scan's own layout: centroids and drift (no k x k
+            // table), then per warp DS_ROWS-row tiles, double-buffered
             c->ip_dense = ps;
+            size_t off = 0;
+            auto take = [&](size_t bytes) -> int32_t {
+                const size_t o = off;
+                off = (off + bytes + 15) & ~(size_t)15;
+                return (int32_t)o;
+            };
+            c->ip_dense.off_cent = take((size_t)k * d * 4);
+            c->ip_dense.off_F = take((size_t)k * 4);
+            c->ip_dense.off_halfD = c->ip_dense.off_s = -1;
+            c->ip_dense.sp_off_warp = take(0);
             c->ip_dense.sp_warp_stride = 2 * DS_ROWS * ps.sp_rs * 4;
-            c->smem_dense = (size_t)ps.sp_off_warp + (size_t)SP_WPB * c->ip_dense.sp_warp_stride;
+            c->smem_dense = off + (size_t)SP_WPB * c->ip_dense.sp_warp_stride;
             KCU(dense_scan_attr(c->dv, c->smem_dense, &bd));
             if (bd < 1) c->dense_split = false;
+            // where the dense scan fits twice as many CTAs per SM as the MTI
+            // scan, the split grid takes a whole multiple of the MTI scan's
+            // CTAs per SM: the dense scan gets the warps, the MTI kernels run
+            // in whole waves
+            else if (bsplit > 0 && bd >= 2 * bsplit) split_mult = bsplit * (bd / bsplit);
         }
         if (!c->dense_split) {
             const size_t sw = plan_layout_warp(c, false, pw);
@@ -932,12 +949,13 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         if (c->mti_split) { c->ip_mti = ps; c->smem_mti = ssc; bm = bsplit; }
         else if (sm) { c->ip_mti = pm; c->smem_mti = sm; KCU(mti_w_attr(c->dv, sm, &bm)); }
         else { c->smem_mti = plan_layout(c, true, c->ip_mti); KCU(mti_attr(c->dv, c->smem_mti, &bm)); }
-        c->grid_split = bsplit * c->num_sms;
+        c->grid_split = split_mult * c->num_sms;
     }
     if (bd < 1 || bm < 1) { c->err = "knor_create: kernel does not fit on an SM"; return bail(KNOR_ERR_CUDA); }
-    // (the dense split scan runs on the split grid, in waves if fewer of its
-    // CTAs fit on an SM)
+    // (the split kernels all run on the split grid, in waves where fewer of
+    // their CTAs fit on an SM)
     c->grid_dense = c->dense_split ? c->grid_split : bd * c->num_sms;
+    if (c->mti_split) c->grid_mti = c->grid_split;
     c->grid_mti = bm * c->num_sms;
     // Both scans use the same accumulation mode: per-CTA partial slots, or,
     // when k x d sums do not fit in shared memory, one slot updated by FP64
