@@ -498,6 +498,27 @@ __global__ void k_reduce(const FinParams f, const int32_t *nslots, const int32_t
 // for every c; s(a) their minimum over c != a.  Then the new copy replaces
 // the old one.  CTA 0 records the iteration's counters and decides whether
 // the device-side loop continues.
+// k_mti_sel's heavy threshold of cluster a from row a of the k x k table:
+// theta[a] = the th_M-th smallest 1/2 d(c_a, c) over c != a (equal values
+// ranked by index), +inf when th_M > k - 1.  One CTA per row.
+__device__ void theta_row(const FinParams &f, int a) {
+    const int k = f.k;
+    const float *row = f.halfD + (size_t)a * k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (c == a) continue;
+        const float h = row[c];
+        int rank = 0;
+        for (int q = 0; q < k; ++q) {
+            const float g = row[q];
+            rank += (q != a && (g < h || (g == h && q < c))) ? 1 : 0;
+        }
+        if (rank == f.th_M - 1) f.theta[a] = h;
+    }
+    if (threadIdx.x == 0 && f.th_M > k - 1) f.theta[a] = CUDART_INF_F;
+}
+
+__global__ void k_theta(const FinParams f) { theta_row(f, blockIdx.x); }
+
 __global__ void k_table(const FinParams f, int32_t *mode_dense, int32_t need_table,
                         int32_t recompute_every, int32_t always_dense) {
     const int a = blockIdx.x, k = f.k, d = f.d, tid = threadIdx.x;
@@ -539,6 +560,10 @@ __global__ void k_table(const FinParams f, int32_t *mode_dense, int32_t need_tab
             float m = CUDART_INF_F;
             for (int i = 0; i < (int)blockDim.x; ++i) m = fminf(m, redf[i]);
             f.s[a] = m;
+        }
+        if (f.theta != nullptr) {
+            __syncthreads(); // row a of the table is written and visible to the CTA
+            theta_row(f, a);
         }
     }
     __syncthreads();
@@ -694,6 +719,12 @@ cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32
     const int64_t threads = (int64_t)f.k * f.d * 32;
     const int blocks = (int)((threads + 255) / 256);
     k_reduce<<<blocks, 256, 0, s>>>(f, nslots, fresh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta(const FinParams &f, cudaStream_t s) {
+    if (f.theta == nullptr) return cudaSuccess;
+    k_theta<<<f.k, 128, 0, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -3,9 +3,16 @@
 // k_mti_sel   Clause 1 ("Minimal Triangle Inequality (MTI) Pruning") on the
 //             packed state of every point.  Each warp owns a contiguous range
 //             of points, streams its state, and puts the points that Clause 1
-//             cannot skip into per-cluster buckets in shared memory (32 local
-//             indices each); a bucket that fills is written out at once as
-//             one batch record (cluster, count, 32 point indices) to the
+//             cannot skip into buckets in shared memory (32 local indices
+//             each): one per cluster for its light points, and one shared
+//             "mixed" bucket for the heavy points and the unassigned ones.
+//             A point is heavy when its bound reaches the M-th smallest
+//             1/2 d(c_a, c) of its cluster, so that Clause 2 would leave it
+//             M or more candidates: one such point in a batch makes the
+//             union the scan walks for all 32 lanes large, so heavy points
+//             are batched apart and scored against every centroid.  A bucket
+//             that fills is written out at once as one batch record
+//             (cluster or k for mixed, count, 32 point indices) to the
 //             warp's own list, and the partial buckets follow at the end.
 //             Nothing but the 8-byte state of a point is read here.
 // k_mti_scan  Clauses 3 and 2 on the records: warp w scans list w in order.
@@ -14,7 +21,8 @@
 //             (cp.async), so the row gathers overlap the arithmetic.  The
 //             points of a batch share their cluster a, hence the row of the
 //             k x k table, and their Clause-2 candidate sets are nested, so
-//             the warp walks one union.  New state; the points that changed
+//             the warp walks one union; the points of a mixed batch score
+//             every centroid.  New state; the points that changed
 //             cluster go to the warp's change list (point, new and old
 //             cluster).
 // k_dense_scan  the full scan (plain Lloyd, the first MTI iteration) over the
@@ -61,9 +69,17 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
     const int k = p.k;
     float *s_s = reinterpret_cast<float *>(sm + p.off_s);
     float *F_s = reinterpret_cast<float *>(sm + p.off_F);
-    for (int c = tid; c < k; c += SPT) { s_s[c] = p.s[c]; F_s[c] = p.F[c]; }
+    float *th_s = reinterpret_cast<float *>(sm + p.off_th); // heavy thresholds (when split)
+    const bool split_heavy = p.theta != nullptr;
+    for (int c = tid; c < k; c += SPT) {
+        s_s[c] = p.s[c];
+        F_s[c] = p.F[c];
+        if (split_heavy) th_s[c] = p.theta[c];
+    }
     unsigned char *wr = sm + p.w_base + w * p.w_stride;
-    int *bk = reinterpret_cast<int *>(wr + p.w_bucket); // (k + 1) buckets of 32 local indices
+    // buckets of 32 local indices: cluster a for its light points, k for
+    // the heavy and the unassigned ones
+    int *bk = reinterpret_cast<int *>(wr + p.w_bucket);
     int *bcnt = bk + (k + 1) * 32;
     PtState *stbuf = reinterpret_cast<PtState *>(wr + p.w_state);
     for (int c = lane; c <= k; c += 32) bcnt[c] = 0;
@@ -129,15 +145,19 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
         }
         unsigned amask = 0;
         int nvalid = 0;
+        int bkey[WPA]; // bucket of each point
 #pragma unroll
         for (int u = 0; u < WPA; ++u) {
             const int a = ps[u].a;
+            bkey[u] = k;
             if (a == -2) continue;
             ++nvalid;
             bool act = true;
             if (a >= 0) {
                 const float uu = __fadd_ru(ps[u].ub, F_s[a]); // u^t = ub + F^t(a)
-                act = !(__fmaf_ru(uu, p.onepk, p.tau) < s_s[a]);
+                const float t = __fmaf_ru(uu, p.onepk, p.tau);
+                act = !(t < s_s[a]);
+                if (!split_heavy || t < th_s[a]) bkey[u] = a;
             }
             amask |= (act ? 1u : 0u) << u;
         }
@@ -157,7 +177,7 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
 #pragma unroll
         for (int u = 0; u < WPA; ++u) {
             if ((amask >> u) & 1u) {
-                stg[pos] = make_int2((int)(i0 + u - lo), ps[u].a);
+                stg[pos] = make_int2((int)(i0 + u - lo), bkey[u]);
                 ++pos;
             }
         }
@@ -167,7 +187,7 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
             const int e = base + lane;
             const bool valid = e < total;
             const int2 ent = valid ? stg[e] : make_int2(0, 0);
-            const int key = valid ? (ent.y < 0 ? k : ent.y) : -1 - lane;
+            const int key = valid ? ent.y : -1 - lane;
             const unsigned grp = __match_any_sync(FULL_MASK, key);
             const int rank = __popc(grp & ((1u << lane) - 1u));
             // the entries that fit go in; a bucket that fills is emitted at
@@ -290,17 +310,24 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
     unsigned my_evals = 0, my_changed = 0;
     // Two batches in flight: the rows of batch j + 2 go into the slot of
     // batch j as soon as batch j's rows are in registers.
+    // The cluster of a lane's point in a mixed record (k: heavy points of any
+    // cluster and unassigned ones, -1), read from the state when the rows of
+    // the record are requested, two batches ahead.
+    auto own_cluster = [&](int cb, int nb, int idx) { return cb == k && lane < nb ? p.st[idx].a : -1; };
     int cb0, nb0, ix0, cb1, nb1, ix1, cb2, nb2, ix2;
     meta(0, cb0, nb0, ix0);
     fetch(0, nb0, ix0);
+    int al0 = own_cluster(cb0, nb0, ix0);
     meta(1, cb1, nb1, ix1);
     fetch(1, nb1, ix1);
+    int al1 = own_cluster(cb1, nb1, ix1);
     meta(2, cb2, nb2, ix2);
     for (int j = 0; j < nrec; ++j) {
         cp_async_wait<1>();
         __syncwarp();
         const float *rb = slots + (size_t)(j & 1) * 32 * rs;
-        const int a = cb0 == k ? -1 : cb0;
+        const bool mixed = cb0 == k;
+        const int a = mixed ? al0 : cb0; // this lane's cluster (-1: none yet)
         const int nb = nb0;
         int best = -1;
         unsigned long long xk[DV / 2];
@@ -315,16 +342,39 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
         }
         __syncwarp(); // every lane has its row: the slot takes batch j + 2
         fetch(j & 1, nb2, ix2);
+        const int al2 = own_cluster(cb2, nb2, ix2);
         int cb3, nb3, ix3;
         meta(j + 3, cb3, nb3, ix3);
         if (lane < nb) {
-            if (a < 0) {
+            if (mixed) {
+                // every centroid, in index order (the argmin with ties to the
+                // lower index); for a heavy point the evaluations counted are
+                // the ones Clauses 3 and 2 leave, as in a cluster's batch
+                const float *hl = halfD + (size_t)max(a, 0) * k;
+                float tl = 0.0f;
+                if (a >= 0) {
+                    tl = __fmaf_ru(bound_up(d2_reg<DV>(xk, cent + (size_t)a * DV), p.g_up, p.tiny), p.onepk, p.tau);
+                    ++my_evals;
+                } else {
+                    my_evals += k;
+                }
                 best = 0;
-                for (int c = 0; c < k; ++c) {
+                int c = 0;
+                for (; c + 4 <= k; c += 4) {
+                    float r[4];
+                    d2_reg4<DV>(xk, cent + (size_t)c * DV, cent + (size_t)(c + 1) * DV, cent + (size_t)(c + 2) * DV,
+                                cent + (size_t)(c + 3) * DV, r);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (r[q] < bd) { bd = r[q]; best = c + q; }
+                        my_evals += (a >= 0 && c + q != a && !(tl < hl[c + q])) ? 1u : 0u;
+                    }
+                }
+                for (; c < k; ++c) {
                     const float r = d2_reg<DV>(xk, cent + (size_t)c * DV);
                     if (r < bd) { bd = r; best = c; }
+                    my_evals += (a >= 0 && c != a && !(tl < hl[c])) ? 1u : 0u;
                 }
-                my_evals += k;
             } else {
                 // Clause 3: tighten u to (a bound on) the exact d(v, c_a)
                 bd = d2_reg<DV>(xk, cent + (size_t)a * DV);
@@ -340,7 +390,7 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
         // union: one that its own bound prunes is strictly farther than c_a
         // in computed FP32 values, so it cannot change the argmin (only the
         // lanes it survives count it as an evaluation).
-        if (a >= 0) {
+        if (!mixed) {
             const float *hrow = halfD + (size_t)a * k;
             // tst >= 0 (sign bit cleared for -0): its bit pattern orders like the value
             const float tmax = __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(tst) & 0x7fffffffu));
@@ -403,8 +453,8 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
                 make_int2(ix0, (int)(((unsigned)best << 16) | ((unsigned)a & 0xFFFFu)));
         nchg += __popc(cm);
         my_changed += __popc(cm);
-        cb0 = cb1; nb0 = nb1; ix0 = ix1;
-        cb1 = cb2; nb1 = nb2; ix1 = ix2;
+        cb0 = cb1; nb0 = nb1; ix0 = ix1; al0 = al1;
+        cb1 = cb2; nb1 = nb2; ix1 = ix2; al1 = al2;
         cb2 = cb3; nb2 = nb3; ix2 = ix3;
     }
     cp_async_wait<0>();
@@ -664,15 +714,35 @@ __global__ void k_elkan_check(const IterParams p, IterStats *stats, const int32_
 
 // ------------------------------------------------------------ delta sums
 
+// Adds (NEG: subtracts) row xrow to cluster cl's TwoSum accumulators, lane jl
+// of the row's lane group taking dimensions jl, jl + 32, ...
+template <int DV, bool NEG>
+__device__ __forceinline__ void dl_add(float *acc_hi, float *acc_lo, int cl, const float *xrow, int jl) {
+    constexpr int GW = DV < 32 ? DV : 32;
+#pragma unroll
+    for (int r = 0; r < DV / GW; ++r) {
+        const int o = cl * DV + jl + GW * r;
+        const float x = xrow[jl + GW * r];
+        float h = acc_hi[o], l = acc_lo[o];
+        two_sum_reg(h, l, NEG ? -x : x);
+        acc_hi[o] = h;
+        acc_lo[o] = l;
+    }
+}
+
 // Phase II by deltas: CTA b takes the change lists of scan CTA b, each
 // split into p.dl_split consecutive parts with one warp per part (warp w:
 // list w / dl_split, part w % dl_split).  A warp takes its entries 32 at a
-// time, loads their rows straight into registers (32 row loads in flight per
-// lane, lanes walking the dimensions), then adds each row to its new cluster
-// and subtracts it from its old one in its TwoSum accumulators (shared
-// memory), in list order; the CTA adds its warps' accumulators in warp order
-// into its partial slot.  Order and grouping depend only on the lists and
-// the fixed split: deterministic.
+// time; the rows of the next 32 are copied into the warp's second row slot
+// (cp.async, 16-byte pieces) while it adds the current ones.  A row takes
+// GW = min(d, 32) lanes, so P = 32 / GW rows go at once (lane group g has
+// row sP + g in step s): each row is added to its new cluster and then
+// subtracted from its old one in the warp's TwoSum accumulators (shared
+// memory).  Rows of one step that meet in a cluster go one group after the
+// other, so every (cluster, dimension) accumulator takes its rows in list
+// order, adds before subtractions within a step.  The CTA adds its warps'
+// accumulators in warp order into its partial slot.  Order and grouping
+// depend only on the lists and the fixed split: deterministic.
 template <int DV>
 __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int32_t *mode_dense, int32_t *nslots,
                                                     int32_t *fresh) {
@@ -681,11 +751,17 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int nthr = blockDim.x;
     const int k = p.k;
-    constexpr int R = DV < 32 ? 1 : DV / 32; // dimensions per lane
+    constexpr int GW = DV < 32 ? DV : 32; // lanes per row
+    constexpr int P = 32 / GW;            // rows per step
+    constexpr int CH = DV / 4;            // 16-byte pieces per row
+    constexpr unsigned GMASK = (1u << P) - 1u;
+    const int g = lane / GW, jl = lane % GW;
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
-    float *acc_hi = reinterpret_cast<float *>(sm + w * p.dl_warp_stride);
+    unsigned char *wr = sm + (size_t)w * p.dl_warp_stride;
+    float *acc_hi = reinterpret_cast<float *>(wr);
     float *acc_lo = acc_hi + (size_t)k * DV;
     int *cnt = reinterpret_cast<int *>(acc_lo + (size_t)k * DV);
+    float *slots = reinterpret_cast<float *>(wr + p.dl_off_rows); // 2 x 32 rows of DV floats
     for (int e = lane; e < 2 * k * DV; e += 32) acc_hi[e] = 0.0f;
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     __syncwarp();
@@ -693,47 +769,89 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     const int2 *chg = p.chg + (size_t)list * p.rec_cap * 32;
     const int nchg = p.chg_cnt[list];
     const int e0 = (int)((int64_t)nchg * part / p.dl_split), e1 = (int)((int64_t)nchg * (part + 1) / p.dl_split);
-    for (int g0 = e0; g0 < e1; g0 += 32) {
-        const int nb = min(32, e1 - g0);
-        int idx = 0, cl = 0;
-        if (lane < nb) {
-            const int2 v = chg[g0 + lane];
-            idx = v.x;
-            cl = v.y;
-            atomicAdd(&cnt[(unsigned)cl >> 16], 1);
-            if ((cl & 0xFFFF) != 0xFFFF) atomicAdd(&cnt[cl & 0xFFFF], -1);
+    auto entry = [&](int g0) { return g0 + lane < e1 ? chg[g0 + lane] : make_int2(0, 0); };
+    // the rows of entries g0 .. g0 + 31 (those below e1) into slot `slot`
+    auto fetch = [&](int slot, int g0, int idx) {
+        const int nb = max(0, min(32, e1 - g0));
+        float *dst = slots + (size_t)slot * 32 * DV;
+#pragma unroll
+        for (int base = 0; base < 32 * CH; base += 32) {
+            const int f = base + lane;
+            const int ir = __shfl_sync(FULL_MASK, idx, f / CH);
+            if (f < nb * CH) cp_async16(dst + (size_t)f * 4, p.X + (int64_t)ir * DV + (f % CH) * 4);
         }
-        float x[32][R];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int iq = __shfl_sync(FULL_MASK, idx, q);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int j = lane + 32 * r;
-                x[q][r] = (q < nb && j < DV) ? __ldg(p.X + (int64_t)iq * DV + j) : 0.0f;
+        cp_async_commit();
+    };
+    int2 cur = entry(e0), nxt = entry(e0 + 32);
+    fetch(0, e0, cur.x);
+    int slot = 0;
+    for (int g0 = e0; g0 < e1; g0 += 32) {
+        const int2 nn = entry(g0 + 64);
+        fetch(slot ^ 1, g0 + 32, nxt.x); // (nothing when g0 + 32 >= e1)
+        const int nb = min(32, e1 - g0);
+        const bool mine = lane < nb; // this lane's entry (entry `lane` of the batch) exists
+        const int cn_l = (int)((unsigned)cur.y >> 16), co_l = cur.y & 0xFFFF;
+        if (mine) {
+            atomicAdd(&cnt[cn_l], 1);
+            if (co_l != 0xFFFF) atomicAdd(&cnt[co_l], -1);
+        }
+        const bool any_old = __any_sync(FULL_MASK, mine && co_l != 0xFFFF);
+        // entries whose step (entry / P) has another entry of the same new
+        // (old) cluster: those steps go one group after the other
+        unsigned clash_n = 0, clash_o = 0;
+        if constexpr (P > 1) {
+            const int st = lane / P;
+            const unsigned mn = __match_any_sync(FULL_MASK, mine ? (st << 16 | cn_l) : -1 - lane);
+            clash_n = __ballot_sync(FULL_MASK, __popc(mn) > 1);
+            if (any_old) {
+                const bool ho = mine && co_l != 0xFFFF;
+                const unsigned mo = __match_any_sync(FULL_MASK, ho ? (st << 16 | co_l) : -1 - lane);
+                clash_o = __ballot_sync(FULL_MASK, __popc(mo) > 1);
             }
         }
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            if (q >= nb) break;
-            const int c = __shfl_sync(FULL_MASK, cl, q);
+        cp_async_wait<1>();
+        __syncwarp();
+        const float *rb = slots + (size_t)slot * 32 * DV;
+        for (int s0 = 0; s0 < nb; s0 += P) {
+            const int q = s0 + g; // this lane group's entry
+            const int c = __shfl_sync(FULL_MASK, cur.y, q);
+            const bool hn = q < nb;
+            const float *xrow = rb + (size_t)q * DV;
             const int cn = (int)((unsigned)c >> 16), co = c & 0xFFFF;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int j = lane + 32 * r;
-                if (j < DV) {
-                    two_sum_acc(&acc_hi[cn * DV + j], &acc_lo[cn * DV + j], x[q][r]);
-                    if (co != 0xFFFF) two_sum_acc(&acc_hi[co * DV + j], &acc_lo[co * DV + j], -x[q][r]);
+            if (P == 1 || ((clash_n >> s0) & GMASK) == 0) {
+                if (hn) dl_add<DV, false>(acc_hi, acc_lo, cn, xrow, jl);
+            } else {
+                for (int gg = 0; gg < P; ++gg) {
+                    if (hn && g == gg) dl_add<DV, false>(acc_hi, acc_lo, cn, xrow, jl);
+                    __syncwarp();
                 }
             }
+            if constexpr (P > 1) __syncwarp(); // later groups see these sums
+            if (any_old) {
+                const bool ho = hn && co != 0xFFFF;
+                if (P == 1 || ((clash_o >> s0) & GMASK) == 0) {
+                    if (ho) dl_add<DV, true>(acc_hi, acc_lo, co, xrow, jl);
+                } else {
+                    for (int gg = 0; gg < P; ++gg) {
+                        if (ho && g == gg) dl_add<DV, true>(acc_hi, acc_lo, co, xrow, jl);
+                        __syncwarp();
+                    }
+                }
+                if constexpr (P > 1) __syncwarp();
+            }
         }
+        __syncwarp(); // every lane is done with the slot before it is refilled
+        cur = nxt;
+        nxt = nn;
+        slot ^= 1;
     }
+    cp_async_wait<0>();
     __syncthreads();
     const int kd = k * DV, nw = nthr >> 5;
     for (int e = tid; e < kd; e += nthr) {
         double sum = 0.0;
         for (int q = 0; q < nw; ++q) {
-            const float *a = reinterpret_cast<const float *>(sm + q * p.dl_warp_stride);
+            const float *a = reinterpret_cast<const float *>(sm + (size_t)q * p.dl_warp_stride);
             sum += (double)a[e];
             sum += (double)a[kd + e];
         }
@@ -741,7 +859,7 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     }
     for (int c = tid; c < k; c += nthr) {
         long long sum = 0;
-        for (int q = 0; q < nw; ++q) sum += reinterpret_cast<const int *>(sm + q * p.dl_warp_stride + (size_t)2 * kd * 4)[c];
+        for (int q = 0; q < nw; ++q) sum += reinterpret_cast<const int *>(sm + (size_t)q * p.dl_warp_stride + (size_t)2 * kd * 4)[c];
         p.part_cnt[(size_t)c * p.part_stride + blockIdx.x] = sum;
     }
 }

@@ -214,6 +214,8 @@ struct knor_ctx {
     float *host_registered = nullptr; // ... registered by knor_create (pageable memory)
     IterParams ip_sel{}, ip_delta{};
     size_t smem_sel = 0;
+    int sel_M = 0;                   // k_mti_sel: heavy from the sel_M-th smallest 1/2 d(c_a, c) (0: no split)
+    float *theta = nullptr;          // k heavy thresholds
     bool mti_split = false, dense_split = false; // the split kernels run the MTI / dense scans
     int grid_split = 0;
     float *xdn = nullptr, *rxdn = nullptr; // FP8: norms of x / sigma (else aliases of xn, rxn)
@@ -292,7 +294,7 @@ static void free_all(knor_ctx *c) {
     void *bufs[] = {c->X_on_host ? nullptr : c->X, c->st,     c->C0,       c->C64,  c->S,     c->part_S, c->C32,  c->C32n,
                     c->halfD,  c->s,      c->F,        c->cnt,  c->cnt_next, c->part_cnt, c->ctr, c->stats,
                     c->flags,  c->d_idx,  c->d_bad,    c->Xb,   c->Cb,    c->xn,     c->cn,   c->absmax, c->pit,
-                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma, c->rec, c->rec_cnt, c->chg, c->chg_cnt, c->lb,
+                    c->a_next, c->rlist,  c->rcount, c->rcand, c->Xc, c->rm1, c->rxn, c->wacc, c->sigma, c->rec, c->rec_cnt, c->chg, c->chg_cnt, c->lb, c->theta,
                     c->xdn != c->xn ? c->xdn : nullptr, c->rxdn != c->rxn ? c->rxdn : nullptr};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -438,9 +440,11 @@ static size_t plan_layout_sel(const knor_ctx *c, IterParams &p) {
     };
     p.off_s = take((size_t)k * 4);
     p.off_F = take((size_t)k * 4);
+    p.off_th = take(c->sel_M > 0 ? (size_t)k * 4 : 0);
     p.w_base = take(0);
     p.w_bucket = 0;
-    const size_t bucket = (((size_t)(k + 1) * (32 + 1) * 4) + 15) & ~(size_t)15; // 32 slots and a count
+    // k + 1 buckets (one per cluster, and the mixed one) of 32 slots and a count
+    const size_t bucket = (((size_t)(k + 1) * (32 + 1) * 4) + 15) & ~(size_t)15;
     p.w_state = (int32_t)bucket;
     p.w_stride = (int32_t)(bucket + (size_t)WSTAGES * WCH * sizeof(PtState));
     p.sp_wpb = SP_WPB;
@@ -472,12 +476,14 @@ static size_t plan_layout_scan(const knor_ctx *c, IterParams &p) {
     p.sp_wpb = SP_WPB;
     const size_t total = off + (size_t)SP_WPB * p.sp_warp_stride;
     if (total > 112 * 1024) return 0; // keep at least two CTAs per SM
-    // k_mti_delta: per warp, TwoSum accumulators and counts; each change list
-    // split over up to 4 warps while a CTA stays within 96 KB
-    p.dl_warp_stride = (int32_t)(((size_t)2 * kd * 4 + (size_t)k * 4 + 15) & ~(size_t)15);
+    // k_mti_delta: per warp, TwoSum accumulators and counts, then two slots
+    // of 32 rows; each change list split over up to 4 warps while two CTAs
+    // fit on an SM
+    p.dl_off_rows = (int32_t)(((size_t)2 * kd * 4 + (size_t)k * 4 + 15) & ~(size_t)15);
+    p.dl_warp_stride = p.dl_off_rows + 2 * 32 * d * 4;
     p.dl_split = 4;
-    while (p.dl_split > 1 && (size_t)SP_WPB * p.dl_split * p.dl_warp_stride > 96 * 1024) p.dl_split /= 2;
-    if ((size_t)SP_WPB * p.dl_split * p.dl_warp_stride > 200 * 1024) return 0;
+    while (p.dl_split > 1 && (size_t)SP_WPB * p.dl_split * p.dl_warp_stride > 113 * 1024) p.dl_split /= 2;
+    if ((size_t)SP_WPB * p.dl_split * p.dl_warp_stride > 227 * 1024) return 0;
     p.warp_kernels = 3;
     p.acc_global = 0;
     return total;
@@ -899,6 +905,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         if (ssc) {
             int bs = 0, bdl = 0;
             KCU(mti_scan_attr(c->dv, SP_WPB, ssc, &bsplit));
+            // heavy points (Clause 2 would leave them M = k / 3 or more
+            // candidates) from k = 8 on; KNOR_SEL_M (a tuning knob) sets M,
+            // 0 turns the split off
+            c->sel_M = std::max(0, getenv_int("KNOR_SEL_M", k >= 8 ? std::max(2, k / 3) : 0));
             c->smem_sel = plan_layout_sel(c, c->ip_sel);
             KCU(mti_sel_attr(SP_WPB, c->smem_sel, &bs));
             KCU(mti_delta_attr(c->dv, (size_t)SP_WPB * ps.dl_split * ps.dl_warp_stride, ps.dl_split, &bdl));
@@ -955,8 +965,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     // (the split kernels all run on the split grid, in waves where fewer of
     // their CTAs fit on an SM)
     c->grid_dense = c->dense_split ? c->grid_split : bd * c->num_sms;
-    if (c->mti_split) c->grid_mti = c->grid_split;
-    c->grid_mti = bm * c->num_sms;
+    c->grid_mti = c->mti_split ? c->grid_split : bm * c->num_sms;
     // Both scans use the same accumulation mode: per-CTA partial slots, or,
     // when k x d sums do not fit in shared memory, one slot updated by FP64
     // atomics.
@@ -994,6 +1003,10 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         if (c->mti_split) {
             KC(dalloc(c, &c->rec, (size_t)(nw * cap * SP_REC)));
             KC(dalloc(c, &c->rec_cnt, (size_t)nw));
+            if (c->sel_M > 0) {
+                KC(dalloc(c, &c->theta, (size_t)k));
+                c->ip_sel.theta = c->theta;
+            }
         }
         KC(dalloc(c, &c->chg, (size_t)(nw * cap * 32)));
         KC(dalloc(c, &c->chg_cnt, (size_t)nw));
@@ -1041,6 +1054,8 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
     f.halfD = c->halfD; f.s = c->s; f.F = c->F; f.cnt_out = c->cnt; f.ctr = c->ctr; f.stats = c->stats;
     f.run_iter = c->flags + F_RUN_ITER; f.total_iter = c->flags + F_TOTAL_ITER;
     f.max_iters_dev = c->flags + F_MAX_ITERS;
+    f.theta = c->theta;
+    f.th_M = c->sel_M;
 
     if (tc_form) {
         // The precision form scans every point each iteration (no MTI bounds):
@@ -1396,6 +1411,7 @@ knor_status knor_set_state(knor_ctx *c, const void *buf, size_t size) {
         KNOR_CUDA(c, cudaMemcpyAsync(pt.dst, p, pt.bytes, cudaMemcpyHostToDevice, c->stream));
         p += pt.bytes;
     }
+    KNOR_CUDA(c, launch_theta(c->fp, c->stream)); // k_mti_sel's thresholds from the restored table
     int32_t fl[F_COUNT] = {0, h.total_iter, 1, h.mode_dense, 1, 1, 0};
     c->host_total_iter = h.total_iter;
     KNOR_CUDA(c, cudaMemcpyAsync(c->flags, fl, sizeof(fl), cudaMemcpyHostToDevice, c->stream));

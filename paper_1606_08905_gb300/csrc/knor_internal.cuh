@@ -127,6 +127,7 @@ struct IterParams {
     int2 *chg;
     int32_t *chg_cnt;
     int32_t dl_warp_stride, dl_split; // k_mti_delta: per-warp region, warps per change list
+    int32_t dl_off_rows;   // k_mti_delta: the two 32-row slots within the per-warp region
     int32_t dl_dense;      // 1: dense iterations sum by change lists (k_dense_scan)
     int32_t dl_mti;        // 1: MTI iterations sum by change lists (k_mti_scan)
     // Elkan's lower bounds (ablation of MTI): n x k FP32, cluster-major
@@ -135,6 +136,11 @@ struct IterParams {
     // d(x_i, c^t) from below; null when not kept
     float *lb;
     float ginv_dn;         // <= (1 - (d+2) 2^-24): turns a computed d^2 into a lower bound
+    // k_mti_sel's heavy points: a surviving point of cluster a whose Clause-1
+    // test value reaches theta[a] goes to the mixed bucket (null: no split);
+    // off_th: the thresholds' place in k_mti_sel's shared memory
+    const float *theta;
+    int32_t off_th;
 };
 
 // Parameters of the reduction / finalize kernels.
@@ -158,6 +164,10 @@ struct FinParams {
     const int32_t *max_iters_dev; // run limit (for the device-side loop)
     int32_t snapshot;       // 1: record stats (0 for the table at reset)
     unsigned long long cond_handle; // cudaGraphConditionalHandle, 0 if none
+    // k_mti_sel's heavy thresholds (null when not used): theta[a] = the
+    // th_M-th smallest of 1/2 d(c_a, c) over c != a (+inf when th_M > k - 1)
+    float *theta;
+    int32_t th_M;
 };
 
 // Candidate slots per re-scored point in the precision form (count + 8,
@@ -241,6 +251,7 @@ cudaError_t elkan_scan_attr(int dv, size_t smem, int *blocks_per_sm);
 cudaError_t launch_elkan_check(int dv, const IterParams &p, IterStats *stats, const int32_t *run_iter,
                                cudaStream_t s);
 cudaError_t launch_reduce(const FinParams &f, const int32_t *nslots, const int32_t *fresh, cudaStream_t s);
+cudaError_t launch_theta(const FinParams &f, cudaStream_t s);
 cudaError_t launch_table(const FinParams &f, int32_t *mode_dense, int need_table, int recompute_every,
                          int always_dense, cudaStream_t s);
 cudaError_t launch_validate(const float *X, int64_t count, unsigned long long *bad, cudaStream_t s);
