@@ -714,19 +714,20 @@ __global__ void k_elkan_check(const IterParams p, IterStats *stats, const int32_
 
 // ------------------------------------------------------------ delta sums
 
-// Adds (NEG: subtracts) row xrow to cluster cl's TwoSum accumulators, lane jl
-// of the row's lane group taking dimensions jl, jl + 32, ...
+// Adds (NEG: subtracts) row xrow to cluster cl's TwoSum accumulators (hi, lo
+// pairs side by side, so that one 8-byte access moves both and a lane group
+// of 16 spans all 32 banks), lane jl of the row's lane group taking
+// dimensions jl, jl + 32, ...
 template <int DV, bool NEG>
-__device__ __forceinline__ void dl_add(float *acc_hi, float *acc_lo, int cl, const float *xrow, int jl) {
+__device__ __forceinline__ void dl_add(float2 *acc, int cl, const float *xrow, int jl) {
     constexpr int GW = DV < 32 ? DV : 32;
 #pragma unroll
     for (int r = 0; r < DV / GW; ++r) {
         const int o = cl * DV + jl + GW * r;
         const float x = xrow[jl + GW * r];
-        float h = acc_hi[o], l = acc_lo[o];
-        two_sum_reg(h, l, NEG ? -x : x);
-        acc_hi[o] = h;
-        acc_lo[o] = l;
+        float2 v = acc[o];
+        two_sum_reg(v.x, v.y, NEG ? -x : x);
+        acc[o] = v;
     }
 }
 
@@ -758,11 +759,10 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     const int g = lane / GW, jl = lane % GW;
     if (blockIdx.x == 0 && tid == 0) { *nslots = (int)gridDim.x; *fresh = 0; }
     unsigned char *wr = sm + (size_t)w * p.dl_warp_stride;
-    float *acc_hi = reinterpret_cast<float *>(wr);
-    float *acc_lo = acc_hi + (size_t)k * DV;
-    int *cnt = reinterpret_cast<int *>(acc_lo + (size_t)k * DV);
+    float2 *acc = reinterpret_cast<float2 *>(wr); // k x DV (hi, lo) pairs
+    int *cnt = reinterpret_cast<int *>(acc + (size_t)k * DV);
     float *slots = reinterpret_cast<float *>(wr + p.dl_off_rows); // 2 x 32 rows of DV floats
-    for (int e = lane; e < 2 * k * DV; e += 32) acc_hi[e] = 0.0f;
+    for (int e = lane; e < k * DV; e += 32) acc[e] = make_float2(0.0f, 0.0f);
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     __syncwarp();
     const int list = blockIdx.x * SPW + w / p.dl_split, part = w % p.dl_split;
@@ -812,32 +812,43 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
         cp_async_wait<1>();
         __syncwarp();
         const float *rb = slots + (size_t)slot * 32 * DV;
-        for (int s0 = 0; s0 < nb; s0 += P) {
-            const int q = s0 + g; // this lane group's entry
-            const int c = __shfl_sync(FULL_MASK, cur.y, q);
-            const bool hn = q < nb;
-            const float *xrow = rb + (size_t)q * DV;
-            const int cn = (int)((unsigned)c >> 16), co = c & 0xFFFF;
-            if (P == 1 || ((clash_n >> s0) & GMASK) == 0) {
-                if (hn) dl_add<DV, false>(acc_hi, acc_lo, cn, xrow, jl);
-            } else {
-                for (int gg = 0; gg < P; ++gg) {
-                    if (hn && g == gg) dl_add<DV, false>(acc_hi, acc_lo, cn, xrow, jl);
-                    __syncwarp();
-                }
+        if (nb == 32 && !any_old && clash_n == 0) {
+            // a full batch of additions without clashes (the dense step's)
+#pragma unroll
+            for (int s0 = 0; s0 < 32; s0 += P) {
+                const int q = s0 + g;
+                const int c = __shfl_sync(FULL_MASK, cur.y, q);
+                dl_add<DV, false>(acc, (int)((unsigned)c >> 16), rb + (size_t)q * DV, jl);
+                if constexpr (P > 1) __syncwarp();
             }
-            if constexpr (P > 1) __syncwarp(); // later groups see these sums
-            if (any_old) {
-                const bool ho = hn && co != 0xFFFF;
-                if (P == 1 || ((clash_o >> s0) & GMASK) == 0) {
-                    if (ho) dl_add<DV, true>(acc_hi, acc_lo, co, xrow, jl);
+        } else {
+            for (int s0 = 0; s0 < nb; s0 += P) {
+                const int q = s0 + g; // this lane group's entry
+                const int c = __shfl_sync(FULL_MASK, cur.y, q);
+                const bool hn = q < nb;
+                const float *xrow = rb + (size_t)q * DV;
+                const int cn = (int)((unsigned)c >> 16), co = c & 0xFFFF;
+                if (P == 1 || ((clash_n >> s0) & GMASK) == 0) {
+                    if (hn) dl_add<DV, false>(acc, cn, xrow, jl);
                 } else {
                     for (int gg = 0; gg < P; ++gg) {
-                        if (ho && g == gg) dl_add<DV, true>(acc_hi, acc_lo, co, xrow, jl);
+                        if (hn && g == gg) dl_add<DV, false>(acc, cn, xrow, jl);
                         __syncwarp();
                     }
                 }
-                if constexpr (P > 1) __syncwarp();
+                if constexpr (P > 1) __syncwarp(); // later groups see these sums
+                if (any_old) {
+                    const bool ho = hn && co != 0xFFFF;
+                    if (P == 1 || ((clash_o >> s0) & GMASK) == 0) {
+                        if (ho) dl_add<DV, true>(acc, co, xrow, jl);
+                    } else {
+                        for (int gg = 0; gg < P; ++gg) {
+                            if (ho && g == gg) dl_add<DV, true>(acc, co, xrow, jl);
+                            __syncwarp();
+                        }
+                    }
+                    if constexpr (P > 1) __syncwarp();
+                }
             }
         }
         __syncwarp(); // every lane is done with the slot before it is refilled
@@ -851,9 +862,9 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     for (int e = tid; e < kd; e += nthr) {
         double sum = 0.0;
         for (int q = 0; q < nw; ++q) {
-            const float *a = reinterpret_cast<const float *>(sm + (size_t)q * p.dl_warp_stride);
-            sum += (double)a[e];
-            sum += (double)a[kd + e];
+            const float2 a = reinterpret_cast<const float2 *>(sm + (size_t)q * p.dl_warp_stride)[e];
+            sum += (double)a.x;
+            sum += (double)a.y;
         }
         p.part_S[(size_t)e * p.part_stride + blockIdx.x] = sum;
     }
