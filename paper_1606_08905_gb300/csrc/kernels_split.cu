@@ -298,11 +298,13 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
     auto fetch = [&](int slot, int nb, int idx) {
         constexpr int CH = DV / 4;
         float *dst = slots + (size_t)slot * 32 * rs;
-        for (int base = 0; base < nb * CH; base += 32) {
-            const int f = base + lane;
-            const int r = min(f / CH, 31);
+        // lane l copies piece l % CH of rows l / CH, l / CH + 32 / CH, ...
+        const int part = lane % CH;
+#pragma unroll
+        for (int base = 0; base < 32 * CH; base += 32) {
+            const int r = (base + lane) / CH;
             const int ir = __shfl_sync(FULL_MASK, idx, r);
-            if (f < nb * CH) cp_async16(dst + r * rs + (f % CH) * 4, p.X + (int64_t)ir * DV + (f % CH) * 4);
+            if (r < nb) cp_async16(dst + r * rs + part * 4, p.X + (int64_t)ir * DV + part * 4);
         }
         cp_async_commit();
     };
