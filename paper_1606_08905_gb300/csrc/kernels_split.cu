@@ -161,19 +161,19 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
             }
             amask |= (act ? 1u : 0u) << u;
         }
-        const int na = __popc(amask);
-        my_skipped += nvalid - na;
-        int incl = na;
+        my_skipped += nvalid - __popc(amask);
+        // this lane's first place among the chunk's survivors, and their
+        // number: one ballot per point slot (independent, short latency)
+        int pos = 0, total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= o) incl += v;
+        for (int u = 0; u < WPA; ++u) {
+            const unsigned b = __ballot_sync(FULL_MASK, (amask >> u) & 1u);
+            pos += __popc(b & ((1u << lane) - 1u));
+            total += __popc(b);
         }
-        const int total = __shfl_sync(FULL_MASK, incl, 31);
         // survivors in point order, staged in the state buffer just read
         int2 *stg = reinterpret_cast<int2 *>(stbuf + stage * WCH);
         __syncwarp();
-        int pos = incl - na;
 #pragma unroll
         for (int u = 0; u < WPA; ++u) {
             if ((amask >> u) & 1u) {
@@ -283,9 +283,10 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
     auto meta = [&](int j, int &cb, int &nb, int &idx) {
         if (j < nrec) {
             const int32_t *r = rec + (size_t)j * SP_REC;
-            cb = r[0];
-            nb = r[1];
-            idx = lane < nb ? r[4 + lane] : 0;
+            const int2 h = *reinterpret_cast<const int2 *>(r);
+            cb = h.x;
+            nb = h.y;
+            idx = r[4 + lane]; // (slots past nb hold stale values, never used)
         } else {
             cb = 0;
             nb = 0;
