@@ -273,16 +273,18 @@ __global__ void __launch_bounds__(SPT, DV <= 32 ? 5 : 2) k_mti_scan(const IterPa
     for (int c = tid; c < k; c += SPT) F_s[c] = p.F[c];
     const int gw = blockIdx.x * SPW + w;
     float *slots = reinterpret_cast<float *>(sm + p.sp_off_warp + w * p.sp_warp_stride); // 2 x 32 rows
-    int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32; // (point, new << 16 | old) of the points that changed
+    int2 *chg = p.chg + (size_t)gw * p.chg_cap; // (point, new << 16 | old) of the points that changed
     int nchg = 0;
     __syncthreads();
 
-    const int32_t *rec = p.rec + (size_t)gw * p.rec_cap * SP_REC;
-    const int nrec = p.rec_cnt[gw];
+    // this warp's record lists (sel_mult of them, back to back in memory)
+    const int32_t *rec = p.rec + (size_t)gw * p.sel_mult * p.rec_cap * SP_REC;
+    const int n0 = p.rec_cnt[gw * p.sel_mult];
+    const int nrec = n0 + (p.sel_mult == 2 ? p.rec_cnt[gw * 2 + 1] : 0);
     // Record j's header and this lane's point index.
     auto meta = [&](int j, int &cb, int &nb, int &idx) {
         if (j < nrec) {
-            const int32_t *r = rec + (size_t)j * SP_REC;
+            const int32_t *r = rec + (size_t)(j < n0 ? j : j - n0 + (int)p.rec_cap) * SP_REC;
             const int2 h = *reinterpret_cast<const int2 *>(r);
             cb = h.x;
             nb = h.y;
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(SPT) k_dense_scan(const IterParams p, const in
     int64_t lo, hi;
     warp_range(p.n, gw, nw, lo, hi);
     const int64_t ntile = (hi - lo + TR - 1) / TR;
-    int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32;
+    int2 *chg = p.chg + (size_t)gw * p.chg_cap;
     int nchg = 0;
     auto load_tile = [&](int slot, int64_t t) {
         if (t < ntile) {
@@ -615,7 +617,7 @@ __global__ void __launch_bounds__(SPT) k_elkan_scan(const IterParams p, const in
     const int gw = blockIdx.x * SPW + w, nw = gridDim.x * SPW;
     int64_t lo, hi;
     warp_range(p.n, gw, nw, lo, hi);
-    int2 *chg = p.chg + (size_t)gw * p.rec_cap * 32;
+    int2 *chg = p.chg + (size_t)gw * p.chg_cap;
     int nchg = 0;
     unsigned my_skipped = 0, my_evals = 0, my_changed = 0;
     for (int64_t base = lo; base < hi; base += 32) {
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(512) k_mti_delta(const IterParams p, const int
     for (int c = lane; c < k; c += 32) cnt[c] = 0;
     __syncwarp();
     const int list = blockIdx.x * SPW + w / p.dl_split, part = w % p.dl_split;
-    const int2 *chg = p.chg + (size_t)list * p.rec_cap * 32;
+    const int2 *chg = p.chg + (size_t)list * p.chg_cap;
     const int nchg = p.chg_cnt[list];
     const int e0 = (int)((int64_t)nchg * part / p.dl_split), e1 = (int)((int64_t)nchg * (part + 1) / p.dl_split);
     auto entry = [&](int g0) { return g0 + lane < e1 ? chg[g0 + lane] : make_int2(0, 0); };

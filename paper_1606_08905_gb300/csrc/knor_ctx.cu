@@ -215,6 +215,7 @@ struct knor_ctx {
     IterParams ip_sel{}, ip_delta{};
     size_t smem_sel = 0;
     int sel_M = 0;                   // k_mti_sel: heavy from the sel_M-th smallest 1/2 d(c_a, c) (0: no split)
+    int sel_mult = 1;                // k_mti_sel warps per scan warp (1 or 2)
     float *theta = nullptr;          // k heavy thresholds
     bool mti_split = false, dense_split = false; // the split kernels run the MTI / dense scans
     int grid_split = 0;
@@ -541,7 +542,7 @@ static cudaError_t scan_mti(knor_ctx *c, cudaStream_t s) {
 // Clause 1 and the batch records of the split MTI scan.
 static cudaError_t scan_select(knor_ctx *c, cudaStream_t s) {
     if (!c->mti_split || c->opts.elkan) return cudaSuccess;
-    return launch_mti_sel(c->ip_sel, c->grid_split, c->smem_sel, s, c->flags + F_MODE_DENSE);
+    return launch_mti_sel(c->ip_sel, c->grid_split * c->sel_mult, c->smem_sel, s, c->flags + F_MODE_DENSE);
 }
 
 // Phase II from the change lists of the split scans (a no-op in a dense
@@ -901,7 +902,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         IterParams ps{};
         const int choice = o.elkan ? 0 : getenv_int("KNOR_MTI_KERNEL", 0);
         const size_t ssc = !tc_form ? plan_layout_scan(c, ps) : 0;
-        int bsplit = 0;
+        int bsplit = 0, bsel = 0;
         if (ssc) {
             int bs = 0, bdl = 0;
             KCU(mti_scan_attr(c->dv, SP_WPB, ssc, &bsplit));
@@ -911,6 +912,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
             c->sel_M = std::max(0, getenv_int("KNOR_SEL_M", k >= 8 ? std::max(2, k / 3) : 0));
             c->smem_sel = plan_layout_sel(c, c->ip_sel);
             KCU(mti_sel_attr(SP_WPB, c->smem_sel, &bs));
+            bsel = bs;
             KCU(mti_delta_attr(c->dv, (size_t)SP_WPB * ps.dl_split * ps.dl_warp_stride, ps.dl_split, &bdl));
             if (bs < 1 || bdl < 1) bsplit = 0;
         }
@@ -960,6 +962,7 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         else if (sm) { c->ip_mti = pm; c->smem_mti = sm; KCU(mti_w_attr(c->dv, sm, &bm)); }
         else { c->smem_mti = plan_layout(c, true, c->ip_mti); KCU(mti_attr(c->dv, c->smem_mti, &bm)); }
         c->grid_split = split_mult * c->num_sms;
+        if (c->mti_split && bsel >= 2 * split_mult && getenv_int("KNOR_SEL_MULT", 2) >= 2) c->sel_mult = 2;
     }
     if (bd < 1 || bm < 1) { c->err = "knor_create: kernel does not fit on an SM"; return bail(KNOR_ERR_CUDA); }
     // (the split kernels all run on the split grid, in waves where fewer of
@@ -1000,9 +1003,15 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         const int64_t units = (n + WPA - 1) / WPA;
         const int64_t range = ((units + nw - 1) / nw) * WPA;
         const int64_t cap = (range + 31) / 32 + k + 1;
+        // k_mti_sel: two warps per scan warp where twice the split grid's
+        // CTAs fit on an SM (its warps wait on shared memory: more of them
+        // hide more), each over half the range, with a record list of its own
+        const int64_t nws = nw * c->sel_mult;
+        const int64_t range_s = ((units + nws - 1) / nws) * WPA;
+        const int64_t cap_s = (range_s + 31) / 32 + k + 1;
         if (c->mti_split) {
-            KC(dalloc(c, &c->rec, (size_t)(nw * cap * SP_REC)));
-            KC(dalloc(c, &c->rec_cnt, (size_t)nw));
+            KC(dalloc(c, &c->rec, (size_t)(nws * cap_s * SP_REC)));
+            KC(dalloc(c, &c->rec_cnt, (size_t)nws));
             if (c->sel_M > 0) {
                 KC(dalloc(c, &c->theta, (size_t)k));
                 c->ip_sel.theta = c->theta;
@@ -1025,7 +1034,9 @@ knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, kn
         for (IterParams *q : {&c->ip_mti, &c->ip_sel, &c->ip_dense, &c->ip_delta}) {
             q->rec = c->rec;
             q->rec_cnt = c->rec_cnt;
-            q->rec_cap = cap;
+            q->rec_cap = cap_s;
+            q->sel_mult = c->sel_mult;
+            q->chg_cap = cap * 32;
             q->chg = c->chg;
             q->chg_cnt = c->chg_cnt;
             q->dl_dense = c->dense_split ? 1 : 0;

@@ -110,22 +110,26 @@ struct IterParams {
     // split MTI scan: the row stride of a staged batch, in floats (d + 4)
     int32_t sp_rs;
     int32_t *err;          // set when a bounded wait gives up (KNOR_ERR_TIMEOUT)
-    // split MTI scan (k_mti_sel + k_mti_scan): per-warp lists of batch
-    // records (SP_REC ints each: cluster, count, 32 point indices, padding),
-    // rec_cap records per warp, rec_cnt[warp] records written; warps per CTA
-    // and the per-warp shared-memory region of the scan (two row slots, then
-    // the warp's member counts)
+    // split MTI scan (k_mti_sel + k_mti_scan): per k_mti_sel warp a list of
+    // batch records (SP_REC ints each: cluster, count, 32 point indices,
+    // padding), rec_cap records each, rec_cnt[list] records written;
+    // k_mti_sel runs sel_mult (1 or 2) warps per scan warp, scan warp w taking
+    // lists w sel_mult, w sel_mult + 1 in order (their ranges make up its
+    // own); warps per CTA and the per-warp shared-memory region of the scan
+    // (two row slots, then the warp's member counts)
     int32_t *rec;
     int32_t *rec_cnt;
     int64_t rec_cap;
+    int32_t sel_mult;
     int32_t sp_wpb;
     int32_t sp_off_warp, sp_warp_stride, sp_off_cnt;
-    // change lists (point, new cluster << 16 | old cluster), 32 * rec_cap
-    // entries per warp, chg_cnt[warp] entries written; the delta kernel's
+    // change lists (point, new cluster << 16 | old cluster), chg_cap entries
+    // per scan warp, chg_cnt[warp] entries written; the delta kernel's
     // per-warp shared-memory region (accumulators and counts) and the number
     // of its warps that share one list
     int2 *chg;
     int32_t *chg_cnt;
+    int64_t chg_cap;
     int32_t dl_warp_stride, dl_split; // k_mti_delta: per-warp region, warps per change list
     int32_t dl_off_rows;   // k_mti_delta: the two 32-row slots within the per-warp region
     int32_t dl_dense;      // 1: dense iterations sum by change lists (k_dense_scan)
