@@ -143,7 +143,7 @@ typedef struct {
  *   init = KNOR_INIT_EXPLICIT: C^0 must be set with knor_set_init_centroids
  *     before the first iteration (KNOR_ERR_STATE otherwise).
  * Errors: KNOR_ERR_ARG if points or out is NULL, n < 1, d < 1, k < 1, k > n,
- * n*d > 2^40, or any coordinate is NaN, infinite or of magnitude above 1e15
+ * n > 2^31, n*d > 2^40, or any coordinate is NaN, infinite or of magnitude above 1e15
  * (so no squared distance can overflow FP32).  opts may be NULL (defaults).
  * On success *out owns the context; free it with knor_destroy. */
 knor_status knor_create(const float *points, int64_t n, int32_t d, int32_t k, knor_init init,
