@@ -69,12 +69,11 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
     const int k = p.k;
     float *s_s = reinterpret_cast<float *>(sm + p.off_s);
     float *F_s = reinterpret_cast<float *>(sm + p.off_F);
-    float *th_s = reinterpret_cast<float *>(sm + p.off_th); // heavy thresholds (when split)
-    const bool split_heavy = p.theta != nullptr;
+    float *th_s = reinterpret_cast<float *>(sm + p.off_th); // heavy thresholds (+inf: no split)
     for (int c = tid; c < k; c += SPT) {
         s_s[c] = p.s[c];
         F_s[c] = p.F[c];
-        if (split_heavy) th_s[c] = p.theta[c];
+        th_s[c] = p.theta != nullptr ? p.theta[c] : CUDART_INF_F;
     }
     unsigned char *wr = sm + p.w_base + w * p.w_stride;
     // buckets of 32 local indices: cluster a for its light points, k for
@@ -87,15 +86,18 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
     const int gw = blockIdx.x * SPW + w, nw = gridDim.x * SPW;
     int64_t lo, hi;
     warp_range(p.n, gw, nw, lo, hi);
-    const int64_t nchunk = (hi - lo + WCH - 1) / WCH;
+    // offsets within the range are 32-bit (n <= 2^31)
+    const int len = (int)(hi - lo);
+    const int nchunk = (len + WCH - 1) / WCH;
+    const PtState *st_lo = p.st + lo;
     int32_t *rec = p.rec + (size_t)gw * p.rec_cap * SP_REC;
     int nrec = 0;
 
-    auto prefetch = [&](int stage, int64_t m) {
+    auto prefetch = [&](int stage, int m) {
         if (m < nchunk) {
-            const int64_t i0 = lo + m * WCH + (int64_t)lane * WPA;
-            if (i0 + WPA <= hi) {
-                const char *src = reinterpret_cast<const char *>(p.st + i0);
+            const int o0 = m * WCH + lane * WPA;
+            if (o0 + WPA <= len) {
+                const char *src = reinterpret_cast<const char *>(st_lo + o0);
                 char *dst = reinterpret_cast<char *>(stbuf + stage * WCH + lane * WPA);
 #pragma unroll
                 for (int v = 0; v < WPA * 8 / 16; ++v) cp_async16(dst + 16 * v, src + 16 * v);
@@ -120,13 +122,13 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
 #pragma unroll
     for (int s = 0; s < WSTAGES - 1; ++s) prefetch(s, s);
     int stage = 0;
-    for (int64_t m = 0; m < nchunk; ++m) {
+    for (int m = 0; m < nchunk; ++m) {
         prefetch((stage + WSTAGES - 1) % WSTAGES, m + WSTAGES - 1);
         cp_async_wait<WSTAGES - 1>();
         __syncwarp();
-        const int64_t i0 = lo + m * WCH + (int64_t)lane * WPA;
+        const int o0 = m * WCH + lane * WPA; // this lane's first point, from lo
         PtState ps[WPA];
-        if (i0 + WPA <= hi) {
+        if (o0 + WPA <= len) {
             const int4 *src = reinterpret_cast<const int4 *>(stbuf + stage * WCH + lane * WPA);
 #pragma unroll
             for (int v = 0; v < WPA / 2; ++v) {
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
         } else {
 #pragma unroll
             for (int u = 0; u < WPA; ++u) {
-                if (i0 + u < hi) ps[u] = p.st[i0 + u];
+                if (o0 + u < len) ps[u] = st_lo[o0 + u];
                 else { ps[u].ub = 0.0f; ps[u].a = -2; }
             }
         }
@@ -148,17 +150,15 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
         int bkey[WPA]; // bucket of each point
 #pragma unroll
         for (int u = 0; u < WPA; ++u) {
+            // branch-free: a = -2 past the range, -1 unassigned, else a cluster
             const int a = ps[u].a;
-            bkey[u] = k;
-            if (a == -2) continue;
-            ++nvalid;
-            bool act = true;
-            if (a >= 0) {
-                const float uu = __fadd_ru(ps[u].ub, F_s[a]); // u^t = ub + F^t(a)
-                const float t = __fmaf_ru(uu, p.onepk, p.tau);
-                act = !(t < s_s[a]);
-                if (!split_heavy || t < th_s[a]) bkey[u] = a;
-            }
+            const int ac = max(a, 0);
+            const float uu = __fadd_ru(ps[u].ub, F_s[ac]); // u^t = ub + F^t(a)
+            const float t = __fmaf_ru(uu, p.onepk, p.tau);
+            const bool valid = a != -2, assigned = a >= 0;
+            const bool act = valid && !(assigned && t < s_s[ac]);
+            bkey[u] = (assigned && t < th_s[ac]) ? a : k; // th = +inf without the heavy split
+            nvalid += valid ? 1 : 0;
             amask |= (act ? 1u : 0u) << u;
         }
         my_skipped += nvalid - __popc(amask);
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(SPT) k_mti_sel(const IterParams p, const int32
 #pragma unroll
         for (int u = 0; u < WPA; ++u) {
             if ((amask >> u) & 1u) {
-                stg[pos] = make_int2((int)(i0 + u - lo), bkey[u]);
+                stg[pos] = make_int2(o0 + u, bkey[u]);
                 ++pos;
             }
         }

@@ -441,7 +441,7 @@ static size_t plan_layout_sel(const knor_ctx *c, IterParams &p) {
     };
     p.off_s = take((size_t)k * 4);
     p.off_F = take((size_t)k * 4);
-    p.off_th = take(c->sel_M > 0 ? (size_t)k * 4 : 0);
+    p.off_th = take((size_t)k * 4);
     p.w_base = take(0);
     p.w_bucket = 0;
     // k + 1 buckets (one per cluster, and the mixed one) of 32 slots and a count

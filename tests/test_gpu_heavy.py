@@ -1,4 +1,5 @@
-"""GPU: the Clause-1 selection's heavy split, pushed to its extremes.
+"""GPU: the Clause-1 selection's heavy split and its warp count, pushed to
+their extremes.
 
 k_mti_sel sends a point whose bound reaches the M-th smallest 1/2 d(c_a, c)
 of its cluster to the mixed bucket, where the scan scores it against every
@@ -31,22 +32,25 @@ def _lib():
     knor.load()
 
 
-def _run(X, k, sel_m, iters):
-    old = os.environ.get("KNOR_SEL_M")
-    if sel_m is None:
-        os.environ.pop("KNOR_SEL_M", None)
-    else:
-        os.environ["KNOR_SEL_M"] = str(sel_m)
+def _run(X, k, sel_m, iters, sel_mult=None):
+    env = {"KNOR_SEL_M": sel_m, "KNOR_SEL_MULT": sel_mult}
+    old = {name: os.environ.get(name) for name in env}
+    for name, v in env.items():
+        if v is None:
+            os.environ.pop(name, None)
+        else:
+            os.environ[name] = str(v)
     try:
         with knor.Context(torch.as_tensor(X).cuda().contiguous(), k, seed=42, prune=True) as ctx:
             assert ctx.kernel_name("select") == "k_mti_sel"
-            stats, ties = step_and_check(X, ctx, iters, f"KNOR_SEL_M={sel_m}")
+            stats, ties = step_and_check(X, ctx, iters, f"KNOR_SEL_M={sel_m} KNOR_SEL_MULT={sel_mult}")
             return ctx.assignments(), stats, ties
     finally:
-        if old is None:
-            os.environ.pop("KNOR_SEL_M", None)
-        else:
-            os.environ["KNOR_SEL_M"] = old
+        for name, v in old.items():
+            if v is None:
+                os.environ.pop(name, None)
+            else:
+                os.environ[name] = v
 
 
 @pytest.mark.parametrize("name,make,k", [
@@ -72,3 +76,16 @@ def test_heavy_split_never_changes_the_result(name, make, k):
         if st_ref[t]["changed"] != ref.changed[t]:
             break
         assert abs(st_ref[t]["dist_evals"] - ref.evals[t]) <= slack + 0.002 * ref.evals[t], (t, st_ref[t], ref.evals[t])
+
+
+def test_one_or_two_selection_warps_per_scan_warp_agree():
+    """k_mti_sel runs two warps per scan warp where they fit (each over half
+    the range, with a record list of its own, the scan taking both lists in
+    order); KNOR_SEL_MULT=1 keeps one.  Only the order of the batches differs:
+    assignments and counters are identical, and both match the oracle."""
+    X = synth.spd_mixture(20000, 32, 20, 34).numpy()
+    a1, st1, _ = _run(X, 20, None, 12, sel_mult=1)
+    a2, st2, _ = _run(X, 20, None, 12, sel_mult=2)
+    assert np.array_equal(a1, a2)
+    for key in ("changed", "clause1_skipped", "dist_evals"):
+        assert [s[key] for s in st1] == [s[key] for s in st2], key
