@@ -153,11 +153,25 @@ __device__ __forceinline__ void tmem_regs_ready(uint32_t *r) {
                    "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
 }
 
-// One d~^2 - ||x||^2 value into a (smallest, its index, second smallest) chain.
-__device__ __forceinline__ void top2_step(float &m1, float &m2, int &i1, float t, int c) {
-    m2 = fminf(m2, fmaxf(m1, t));
-    if (t < m1) i1 = c;
-    m1 = fminf(m1, t);
+// (a * b + c) lane by lane for packed FP32 pairs, each lane rounded like the
+// scalar fma.
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Two d~^2 - ||x||^2 values, of adjacent columns c0 and c0 + 1, into a
+// (smallest m1, its index i1, second smallest m2) chain: the smaller of the
+// two (ties: t0) is compared with m1, the larger can only become the new
+// second smallest.  The result equals taking t0 and then t1 one at a time
+// (m1 and i1 replaced on a strictly smaller value, m2 = min(m2, max(m1, t))).
+__device__ __forceinline__ void top2_pair(float &m1, float &m2, int &i1, float t0, float t1, int c0) {
+    const float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+    const int ilo = t1 < t0 ? c0 + 1 : c0;
+    m2 = fminf(fminf(m2, hi), fmaxf(m1, lo));
+    if (lo < m1) i1 = ilo;
+    m1 = fminf(m1, lo);
 }
 // Merges chain b into chain a.  On equal minima the merged second smallest
 // equals the smallest: the gap is 0 and the point is never certified, so the
@@ -402,13 +416,21 @@ __global__ void __launch_bounds__(PREC_THREADS, 1)
                     const int cb = j * TN + h * HALF + cc;
                     const float4 *cn4 = reinterpret_cast<const float4 *>(cn_s + cb);
                     if (p.mode == 0) {
+                        // t = acc (-2 / (s_x s_c)) + ||c||^2 for two columns per
+                        // packed fma (each lane rounded like the scalar one);
+                        // pairs of adjacent columns into the four chains in turn
+                        const unsigned long long n2 = pack2(neg2inv, neg2inv);
 #pragma unroll
                         for (int v = 0; v < 16; ++v) {
                             const float4 cv = cn4[v];
-                            top2_step(a1[0], a2[0], ai[0], __fmaf_rn(__uint_as_float(r[4 * v + 0]), neg2inv, cv.x), cb + 4 * v + 0);
-                            top2_step(a1[1], a2[1], ai[1], __fmaf_rn(__uint_as_float(r[4 * v + 1]), neg2inv, cv.y), cb + 4 * v + 1);
-                            top2_step(a1[2], a2[2], ai[2], __fmaf_rn(__uint_as_float(r[4 * v + 2]), neg2inv, cv.z), cb + 4 * v + 2);
-                            top2_step(a1[3], a2[3], ai[3], __fmaf_rn(__uint_as_float(r[4 * v + 3]), neg2inv, cv.w), cb + 4 * v + 3);
+                            float t0, t1, t2, t3;
+                            unpack2(fma2(pack2(__uint_as_float(r[4 * v + 0]), __uint_as_float(r[4 * v + 1])), n2,
+                                         pack2(cv.x, cv.y)), t0, t1);
+                            unpack2(fma2(pack2(__uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3])), n2,
+                                         pack2(cv.z, cv.w)), t2, t3);
+                            const int ch = 2 * (v & 1);
+                            top2_pair(a1[ch], a2[ch], ai[ch], t0, t1, cb + 4 * v);
+                            top2_pair(a1[ch + 1], a2[ch + 1], ai[ch + 1], t2, t3, cb + 4 * v + 2);
                         }
                     } else {
                         // bit u of (mlo, mhi): column cb + u is a candidate
