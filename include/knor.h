@@ -250,8 +250,7 @@ knor_status knor_set_state(knor_ctx *ctx, const void *buf, size_t size);
  * library's device image, held by every GPU that loads the library until the
  * process exits; it limits k * (d + 1) to 4096 (larger sizes return
  * KNOR_ERR_ARG).  The first call on each device looks the array's device
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture on that device.  All calls share the array: calls that overlap on
+ * address up (cudaGetSymbolAddress).  All calls share the array: calls that overlap on
  * the GPU (other streams, other threads) race and give wrong results.
  * Errors: KNOR_ERR_ARG for NULL or non-device buffers and bad sizes,
  * KNOR_ERR_CUDA for CUDA failures; the message is knor_last_error(NULL). */
