@@ -28,6 +28,14 @@
  *   - Assignments follow Algorithm 1's scan: the nearest centroid, ties to the
  *     lowest index.  Iteration 1 starts from "no assignment", so every point
  *     counts as changed in it.
+ *   - Tuning switches, read from the environment by knor_create, change how
+ *     the work is grouped, never a result or a counter: KNOR_SEL_M (Clause-1
+ *     selection: a point whose bound would leave it this many Clause-2
+ *     candidates or more is scored against every centroid in a batch of its
+ *     own; default k / 3 from k = 8 on, 0 never), KNOR_SEL_MULT=1 (one
+ *     selection warp per scan warp instead of two where two fit),
+ *     KNOR_MTI_KERNEL=1 (the one-kernel MTI scan instead of the split
+ *     selection / scan / delta kernels).
  */
 #ifndef KNOR_H
 #define KNOR_H
