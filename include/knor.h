@@ -29,7 +29,7 @@
  *     lowest index.  Iteration 1 starts from "no assignment", so every point
  *     counts as changed in it.
  *   - Tuning switches, read from the environment by knor_create, change how
- *     the work is grouped, never a result or a counter: KNOR_SEL_M (Clause-1
+ *     the work is grouped, not the assignments or centroids: KNOR_SEL_M (Clause-1
  *     selection: a point whose bound would leave it this many Clause-2
  *     candidates or more is scored against every centroid in a batch of its
  *     own; default k / 3 from k = 8 on, 0 never), KNOR_SEL_MULT=1 (one
