@@ -10,10 +10,12 @@ seed 42, at most 50 iterations (the MTI FP32 configuration).
 
 Printed (rank 0, one JSON line): the device-timed throughput, the same run
 through the C ABI from pinned host memory (e2e), the roofline of the
-dominant kernel (its CUDA-event time per launch against its algorithmic
-bytes), the speed of plain FP32 Lloyd on the same input (with a check that it
-assigns identically), the FP64 CPU oracle timed on the host cores on a
-bounded sample (cpu_baseline), and the SM clocks sampled while timing.
+dominant step (the CUDA-event time of its kernels per iteration against its
+algorithmic bytes, or against its FP32 operations at the FMA rate measured in
+the same run when that roof binds), the speed of plain FP32 Lloyd on the same
+input (with a check that it assigns identically), the FP64 CPU oracle timed
+on the host cores on a bounded sample (cpu_baseline), and the SM clocks
+sampled while timing.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
                   [--workload NAME] [--no-e2e] [--no-plain] [--no-cpu]
