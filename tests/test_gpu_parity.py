@@ -161,6 +161,18 @@ def test_many_batches_per_cta(d, k):
                 check_centroids(c.centroids(), C_ref, f"d{d} k{k} it {t + 1}")
 
 
+@pytest.mark.parametrize("k", [110, 111])
+def test_split_path_largest_k(k):
+    """k = 110 is the largest k whose k x k table the split MTI scan stages
+    (48.4 KB of its CTA); k = 111 takes the other MTI kernels.  Both match the
+    oracle at every iteration, and k = 110 runs the split kernels (heavy
+    points batched apart at rank 36)."""
+    X = synth.spd_mixture(30000, 16, k, 60 + k, mean_lo=0.0, mean_hi=10.0).numpy()
+    with knor.Context(_dev(X), k, seed=8, prune=True) as c:
+        assert (c.kernel_name("mti") == "k_mti_scan<16>") == (k == 110)
+        step_and_check(X, c, 8, f"k{k}")
+
+
 def test_deterministic_rerun():
     X = _dev(synth.spd_mixture(50000, 32, 20, 22))
     out = []
